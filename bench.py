@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Benchmark of the funnel-transform hot path on GB300.
+
+Workload: 64 synthetic 1024 x 1024 FP32 images per GPU (1-20 ridge/step lines,
+occluders, noise), map 1024 x 1024 (n_slope = W, n_intercept = H), top-32
+peaks per image.  One step = ft_forward (Sec. 3.1 steps 1-4) + ft_peaks
+(Sec. 4.4) over the resident batch.  Metric: megapixels (input pixels) per
+second, whole job.  Inputs (268 MB) and maps (268 MB) exceed the 129 MB L2.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs its own 64 images (weak scaling, no
+collective on the data path); the timed region is bracketed by barriers and
+the max over ranks is reported by rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BATCH = 64
+SIDE = 1024
+TOP_K = 32
+METRIC = "megapixels/s funnel fwd(+bwd) at 1024² FP32 vs plain form; % of HBM roofline"
+UNIT = "Mpx/s"
+WORKLOAD = "64 x 1024x1024 FP32 synthetic line images, map 1024x1024, top-32 peaks per image"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--images", type=int, default=64,
+                    help="images per GPU (64 = the benchmark workload; smaller only for ncu captures)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def make_batch(rank: int) -> np.ndarray:
+    from paper_1904_09409_gb300 import synth
+    return synth.batch_1024(BATCH, start=rank * BATCH, side=SIDE)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_bytes(name: str, H: int, W: int, S: int, Hp: int, K: int) -> float:
+    """Algorithmic DRAM bytes per image of each kernel (compulsory reads and
+    writes of its own inputs and outputs)."""
+    L = Hp // 2 + 1
+    ntiles = ((Hp + 31) // 32) * ((S + 63) // 64)
+    kt = min(K, 512)
+    return {
+        "k_col_r2c": 4.0 * H * W + 8.0 * L * W,          # image in, half spectrum out
+        "k_nvmt_rows": 8.0 * L * W + 8.0 * L * S,        # spectrum rows in, G rows out
+        "k_col_c2r": 8.0 * L * S + 4.0 * Hp * S,         # G in, map out
+        "k_peak_tiles": 4.0 * Hp * S + 8.0 * ntiles * kt,  # map in, tile keys out
+        "k_peak_select": 8.0 * ntiles * kt + 20.0 * K + 4.0,
+    }.get(name, 0.0)
+
+
+def source_digest() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1904_09409_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, batch: int):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled
+    to `batch` images, or None when absent or taken on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("source_digest") != source_digest():
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    if not k:
+        return None
+    return float(k["dram_bytes_per_image"]) * batch
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons of one GPU, sampled every 200 ms."""
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.uuid and self.uuid not in parts[0]:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------- oracle (CPU) legs
+def _oracle_one(img):
+    import oracle
+    t = time.perf_counter()
+    P = oracle.funnel_ref(img, SIDE, SIDE)
+    oracle.peaks_ref(np.abs(P), TOP_K)
+    return time.perf_counter() - t
+
+
+def oracle_pool(cores: int):
+    return mp.get_context("spawn").Pool(cores)
+
+
+def time_oracle_sample(pool, imgs):
+    """Wall time of the oracle (map + peak list) on the given images, one image
+    per task, run by the pool in parallel."""
+    t = time.perf_counter()
+    per = pool.map(_oracle_one, list(imgs), chunksize=1)
+    return time.perf_counter() - t, per
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(imgs):
+    n_images = len(imgs)
+    cores = min(host_cores(), n_images)
+    with oracle_pool(cores) as pool:
+        time_oracle_sample(pool, imgs[:cores])                      # warm-up (imports)
+        wall, per = time_oracle_sample(pool, imgs)
+    px = n_images * SIDE * SIDE
+    return {"value": px / wall / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_images} of the 64 images (FP64 NumPy map + Sec. 4.4 peak list), "
+                      f"one image per task, {cores} processes; {sum(per):.1f} CPU-s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    cores = host_cores()
+    imgs = make_batch(0)
+    with oracle_pool(cores) as pool:
+        _, per0 = time_oracle_sample(pool, imgs[:cores])            # calibration (also warm-up)
+        t_img = statistics.median(per0)
+        budget = 150.0                                             # seconds for the whole run
+        n = int(budget * cores / max(t_img, 1e-3) / (args.steps + args.warmup))
+        n = max(1, min(BATCH, n))
+        for _ in range(args.warmup):
+            time_oracle_sample(pool, imgs[:n])
+        walls = [time_oracle_sample(pool, imgs[:n])[0] for _ in range(args.steps)]
+    total = sum(walls)
+    value = args.steps * n * SIDE * SIDE / total / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "global_batch": BATCH, "images_per_step_sampled": n,
+                   "parallelism": f"{cores} host processes"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{n} of the 64 images per step, one image per process"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- GPU arm
+def run_ours(args):
+    global BATCH
+    BATCH = args.images
+    import torch
+    from paper_1904_09409_gb300 import funnel as f
+
+    ws, rank, local = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    # CPU baseline first (spawned pool, before any kernel of ours runs)
+    imgs = make_batch(rank)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(imgs)
+
+    plan = f.Plan(SIDE, SIDE, SIDE, SIDE)
+    x = torch.from_numpy(imgs).to(dev)
+    m = torch.empty((BATCH, SIDE, SIDE), dtype=torch.float32, device=dev)
+    pk = torch.empty(BATCH * TOP_K * f.PEAK_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    cnt = torch.empty(BATCH, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        f.ft_forward(plan, x, m, stream=stream)
+        f.ft_peaks(plan, m, TOP_K, out=pk, count=cnt, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize(dev)
+
+    uuid = str(getattr(torch.cuda.get_device_properties(dev), "uuid", "") or "")
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    time.sleep(0.5)
+    f.ft_profile_enable(plan, True)
+    f.ft_profile_read(plan)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    clocks = sampler.stop()
+    prof = f.ft_profile_read(plan)
+    f.ft_profile_enable(plan, False)
+
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the public host-buffer call: H2D of the step's images
+    # from pinned memory, forward + peaks, D2H of the peaks and counts
+    h_img = torch.from_numpy(imgs).pin_memory()
+    h_pk = torch.empty(BATCH * TOP_K * f.PEAK_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    h_cnt = torch.empty(BATCH, dtype=torch.int32).pin_memory()
+    e2e_steps = max(3, min(args.steps, 30))
+    for _ in range(2):
+        f.ft_detect_host(plan, h_img, TOP_K, out_host=h_pk, count_host=h_cnt, stream=stream)
+    if ws > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        f.ft_detect_host(plan, h_img, TOP_K, out_host=h_pk, count_host=h_cnt, stream=stream)
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    px_step = ws * BATCH * SIDE * SIDE
+    value = args.steps * px_step / (ms / 1e3) / 1e6
+    e2e_value = e2e_steps * px_step / e2e_s / 1e6
+
+    # roofline of the dominant kernel
+    kernels = {}
+    total_kernel_ms = sum(v[0] for v in prof.values()) or 1.0
+    for name, (kms, n) in prof.items():
+        per = kms / n
+        b = kernel_bytes(name, SIDE, SIDE, SIDE, SIDE, TOP_K) * BATCH
+        kernels[name] = {"ms_per_launch": per, "launches": n, "share": kms / total_kernel_ms,
+                         "algorithmic_bytes_per_launch": b, "achieved_gbs": b / (per / 1e3) / 1e9}
+    hbm, src = measured_peaks()
+    dom = max(kernels, key=lambda k: kernels[k]["share"]) if kernels else None
+    roof = None
+    if dom:
+        k = kernels[dom]
+        roof = {"kernel": dom, "bound": "hbm", "achieved": k["achieved_gbs"], "peak": hbm,
+                "unit": "GB/s", "frac": k["achieved_gbs"] / hbm, "peak_source": src,
+                "traffic": ncu_traffic(dom, BATCH),
+                "algorithmic_bytes_per_launch": k["algorithmic_bytes_per_launch"]}
+    launches_per_step = f.ft_forward_launches(plan) + f.ft_peaks_launches(plan)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "global_batch": ws * BATCH, "images_per_gpu": BATCH,
+                       "H": SIDE, "W": SIDE, "n_slope": SIDE, "n_intercept": SIDE, "interp": "linear",
+                       "top_k": TOP_K, "l2": "inputs larger than L2 (268 MB images + 268 MB maps per GPU)",
+                       "parallelism": f"replicas x{ws}, no collective on the data path"},
+            "roofline": roof,
+            "kernels": kernels,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": ws * BATCH * SIDE * SIDE * 4,
+                    "d2h_bytes_per_step": ws * (BATCH * TOP_K * f.PEAK_DTYPE.itemsize + BATCH * 4),
+                    "call": "ft_detect_host", "steps": e2e_steps},
+            "gpu_launches": args.steps * launches_per_step,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

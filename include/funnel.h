@@ -1,0 +1,157 @@
+/*
+ * funnel.h — C ABI of the GB300 (sm_103a) funnel-transform library, libfunnel.so.
+ *
+ * The funnel transform (Wei, Feng & Zheng, "Funnel Transform for Straight Line
+ * Detection", Sec. 3.1) maps a real grayscale image to a real slope-intercept
+ * parameter map whose local maxima are the image's straight lines:
+ *   step 1  1D Fourier transform along y of the zero-expanded image (eq. 16, Sec. 4.2)
+ *   step 2  nonlinear variable-metric transform (NVMT) x' = (w2 / w_max) x, a 1D
+ *           interpolated resampling of every kept frequency row (eqs. 17-18)
+ *   step 3  1D Fourier transform along x'
+ *   step 4  inverse 1D Fourier transform along w2 (eq. 19)
+ * followed by |.| and the list-based peak detection of Sec. 4.4.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Sizes: image H x W; n_intercept = H' >= H (the expanded height, Sec. 4.2:
+ *    (H'-H)/2 zero rows above, the rest below); n_slope = S >= W (zero insertion
+ *    along x', Sec. 4.3).  W, H', S must be even; H' and S must be of the form
+ *    2^a 3^b and at most FT_MAX_LENGTH.  Otherwise FT_ERR_UNSUPPORTED_SIZE.
+ *  - Layouts (all row-major, densely packed, FP32):
+ *      image  [batch][H][W]            row = image row, col = image column
+ *      map    [batch][H'][S]           map[t][s]: intercept n = t - H'/2,
+ *                                      slope index m = s - S/2, so k = 2m/S, b = n
+ *                                      (eqs. 22-23, centred coordinates of the
+ *                                      expanded image: x = col - W/2,
+ *                                      y = row + (H'-H)/2 - H'/2)
+ *  - Ownership: the caller owns every buffer it passes.  Pointers named d_* are
+ *    device pointers on the plan's device; h_* are host pointers (pinned memory
+ *    gives the fastest copies).  The plan owns its tables and its workspace, which
+ *    grows on demand with the batch (grow = synchronise the device, free, allocate).
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device calls are asynchronous and stream-ordered.  One plan may be
+ *    used by one stream at a time; calls that overlap on the GPU with the same plan
+ *    race on its workspace.
+ *  - Errors: argument errors return synchronously without touching the GPU.  A
+ *    CUDA error seen at a call returns FT_ERR_CUDA; ft_last_error() then gives
+ *    the CUDA error text.  No C++ exception crosses the ABI.
+ */
+#ifndef FUNNEL_H
+#define FUNNEL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FT_MAX_LENGTH 8192   /* largest supported H' and S */
+#define FT_MAX_TOPK 1024     /* largest top_k of ft_peaks */
+
+typedef struct ft_plan_s* ft_plan;
+
+typedef enum {
+    FT_OK = 0,
+    FT_ERR_INVALID_ARG = 1,      /* null pointer, batch < 0, top_k out of range, bad enum */
+    FT_ERR_UNSUPPORTED_SIZE = 2, /* odd / non 2^a 3^b / too large / n_slope < W ... */
+    FT_ERR_OOM = 3,              /* a device or host allocation failed */
+    FT_ERR_CUDA = 4,             /* a CUDA runtime call or launch failed */
+    FT_ERR_TIMEOUT = 5           /* reserved for bounded waits */
+} ft_status;
+
+/* Step 2 interpolator.  Sec. IV adopts a chirp-z (band-limited) interpolator,
+ * Sec. V a linear one.  LINEAR: rows are zero outside the image columns, the
+ * sample x' H' / (2 l) is split exactly into its integer floor and remainder and
+ * the fraction is one FP32 division.  CUBIC: Keys' kernel, a = -0.5. */
+typedef enum {
+    FT_INTERP_LINEAR = 0,
+    FT_INTERP_CUBIC = 1
+} ft_interp;
+
+/* One detected peak (Sec. 4.4) with its line (eqs. 22-23):
+ * t, s = map row / column; value = |P[t][s]|; k = 2 (s - S/2) / S;
+ * b = t - H'/2 (intercept in centred coordinates of the expanded image). */
+typedef struct {
+    int32_t t;
+    int32_t s;
+    float value;
+    float k;
+    float b;
+} ft_peak;
+
+/* Create a plan for H x W images, n_slope x n_intercept maps, interpolator
+ * `interp` (an ft_interp).  Builds the FP64-derived twiddle tables on the host and
+ * copies them to the current CUDA device, which becomes the plan's device.
+ * *out is set to NULL on failure. */
+ft_status ft_plan_create(ft_plan* out, int H, int W, int n_slope, int n_intercept, int interp);
+
+/* Release the plan's tables and workspace (synchronises the plan's device).
+ * NULL is accepted. */
+ft_status ft_plan_destroy(ft_plan plan);
+
+/* Sec. 3.1 steps 1-4: d_map[b] = P(d_img[b]) for b < batch.  batch = 0 is a
+ * no-op.  d_img: [batch][H][W], d_map: [batch][H'][S], both FP32, 8-byte
+ * aligned.  Launches 3 kernels on `stream`. */
+ft_status ft_forward(ft_plan plan, const float* d_img, float* d_map, int batch, void* stream);
+
+/* Exact adjoint (transpose) of ft_forward, which is linear in the image:
+ * d_grad_img = A^T d_grad_map, so <A x, y> = <x, A^T y>.  Same layouts and rules
+ * as ft_forward with the roles of the two buffers exchanged. */
+ft_status ft_backward(ft_plan plan, const float* d_grad_map, float* d_grad_img, int batch,
+                      void* stream);
+
+/* Sec. 4.4 on |d_map| per image: the cells that no earlier-visited 3 x 3
+ * neighbour precedes (order: |P| descending, then linear index t*S + s
+ * ascending; the neighbourhood wraps around both axes), with |P| >= threshold,
+ * the first top_k of them in that order.  d_out: [batch][top_k] ft_peak;
+ * d_count: [batch] int32, the number of peaks written (< top_k when fewer pass
+ * the threshold; unused slots are zeroed).  1 <= top_k <= FT_MAX_TOPK. */
+ft_status ft_peaks(ft_plan plan, const float* d_map, int batch, int top_k, float threshold,
+                   ft_peak* d_out, int32_t* d_count, void* stream);
+
+/* End-to-end detection from host memory: copies h_img ([batch][H][W]) to a
+ * plan-owned device buffer, runs ft_forward and ft_peaks, copies the peaks and
+ * counts back to h_out ([batch][top_k]) and h_count ([batch]) and synchronises
+ * `stream` before returning. */
+ft_status ft_detect_host(ft_plan plan, const float* h_img, int batch, int top_k, float threshold,
+                         ft_peak* h_out, int32_t* h_count, void* stream);
+
+/* Bytes of plan-owned device workspace that a call with this batch needs. */
+size_t ft_workspace_bytes(ft_plan plan, int batch);
+
+/* Number of kernel launches ft_forward / ft_peaks issue per call. */
+int ft_forward_launches(ft_plan plan);
+int ft_peaks_launches(ft_plan plan);
+
+/* Kernel identifiers of the per-launch timing below. */
+typedef enum {
+    FT_KERNEL_COL_R2C = 0,         /* step 1 (and the transpose of step 4) */
+    FT_KERNEL_NVMT_ROWS = 1,       /* steps 2-3 */
+    FT_KERNEL_COL_C2R = 2,         /* step 4 (and the transpose of step 1) */
+    FT_KERNEL_PEAK_TILES = 3,      /* Sec. 4.4, local maxima per tile */
+    FT_KERNEL_PEAK_SELECT = 4,     /* Sec. 4.4, top_k per image */
+    FT_KERNEL_NVMT_ROWS_ADJ = 5,   /* transpose of steps 2-3 */
+    FT_KERNEL_COUNT = 6
+} ft_kernel_id;
+
+/* Per-launch timing (a measurement aid, off by default).  While enabled, every
+ * kernel launch of this plan is bracketed by two CUDA events recorded on the
+ * launching stream.  ft_profile_read synchronises those events, adds each
+ * launch's elapsed time to total_ms[id] and its count to launches[id] for
+ * id < n (arrays of n entries, zeroed first), and forgets the records. */
+ft_status ft_profile_enable(ft_plan plan, int enable);
+ft_status ft_profile_read(ft_plan plan, double* total_ms, int32_t* launches, int n);
+const char* ft_kernel_name(int id);
+
+/* Static text for a status; never NULL. */
+const char* ft_status_string(ft_status status);
+
+/* Text of the last CUDA error seen by any call in this thread ("" if none). */
+const char* ft_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FUNNEL_H */

@@ -1,0 +1,231 @@
+// Internal declarations of libfunnel: plan object, FFT descriptors, complex
+// helpers, the shared-memory mixed-radix FFT used by every transform kernel,
+// and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "funnel.h"
+
+#define FT_MAX_STAGES 16
+#define FT_THREADS 256
+
+// One FFT length N = 2^a 3^b: its radix sequence and twiddle table
+// tw[t] = exp(-2 pi i t / N), t in [0, N), rounded to FP32 from FP64 values.
+struct FftLen {
+    int N;
+    int nst;
+    int radix[FT_MAX_STAGES];
+    const float2* tw;
+};
+
+// ------------------------------------------------------------ complex helpers
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// multiply by (SIGN * i): SIGN = +1 -> i*a, SIGN = -1 -> -i*a
+template <int SIGN>
+__device__ __forceinline__ float2 cmul_si(float2 a) {
+    return SIGN > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// Twiddle exp(SIGN * 2 pi i t / N) from the table of exp(-2 pi i t / N).
+template <int SIGN>
+__device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int t) {
+    float2 w = __ldg(tw + t);
+    return SIGN > 0 ? make_float2(w.x, -w.y) : w;
+}
+
+// ---------------------------------------------------------- radix-R kernels
+// y_k = sum_q u_q exp(SIGN 2 pi i q k / R), in place.
+template <int R, int SIGN>
+struct Dft;
+
+template <int SIGN>
+struct Dft<2, SIGN> {
+    __device__ __forceinline__ static void run(float2* u) {
+        float2 a = u[0], b = u[1];
+        u[0] = cadd(a, b);
+        u[1] = csub(a, b);
+    }
+};
+
+template <int SIGN>
+struct Dft<3, SIGN> {
+    __device__ __forceinline__ static void run(float2* u) {
+        const float h = 0.86602540378443864676f;   // sqrt(3)/2
+        float2 s = cadd(u[1], u[2]);
+        float2 d = csub(u[1], u[2]);
+        float2 y0 = cadd(u[0], s);
+        float2 t1 = make_float2(u[0].x - 0.5f * s.x, u[0].y - 0.5f * s.y);
+        float2 t2 = cscale(cmul_si<SIGN>(d), h);
+        u[0] = y0;
+        u[1] = cadd(t1, t2);
+        u[2] = csub(t1, t2);
+    }
+};
+
+template <int SIGN>
+struct Dft<4, SIGN> {
+    __device__ __forceinline__ static void run(float2* u) {
+        float2 a = cadd(u[0], u[2]), b = csub(u[0], u[2]);
+        float2 c = cadd(u[1], u[3]), d = cmul_si<SIGN>(csub(u[1], u[3]));
+        u[0] = cadd(a, c);
+        u[2] = csub(a, c);
+        u[1] = cadd(b, d);
+        u[3] = csub(b, d);
+    }
+};
+
+template <int SIGN>
+struct Dft<8, SIGN> {
+    __device__ __forceinline__ static void run(float2* u) {
+        const float r = 0.70710678118654752440f;   // sqrt(2)/2
+        float2 e[4] = {u[0], u[2], u[4], u[6]};
+        float2 o[4] = {u[1], u[3], u[5], u[7]};
+        Dft<4, SIGN>::run(e);
+        Dft<4, SIGN>::run(o);
+        // w8^k = exp(SIGN 2 pi i k / 8)
+        float2 o1 = make_float2(r * (o[1].x - SIGN * o[1].y), r * (o[1].y + SIGN * o[1].x));
+        float2 o2 = cmul_si<SIGN>(o[2]);
+        float2 o3 = make_float2(r * (-o[3].x - SIGN * o[3].y), r * (-o[3].y + SIGN * o[3].x));
+        u[0] = cadd(e[0], o[0]);
+        u[4] = csub(e[0], o[0]);
+        u[1] = cadd(e[1], o1);
+        u[5] = csub(e[1], o1);
+        u[2] = cadd(e[2], o2);
+        u[6] = csub(e[2], o2);
+        u[3] = cadd(e[3], o3);
+        u[7] = csub(e[3], o3);
+    }
+};
+
+// ------------------------------------------------- Stockham stage (autosort)
+// B transforms of length N interleaved in shared memory as x[n * B + f].
+// Stage with radix R after sub-transforms of length p: for i in [0, N/R),
+// k = i mod p, inputs x[i + q N/R] twiddled by exp(SIGN 2 pi i q k / (p R)),
+// radix-R DFT, outputs y[(i - k) R + k + q p].
+template <int R, int SIGN>
+__device__ __forceinline__ void fft_stage(const float2* __restrict__ x, float2* __restrict__ y,
+                                          int N, int logB, int p, const float2* __restrict__ tw) {
+    const int B = 1 << logB;
+    const int NR = N / R;
+    const int tws = N / (p * R);
+    const int total = NR << logB;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int f = idx & (B - 1);
+        const int i = idx >> logB;
+        const int k = i % p;
+        float2 u[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) u[q] = x[((i + q * NR) << logB) + f];
+        if (p > 1) {
+#pragma unroll
+            for (int q = 1; q < R; ++q) u[q] = cmul(u[q], twiddle<SIGN>(tw, q * k * tws));
+        }
+        Dft<R, SIGN>::run(u);
+        const int j = (i - k) * R + k;
+#pragma unroll
+        for (int q = 0; q < R; ++q) y[((j + q * p) << logB) + f] = u[q];
+    }
+}
+
+// Full transform of the B interleaved sequences in `a` (length N each) using
+// `b` as the ping-pong buffer.  Returns the buffer that holds the result.
+// Must be called by every thread of the block; ends with __syncthreads().
+template <int SIGN>
+__device__ float2* cta_fft(float2* a, float2* b, const FftLen& L, int logB) {
+    int p = 1;
+    for (int s = 0; s < L.nst; ++s) {
+        const int R = L.radix[s];
+        switch (R) {
+            case 2: fft_stage<2, SIGN>(a, b, L.N, logB, p, L.tw); break;
+            case 3: fft_stage<3, SIGN>(a, b, L.N, logB, p, L.tw); break;
+            case 4: fft_stage<4, SIGN>(a, b, L.N, logB, p, L.tw); break;
+            default: fft_stage<8, SIGN>(a, b, L.N, logB, p, L.tw); break;
+        }
+        __syncthreads();
+        float2* t = a;
+        a = b;
+        b = t;
+        p *= R;
+    }
+    return a;
+}
+
+// -------------------------------------------------------------- plan object
+struct ft_plan_s {
+    int H, W, S, Hp, L, interp, top;
+    int device;
+    FftLen fy;              // length H' (steps 1 and 4)
+    FftLen fx;              // length S  (step 3)
+    float2* d_tw;           // both twiddle tables in one allocation
+    // workspace: spectrum / G rows [batch][L][S] complex, then peak keys
+    void* d_ws;
+    size_t ws_bytes;
+    // host-path buffers of ft_detect_host
+    float* d_img_host;
+    size_t img_host_bytes;
+    float* d_map_host;
+    size_t map_host_bytes;
+    ft_peak* d_peaks_host;
+    int32_t* d_count_host;
+    size_t peaks_host_bytes;
+    // launch shapes
+    int col_logB_y;         // transforms per CTA (log2) for length H'
+    int row_logB_x;         // rows per CTA (log2) for length S
+    // per-launch timing (ft_profile_enable / ft_profile_read)
+    int prof_on;
+    size_t prof_used;
+    std::vector<cudaEvent_t> prof_pool;
+    std::vector<int> prof_ids;      // kernel id of each recorded launch (events 2i, 2i+1)
+};
+
+// -------------------------------------------------------- kernel launchers
+// All return the cudaError_t of the launch.
+
+// Step 1 (and the transpose of step 4): real columns -> half spectra.
+// in: [batch] x rows_in x ncols (pitch in_pitch floats, image stride in_img),
+// zero-expanded to N rows with the first input row at expanded row `row0`.
+// out[l][c] (complex, pitch out_pitch, image stride out_img) for l in [0, N/2],
+// scaled by end_scale (l = 0, N/2) or mid_scale (0 < l < N/2).
+cudaError_t launch_col_r2c(const float* in, int rows_in, int ncols, int in_pitch, size_t in_img,
+                           int row0, const FftLen& f, int logB, float2* out, int out_pitch,
+                           size_t out_img, float end_scale, float mid_scale, int batch,
+                           cudaStream_t st);
+
+// Step 4 (and the transpose of step 1): half spectra -> real columns.
+// in[l][c] (complex, pitch in_pitch, image stride in_img) for l in [0, N/2]; the
+// end bins enter through their real part, interior bins are scaled by mid_scale;
+// out rows t in [row0, row0 + rows_out) of the length-N result, times out_scale,
+// go to out[(t - row0)][c] (pitch out_pitch floats, image stride out_img).
+cudaError_t launch_col_c2r(const float2* in, int ncols, int in_pitch, size_t in_img,
+                           const FftLen& f, int logB, float mid_scale, float* out, int row0,
+                           int rows_out, int out_pitch, size_t out_img, float out_scale,
+                           int batch, cudaStream_t st);
+
+// Steps 2-3 in place on ws rows l in [0, L): gather/interpolate W columns to S
+// samples, transform with exp(+j), write S values.  Row 0 becomes zero.
+cudaError_t launch_nvmt_rows(float2* ws, int W, int S, int Hp, int L, int interp,
+                             const FftLen& fx, int logRB, int batch, cudaStream_t st);
+
+// Transpose of steps 2-3 in place: S values -> transform with exp(-j) ->
+// scatter of the interpolation weights gathered back to W columns.
+cudaError_t launch_nvmt_rows_adjoint(float2* ws, int W, int S, int Hp, int L, int interp,
+                                     const FftLen& fx, int logRB, int batch, cudaStream_t st);
+
+// Peak detection of Sec. 4.4: per-tile strict local maxima -> per-tile best
+// keys (launch_peak_tiles), then per-image selection of the top_k keys in order
+// (launch_peak_select).  keys must hold peaks_key_bytes() bytes.
+cudaError_t launch_peak_tiles(const float* map, int Hp, int S, int batch, int top_k, float threshold,
+                              unsigned long long* keys, cudaStream_t st);
+cudaError_t launch_peak_select(const unsigned long long* keys, int Hp, int S, int batch, int top_k,
+                               ft_peak* out, int32_t* count, cudaStream_t st);
+size_t peaks_key_bytes(int Hp, int S, int batch, int top_k);

@@ -1,0 +1,367 @@
+// C ABI of libfunnel: plan creation (validation, FP64-derived twiddle tables,
+// launch shapes), workspace management and the forward / adjoint / peak /
+// host-buffer entry points declared in funnel.h.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "ft_internal.cuh"
+
+static thread_local char g_last_error[256] = "";
+
+static ft_status cuda_fail(cudaError_t e, const char* where) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
+    return FT_ERR_CUDA;
+}
+
+#define FT_CUDA(call, where)                              \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+// N = 2^a 3^b with N even?  Fills the radix list (8s, then one 4 or 2, then 3s).
+static bool factorize(int N, FftLen* f) {
+    if (N < 2 || N > FT_MAX_LENGTH || (N & 1)) return false;
+    int m = N, p2 = 0, p3 = 0;
+    while (m % 2 == 0) { m /= 2; ++p2; }
+    while (m % 3 == 0) { m /= 3; ++p3; }
+    if (m != 1) return false;
+    int n = 0;
+    while (p2 >= 3) { f->radix[n++] = 8; p2 -= 3; }
+    if (p2 == 2) f->radix[n++] = 4;
+    if (p2 == 1) f->radix[n++] = 2;
+    for (int i = 0; i < p3; ++i) f->radix[n++] = 3;
+    if (n > FT_MAX_STAGES) return false;
+    f->N = N;
+    f->nst = n;
+    return true;
+}
+
+// tw[t] = exp(-2 pi i t / N) in FP64, rounded once to FP32.  The angle is reduced
+// to the first octant with exact integer arithmetic before calling cos/sin.
+static void twiddles(int N, float2* out) {
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int t = 0; t < N; ++t) {
+        // 8 t / N = octant + remainder; use symmetries of cos/sin
+        long long u = (long long)t * 8;
+        int oct = (int)(u / N);
+        long long r = u - (long long)oct * N;    // angle = 2 pi (oct N + r) / (8 N)
+        double th = two_pi * (double)r / (8.0 * N);
+        double c = cos(th), s = sin(th);
+        // rotate by oct * 45 degrees exactly via exact pairs
+        double cc, ss;
+        const double h = 0.70710678118654752440084436210485;
+        switch (oct & 7) {
+            case 0: cc = c; ss = s; break;
+            case 1: cc = h * (c - s); ss = h * (c + s); break;
+            case 2: cc = -s; ss = c; break;
+            case 3: cc = -h * (c + s); ss = h * (c - s); break;
+            case 4: cc = -c; ss = -s; break;
+            case 5: cc = -h * (c - s); ss = -h * (c + s); break;
+            case 6: cc = s; ss = -c; break;
+            default: cc = h * (c + s); ss = -h * (c - s); break;
+        }
+        out[t] = make_float2((float)cc, (float)(-ss));
+    }
+}
+
+// ------------------------------------------------------ per-launch timing
+static bool prof_begin(ft_plan p, int id, cudaStream_t st) {
+    if (!p->prof_on) return false;
+    while (p->prof_pool.size() < p->prof_used + 2) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return false;
+        p->prof_pool.push_back(e);
+    }
+    if (cudaEventRecord(p->prof_pool[p->prof_used], st) != cudaSuccess) return false;
+    p->prof_ids.push_back(id);
+    p->prof_used += 2;
+    return true;
+}
+
+static void prof_end(ft_plan p, cudaStream_t st) { cudaEventRecord(p->prof_pool[p->prof_used - 1], st); }
+
+#define FT_LAUNCH(p, id, st, call, where)                    \
+    do {                                                     \
+        const bool pr_ = prof_begin((p), (id), (st));        \
+        cudaError_t e_ = (call);                             \
+        if (pr_) prof_end((p), (st));                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where);  \
+    } while (0)
+
+static int log2_floor(int v) {
+    int l = 0;
+    while ((2 << l) <= v) ++l;
+    return l;
+}
+
+static void free_ws(ft_plan p) {
+    if (p->d_ws) cudaFree(p->d_ws);
+    p->d_ws = nullptr;
+    p->ws_bytes = 0;
+}
+
+static ft_status ensure(void** ptr, size_t* have, size_t need, const char* what) {
+    if (need <= *have && *ptr) return FT_OK;
+    if (*ptr) {
+        cudaDeviceSynchronize();
+        cudaFree(*ptr);
+        *ptr = nullptr;
+        *have = 0;
+    }
+    cudaError_t e = cudaMalloc(ptr, need);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cuda_fail(e, what);
+        return FT_ERR_OOM;
+    }
+    *have = need;
+    return FT_OK;
+}
+
+static size_t spec_bytes(ft_plan p, int batch) { return (size_t)batch * p->L * p->S * sizeof(float2); }
+
+extern "C" {
+
+const char* ft_status_string(ft_status s) {
+    switch (s) {
+        case FT_OK: return "ok";
+        case FT_ERR_INVALID_ARG: return "invalid argument";
+        case FT_ERR_UNSUPPORTED_SIZE: return "unsupported size";
+        case FT_ERR_OOM: return "out of memory";
+        case FT_ERR_CUDA: return "CUDA error";
+        case FT_ERR_TIMEOUT: return "timeout";
+    }
+    return "unknown status";
+}
+
+const char* ft_last_error(void) { return g_last_error; }
+
+ft_status ft_plan_create(ft_plan* out, int H, int W, int n_slope, int n_intercept, int interp) {
+    if (!out) return FT_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (interp != FT_INTERP_LINEAR && interp != FT_INTERP_CUBIC) return FT_ERR_INVALID_ARG;
+    if (H < 1 || W < 2 || (W & 1) || n_slope < W || n_intercept < H) return FT_ERR_UNSUPPORTED_SIZE;
+    FftLen fy = {}, fx = {};
+    if (!factorize(n_intercept, &fy) || !factorize(n_slope, &fx)) return FT_ERR_UNSUPPORTED_SIZE;
+
+    ft_plan p = new (std::nothrow) ft_plan_s();
+    if (!p) return FT_ERR_OOM;
+    p->H = H;
+    p->W = W;
+    p->S = n_slope;
+    p->Hp = n_intercept;
+    p->L = n_intercept / 2 + 1;
+    p->interp = interp;
+    p->top = (n_intercept - H) / 2;
+    p->fy = fy;
+    p->fx = fx;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    std::vector<float2> tw((size_t)fy.N + fx.N);
+    twiddles(fy.N, tw.data());
+    twiddles(fx.N, tw.data() + fy.N);
+    e = cudaMalloc(&p->d_tw, tw.size() * sizeof(float2));
+    if (e != cudaSuccess) {
+        delete p;
+        cuda_fail(e, "cudaMalloc(twiddles)");
+        return FT_ERR_OOM;
+    }
+    e = cudaMemcpy(p->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(p->d_tw);
+        delete p;
+        return cuda_fail(e, "cudaMemcpy(twiddles)");
+    }
+    p->fy.tw = p->d_tw;
+    p->fx.tw = p->d_tw + fy.N;
+    // transforms per block: 2 ping-pong buffers of N x B complex within 96 KB
+    const int cap = 96 * 1024 / (int)(2 * sizeof(float2));
+    p->col_logB_y = log2_floor(cap / fy.N > 0 ? cap / fy.N : 1);
+    if (p->col_logB_y > 4) p->col_logB_y = 4;
+    const int rcap = 96 * 1024 / (int)sizeof(float2) / (W + 2 * n_slope);
+    p->row_logB_x = log2_floor(rcap > 0 ? rcap : 1);
+    if (p->row_logB_x > 4) p->row_logB_x = 4;
+    *out = p;
+    return FT_OK;
+}
+
+ft_status ft_plan_destroy(ft_plan p) {
+    if (!p) return FT_OK;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(p->device);
+    cudaDeviceSynchronize();
+    free_ws(p);
+    if (p->d_tw) cudaFree(p->d_tw);
+    if (p->d_img_host) cudaFree(p->d_img_host);
+    if (p->d_map_host) cudaFree(p->d_map_host);
+    if (p->d_peaks_host) cudaFree(p->d_peaks_host);
+    for (cudaEvent_t e : p->prof_pool) cudaEventDestroy(e);
+    cudaSetDevice(cur);
+    delete p;
+    return FT_OK;
+}
+
+size_t ft_workspace_bytes(ft_plan p, int batch) {
+    if (!p || batch <= 0) return 0;
+    return spec_bytes(p, batch);
+}
+
+int ft_forward_launches(ft_plan p) { return p ? 3 : 0; }
+int ft_peaks_launches(ft_plan p) { return p ? 2 : 0; }
+
+ft_status ft_forward(ft_plan p, const float* d_img, float* d_map, int batch, void* stream) {
+    if (!p || batch < 0 || batch > 65535) return FT_ERR_INVALID_ARG;
+    if (batch == 0) return FT_OK;
+    if (!d_img || !d_map || ((uintptr_t)d_img & 7) || ((uintptr_t)d_map & 7)) return FT_ERR_INVALID_ARG;
+    ft_status s = ensure(&p->d_ws, &p->ws_bytes, spec_bytes(p, batch), "cudaMalloc(workspace)");
+    if (s != FT_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    float2* ws = (float2*)p->d_ws;
+    const size_t ws_img = (size_t)p->L * p->S;
+    FT_LAUNCH(p, FT_KERNEL_COL_R2C, st,
+              launch_col_r2c(d_img, p->H, p->W, p->W, (size_t)p->H * p->W, p->top, p->fy,
+                             p->col_logB_y, ws, p->S, ws_img, 1.f, 1.f, batch, st),
+              "step 1 (column R2C)");
+    FT_LAUNCH(p, FT_KERNEL_NVMT_ROWS, st,
+              launch_nvmt_rows(ws, p->W, p->S, p->Hp, p->L, p->interp, p->fx, p->row_logB_x, batch, st),
+              "steps 2-3 (NVMT + row FFT)");
+    FT_LAUNCH(p, FT_KERNEL_COL_C2R, st,
+              launch_col_c2r(ws, p->S, p->S, ws_img, p->fy, p->col_logB_y, 1.f, d_map, 0, p->Hp, p->S,
+                             (size_t)p->Hp * p->S, 1.f / (float)p->Hp, batch, st),
+              "step 4 (column C2R)");
+    return FT_OK;
+}
+
+ft_status ft_backward(ft_plan p, const float* d_grad_map, float* d_grad_img, int batch, void* stream) {
+    if (!p || batch < 0 || batch > 65535) return FT_ERR_INVALID_ARG;
+    if (batch == 0) return FT_OK;
+    if (!d_grad_map || !d_grad_img || ((uintptr_t)d_grad_map & 7) || ((uintptr_t)d_grad_img & 7))
+        return FT_ERR_INVALID_ARG;
+    ft_status s = ensure(&p->d_ws, &p->ws_bytes, spec_bytes(p, batch), "cudaMalloc(workspace)");
+    if (s != FT_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    float2* ws = (float2*)p->d_ws;
+    const size_t ws_img = (size_t)p->L * p->S;
+    const float inv = 1.f / (float)p->Hp;
+    FT_LAUNCH(p, FT_KERNEL_COL_R2C, st,
+              launch_col_r2c(d_grad_map, p->Hp, p->S, p->S, (size_t)p->Hp * p->S, 0, p->fy,
+                             p->col_logB_y, ws, p->S, ws_img, inv, 2.f * inv, batch, st),
+              "adjoint of step 4");
+    FT_LAUNCH(p, FT_KERNEL_NVMT_ROWS_ADJ, st,
+              launch_nvmt_rows_adjoint(ws, p->W, p->S, p->Hp, p->L, p->interp, p->fx, p->row_logB_x,
+                                       batch, st),
+              "adjoint of steps 2-3");
+    FT_LAUNCH(p, FT_KERNEL_COL_C2R, st,
+              launch_col_c2r(ws, p->W, p->S, ws_img, p->fy, p->col_logB_y, 0.5f, d_grad_img, p->top,
+                             p->H, p->W, (size_t)p->H * p->W, 1.f, batch, st),
+              "adjoint of step 1");
+    return FT_OK;
+}
+
+ft_status ft_peaks(ft_plan p, const float* d_map, int batch, int top_k, float threshold,
+                   ft_peak* d_out, int32_t* d_count, void* stream) {
+    if (!p || batch < 0 || batch > 65535) return FT_ERR_INVALID_ARG;
+    if (top_k < 1 || top_k > FT_MAX_TOPK) return FT_ERR_INVALID_ARG;
+    if (batch == 0) return FT_OK;
+    if (!d_map || !d_out || !d_count) return FT_ERR_INVALID_ARG;
+    // the key buffer lives after the spectrum workspace of this batch
+    const size_t spec = spec_bytes(p, batch);
+    const size_t keys = peaks_key_bytes(p->Hp, p->S, batch, top_k);
+    const size_t off = (spec + 255) & ~(size_t)255;
+    ft_status s = ensure(&p->d_ws, &p->ws_bytes, off + keys, "cudaMalloc(workspace)");
+    if (s != FT_OK) return s;
+    unsigned long long* kbuf = (unsigned long long*)((char*)p->d_ws + off);
+    cudaStream_t st = (cudaStream_t)stream;
+    FT_LAUNCH(p, FT_KERNEL_PEAK_TILES, st,
+              launch_peak_tiles(d_map, p->Hp, p->S, batch, top_k, threshold, kbuf, st),
+              "peak detection (tiles)");
+    FT_LAUNCH(p, FT_KERNEL_PEAK_SELECT, st,
+              launch_peak_select(kbuf, p->Hp, p->S, batch, top_k, d_out, d_count, st),
+              "peak detection (select)");
+    return FT_OK;
+}
+
+ft_status ft_profile_enable(ft_plan p, int enable) {
+    if (!p) return FT_ERR_INVALID_ARG;
+    p->prof_on = enable ? 1 : 0;
+    return FT_OK;
+}
+
+ft_status ft_profile_read(ft_plan p, double* total_ms, int32_t* launches, int n) {
+    if (!p || n < 0 || (n > 0 && (!total_ms || !launches))) return FT_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+        total_ms[i] = 0.0;
+        launches[i] = 0;
+    }
+    ft_status st = FT_OK;
+    for (size_t r = 0; r < p->prof_ids.size(); ++r) {
+        cudaEvent_t a = p->prof_pool[2 * r], b = p->prof_pool[2 * r + 1];
+        cudaError_t e = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "ft_profile_read");
+            break;
+        }
+        const int id = p->prof_ids[r];
+        if (id < n) {
+            total_ms[id] += ms;
+            launches[id] += 1;
+        }
+    }
+    p->prof_ids.clear();
+    p->prof_used = 0;
+    return st;
+}
+
+const char* ft_kernel_name(int id) {
+    switch (id) {
+        case FT_KERNEL_COL_R2C: return "k_col_r2c";
+        case FT_KERNEL_NVMT_ROWS: return "k_nvmt_rows";
+        case FT_KERNEL_COL_C2R: return "k_col_c2r";
+        case FT_KERNEL_PEAK_TILES: return "k_peak_tiles";
+        case FT_KERNEL_PEAK_SELECT: return "k_peak_select";
+        case FT_KERNEL_NVMT_ROWS_ADJ: return "k_nvmt_rows_adjoint";
+    }
+    return "unknown";
+}
+
+ft_status ft_detect_host(ft_plan p, const float* h_img, int batch, int top_k, float threshold,
+                         ft_peak* h_out, int32_t* h_count, void* stream) {
+    if (!p || batch < 0 || batch > 65535 || top_k < 1 || top_k > FT_MAX_TOPK) return FT_ERR_INVALID_ARG;
+    if (batch == 0) return FT_OK;
+    if (!h_img || !h_out || !h_count) return FT_ERR_INVALID_ARG;
+    const size_t img_b = (size_t)batch * p->H * p->W * sizeof(float);
+    const size_t map_b = (size_t)batch * p->Hp * p->S * sizeof(float);
+    const size_t pk_b = (size_t)batch * top_k * sizeof(ft_peak);
+    const size_t cnt_off = (pk_b + 255) & ~(size_t)255;
+    ft_status s;
+    if ((s = ensure((void**)&p->d_img_host, &p->img_host_bytes, img_b, "cudaMalloc(image)")) != FT_OK) return s;
+    if ((s = ensure((void**)&p->d_map_host, &p->map_host_bytes, map_b, "cudaMalloc(map)")) != FT_OK) return s;
+    if ((s = ensure((void**)&p->d_peaks_host, &p->peaks_host_bytes, cnt_off + batch * sizeof(int32_t),
+                    "cudaMalloc(peaks)")) != FT_OK)
+        return s;
+    p->d_count_host = (int32_t*)((char*)p->d_peaks_host + cnt_off);
+    cudaStream_t st = (cudaStream_t)stream;
+    FT_CUDA(cudaMemcpyAsync(p->d_img_host, h_img, img_b, cudaMemcpyHostToDevice, st), "copy image in");
+    if ((s = ft_forward(p, p->d_img_host, p->d_map_host, batch, stream)) != FT_OK) return s;
+    if ((s = ft_peaks(p, p->d_map_host, batch, top_k, threshold, p->d_peaks_host, p->d_count_host,
+                      stream)) != FT_OK)
+        return s;
+    FT_CUDA(cudaMemcpyAsync(h_out, p->d_peaks_host, pk_b, cudaMemcpyDeviceToHost, st), "copy peaks out");
+    FT_CUDA(cudaMemcpyAsync(h_count, p->d_count_host, batch * sizeof(int32_t), cudaMemcpyDeviceToHost, st),
+            "copy counts out");
+    FT_CUDA(cudaStreamSynchronize(st), "synchronise");
+    return FT_OK;
+}
+
+}  // extern "C"

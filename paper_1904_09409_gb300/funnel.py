@@ -1,0 +1,280 @@
+"""ctypes binding of libfunnel.so (include/funnel.h), same names as the C ABI.
+
+Argument marshalling only: every step of the transform runs in the library's
+CUDA kernels.  Tensors are torch CUDA tensors (device memory and streams come
+from PyTorch); host-buffer calls take contiguous CPU tensors or numpy arrays.
+There is no CPU fallback: if the library is not built, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Tuple
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libfunnel.so")
+
+FT_OK = 0
+FT_ERR_INVALID_ARG = 1
+FT_ERR_UNSUPPORTED_SIZE = 2
+FT_ERR_OOM = 3
+FT_ERR_CUDA = 4
+FT_ERR_TIMEOUT = 5
+FT_INTERP_LINEAR = 0
+FT_INTERP_CUBIC = 1
+FT_MAX_LENGTH = 8192
+FT_MAX_TOPK = 1024
+INTERP_NAMES = {"linear": FT_INTERP_LINEAR, "cubic": FT_INTERP_CUBIC}
+
+EXPORTED = (
+    "ft_plan_create", "ft_plan_destroy", "ft_forward", "ft_backward", "ft_peaks",
+    "ft_detect_host", "ft_workspace_bytes", "ft_forward_launches", "ft_peaks_launches",
+    "ft_status_string", "ft_last_error", "ft_profile_enable", "ft_profile_read", "ft_kernel_name",
+)
+FT_KERNEL_COUNT = 6
+
+
+class FtPeak(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_int32), ("s", ctypes.c_int32), ("value", ctypes.c_float),
+                ("k", ctypes.c_float), ("b", ctypes.c_float)]
+
+
+PEAK_DTYPE = np.dtype([("t", np.int32), ("s", np.int32), ("value", np.float32),
+                       ("k", np.float32), ("b", np.float32)])
+
+
+class FunnelError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: status {status}" + (f" ({detail})" if detail else ""))
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libfunnel.so (built by ``paper_1904_09409_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; run `python -c \"import __graft_entry__ as g; "
+                           "g.build()\"` first (there is no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, ci, cf = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+    L.ft_plan_create.argtypes = [ctypes.POINTER(vp), ci, ci, ci, ci, ci]
+    L.ft_plan_destroy.argtypes = [vp]
+    L.ft_forward.argtypes = [vp, vp, vp, ci, vp]
+    L.ft_backward.argtypes = [vp, vp, vp, ci, vp]
+    L.ft_peaks.argtypes = [vp, vp, ci, ci, cf, vp, vp, vp]
+    L.ft_detect_host.argtypes = [vp, vp, ci, ci, cf, vp, vp, vp]
+    L.ft_workspace_bytes.argtypes = [vp, ci]
+    L.ft_workspace_bytes.restype = ctypes.c_size_t
+    L.ft_forward_launches.argtypes = [vp]
+    L.ft_peaks_launches.argtypes = [vp]
+    L.ft_status_string.argtypes = [ci]
+    L.ft_status_string.restype = ctypes.c_char_p
+    L.ft_last_error.argtypes = []
+    L.ft_last_error.restype = ctypes.c_char_p
+    L.ft_profile_enable.argtypes = [vp, ci]
+    L.ft_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32), ci]
+    L.ft_kernel_name.argtypes = [ci]
+    L.ft_kernel_name.restype = ctypes.c_char_p
+    for name in ("ft_profile_enable", "ft_profile_read", "ft_plan_create", "ft_plan_destroy", "ft_forward", "ft_backward", "ft_peaks",
+                 "ft_detect_host", "ft_forward_launches", "ft_peaks_launches"):
+        getattr(L, name).restype = ci
+    _lib = L
+    return L
+
+
+def _check(status: int, where: str) -> None:
+    if status != FT_OK:
+        L = lib()
+        text = L.ft_status_string(status).decode()
+        detail = L.ft_last_error().decode() if status == FT_ERR_CUDA else ""
+        raise FunnelError(status, where, text + (f"; {detail}" if detail else ""))
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dev_ptr(t, dtype_name: str, numel: int, what: str) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if t.dtype != getattr(torch, dtype_name) or not t.is_contiguous():
+        raise TypeError(f"{what} must be a contiguous {dtype_name} tensor")
+    if t.numel() < numel:
+        raise ValueError(f"{what} holds {t.numel()} elements, needs {numel}")
+    return t.data_ptr()
+
+
+class Plan:
+    """Owns an ft_plan handle; sizes as in ft_plan_create."""
+
+    def __init__(self, H: int, W: int, n_slope: Optional[int] = None,
+                 n_intercept: Optional[int] = None, interp="linear"):
+        self.H, self.W = int(H), int(W)
+        self.S = self.W if n_slope is None else int(n_slope)
+        self.Hp = self.H if n_intercept is None else int(n_intercept)
+        self.interp = INTERP_NAMES[interp] if isinstance(interp, str) else int(interp)
+        self.handle = ft_plan_create(self.H, self.W, self.S, self.Hp, self.interp)
+
+    def close(self):
+        if self.handle:
+            ft_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def map_shape(self) -> Tuple[int, int]:
+        return self.Hp, self.S
+
+
+# ------------------------------------------------------------ C-ABI functions
+def ft_plan_create(H: int, W: int, n_slope: int, n_intercept: int, interp: int = FT_INTERP_LINEAR):
+    h = ctypes.c_void_p()
+    _check(lib().ft_plan_create(ctypes.byref(h), int(H), int(W), int(n_slope), int(n_intercept),
+                                int(interp)), "ft_plan_create")
+    return h
+
+
+def ft_plan_destroy(plan) -> None:
+    _check(lib().ft_plan_destroy(plan), "ft_plan_destroy")
+
+
+def ft_forward(plan: Plan, img, out_map, batch: Optional[int] = None, stream=None) -> None:
+    b = img.shape[0] if batch is None else int(batch)
+    ip = _dev_ptr(img, "float32", b * plan.H * plan.W, "img")
+    mp = _dev_ptr(out_map, "float32", b * plan.Hp * plan.S, "map")
+    _check(lib().ft_forward(plan.handle, ip, mp, b, _stream_ptr(stream)), "ft_forward")
+
+
+def ft_backward(plan: Plan, grad_map, grad_img, batch: Optional[int] = None, stream=None) -> None:
+    b = grad_map.shape[0] if batch is None else int(batch)
+    gp = _dev_ptr(grad_map, "float32", b * plan.Hp * plan.S, "grad_map")
+    ip = _dev_ptr(grad_img, "float32", b * plan.H * plan.W, "grad_img")
+    _check(lib().ft_backward(plan.handle, gp, ip, b, _stream_ptr(stream)), "ft_backward")
+
+
+def ft_peaks(plan: Plan, fmap, top_k: int, threshold: float = float("-inf"), out=None, count=None,
+             batch: Optional[int] = None, stream=None):
+    """Returns (peaks, count): peaks a uint8 CUDA tensor holding [batch][top_k]
+    ft_peak records (view with ``peaks_to_numpy``), count an int32 tensor."""
+    import torch
+    b = fmap.shape[0] if batch is None else int(batch)
+    mp = _dev_ptr(fmap, "float32", b * plan.Hp * plan.S, "map")
+    if out is None:
+        out = torch.empty(b * top_k * PEAK_DTYPE.itemsize, dtype=torch.uint8, device=fmap.device)
+    if count is None:
+        count = torch.empty(b, dtype=torch.int32, device=fmap.device)
+    op = _dev_ptr(out, "uint8", b * top_k * PEAK_DTYPE.itemsize, "out")
+    cp = _dev_ptr(count, "int32", b, "count")
+    _check(lib().ft_peaks(plan.handle, mp, b, int(top_k), float(threshold), op, cp,
+                          _stream_ptr(stream)), "ft_peaks")
+    return out, count
+
+
+def peaks_to_numpy(out, count, top_k: int):
+    """Device peak records -> list (per image) of numpy structured arrays."""
+    raw = out.cpu().numpy().view(PEAK_DTYPE).reshape(-1, top_k)
+    cnt = count.cpu().numpy()
+    return [raw[i, :cnt[i]] for i in range(raw.shape[0])]
+
+
+def ft_detect_host(plan: Plan, img_host, top_k: int, threshold: float = float("-inf"),
+                   out_host=None, count_host=None, stream=None):
+    """End-to-end call on host buffers (pinned CPU tensors are fastest)."""
+    import torch
+    if isinstance(img_host, np.ndarray):
+        img_host = torch.from_numpy(np.ascontiguousarray(img_host, dtype=np.float32))
+    if img_host.is_cuda or img_host.dtype != torch.float32 or not img_host.is_contiguous():
+        raise TypeError("img_host must be a contiguous float32 CPU tensor")
+    b = img_host.shape[0]
+    if out_host is None:
+        out_host = torch.empty(b * top_k * PEAK_DTYPE.itemsize, dtype=torch.uint8)
+    if count_host is None:
+        count_host = torch.empty(b, dtype=torch.int32)
+    _check(lib().ft_detect_host(plan.handle, img_host.data_ptr(), b, int(top_k), float(threshold),
+                                out_host.data_ptr(), count_host.data_ptr(), _stream_ptr(stream)),
+           "ft_detect_host")
+    return out_host, count_host
+
+
+def ft_workspace_bytes(plan: Plan, batch: int) -> int:
+    return int(lib().ft_workspace_bytes(plan.handle, int(batch)))
+
+
+def ft_forward_launches(plan: Plan) -> int:
+    return int(lib().ft_forward_launches(plan.handle))
+
+
+def ft_peaks_launches(plan: Plan) -> int:
+    return int(lib().ft_peaks_launches(plan.handle))
+
+
+def ft_profile_enable(plan: Plan, enable: bool = True) -> None:
+    _check(lib().ft_profile_enable(plan.handle, int(bool(enable))), "ft_profile_enable")
+
+
+def ft_profile_read(plan: Plan):
+    """{kernel name: (total ms, launches)} of the launches recorded since the last read."""
+    n = FT_KERNEL_COUNT
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int32 * n)()
+    _check(lib().ft_profile_read(plan.handle, ms, cnt, n), "ft_profile_read")
+    return {ft_kernel_name(i): (float(ms[i]), int(cnt[i])) for i in range(n) if cnt[i]}
+
+
+def ft_kernel_name(kernel_id: int) -> str:
+    return lib().ft_kernel_name(int(kernel_id)).decode()
+
+
+def ft_status_string(status: int) -> str:
+    return lib().ft_status_string(int(status)).decode()
+
+
+def ft_last_error() -> str:
+    return lib().ft_last_error().decode()
+
+
+# ------------------------------------------------------------ autograd wrapper
+def funnel_transform(img, plan: Plan):
+    """Differentiable forward: P = A img through ft_forward / ft_backward."""
+    import torch
+
+    class _Funnel(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, x):
+            x = x.contiguous()
+            out = torch.empty((x.shape[0], plan.Hp, plan.S), dtype=torch.float32, device=x.device)
+            ft_forward(plan, x, out)
+            return out
+
+        @staticmethod
+        def backward(ctx, g):
+            g = g.contiguous()
+            gi = torch.empty((g.shape[0], plan.H, plan.W), dtype=torch.float32, device=g.device)
+            ft_backward(plan, g, gi)
+            return gi
+
+    return _Funnel.apply(img)

@@ -1,0 +1,184 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: relative L2 error <= 1e-5 on every map (FP32 path vs FP64 oracle);
+peak lists computed by both sides from the same FP32 map must be identical
+(index work is exact); peak lists from the FP32 map vs the FP64 map must agree
+on every rank whose margins exceed 2e-5 max|P|.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1904_09409_gb300 import synth
+from tests import _gpu
+from tests._lines import ridge_image
+
+pytestmark = pytest.mark.gpu
+TOL_MAP = 1e-5
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return _gpu.torch_cuda()
+
+
+def make_plan(H, W, S, Hp, interp="linear"):
+    from paper_1904_09409_gb300 import funnel as f
+    return f.Plan(H, W, S, Hp, interp)
+
+
+def inputs(H, W, n, seed):
+    rng = np.random.default_rng(seed)
+    out = np.empty((n, H, W), np.float32)
+    for i in range(n):
+        if i % 3 == 0:
+            out[i] = rng.standard_normal((H, W))                       # white noise
+        else:
+            out[i] = synth.mixed_image(synth.WL_BATCH_1024, 1000 + seed * 10 + i, H, W).img
+    return out
+
+
+FORWARD_CASES = [
+    # H, W, S, H'           what it covers
+    (2, 2, 2, 2),          # smallest transform (radix 2 only)
+    (1, 2, 2, 4),          # one image row, expansion
+    (6, 4, 6, 6),          # radix 3 x 2, tiny
+    (32, 32, 32, 32),
+    (64, 64, 64, 64),      # several column blocks, radix 8 x 8
+    (48, 40, 64, 72),      # ragged: H < H', W < S, H' = 8 * 9 (radix 3 stages)
+    (100, 96, 96, 192),    # odd expansion split, 192 = 64 * 3
+    (128, 96, 192, 144),   # zero insertion S = 2 W, 144 = 16 * 9
+    (256, 256, 256, 256),  # the single-image workload size
+    (384, 384, 384, 384),
+    (200, 300, 384, 512),  # W not a multiple of the column block
+    (768, 768, 768, 768),
+    (64, 16, 16, 8192),    # longest column transform
+    (8, 16, 8192, 8),      # longest row transform
+]
+
+
+@pytest.mark.parametrize("H,W,S,Hp", FORWARD_CASES)
+def test_forward_matches_oracle(torch, H, W, S, Hp):
+    n = 3 if H * W <= 256 * 256 else 2
+    imgs = inputs(H, W, n, seed=H * 7 + W)
+    with make_plan(H, W, S, Hp) as plan:
+        got = _gpu.forward(plan, imgs)
+    for i in range(n):
+        ref = oracle.funnel_ref(imgs[i], S, Hp)
+        assert np.all(np.isfinite(got[i]))
+        err = _gpu.rel_l2(got[i], ref)
+        assert err <= TOL_MAP, (i, err)
+
+
+@pytest.mark.parametrize("H,W,S,Hp", [(32, 32, 32, 32), (48, 40, 64, 72), (256, 256, 256, 256),
+                                      (128, 96, 192, 144)])
+def test_forward_cubic_matches_oracle(torch, H, W, S, Hp):
+    imgs = inputs(H, W, 2, seed=99)
+    with make_plan(H, W, S, Hp, "cubic") as plan:
+        got = _gpu.forward(plan, imgs)
+    for i in range(2):
+        assert _gpu.rel_l2(got[i], oracle.funnel_ref(imgs[i], S, Hp, "cubic")) <= TOL_MAP
+
+
+def test_line_peaks_where_eqs_22_23_say(torch):
+    H = W = S = 128
+    Hp = 256
+    lines = [(0.5, 20.0), (-0.25, -40.0), (0.875, 5.0)]
+    img = ridge_image(H, W, Hp, lines)[None].astype(np.float32)
+    with make_plan(H, W, S, Hp) as plan:
+        m = _gpu.forward(plan, img)
+        pk, recs = _gpu.peaks(plan, m, 3)
+    got = sorted((round(float(r["k"]), 4), float(r["b"])) for r in recs[0])
+    exp = sorted(lines)
+    for (k, b), (ke, be) in zip(got, exp):
+        assert abs(k - ke) <= 2.0 / S + 1e-6 and abs(b - be) <= 1.0
+
+
+def test_batch_zero_is_a_noop(torch):
+    from paper_1904_09409_gb300 import funnel as f
+    with make_plan(16, 16, 16, 16) as plan:
+        x = torch.zeros((1, 16, 16), device="cuda")
+        m = torch.full((1, 16, 16), 7.0, device="cuda")
+        f.ft_forward(plan, x, m, batch=0)
+        torch.cuda.synchronize()
+        assert bool((m == 7.0).all())
+
+
+def test_linearity_on_gpu(torch):
+    H = W = S = Hp = 256
+    a, b = inputs(H, W, 2, seed=5)
+    with make_plan(H, W, S, Hp) as plan:
+        pa, pb, pab = _gpu.forward(plan, np.stack([a, b, 2.0 * a - 0.5 * b]))
+    assert _gpu.rel_l2(pab, 2.0 * pa.astype(np.float64) - 0.5 * pb) <= 2e-6
+
+
+def test_full_size_batch_sampled(torch):
+    """The benchmark's workload in its launch configuration (64 x 1024^2 in one
+    call), checked on sampled images against the full oracle map and its peaks."""
+    imgs = synth.batch_1024(64)
+    with make_plan(1024, 1024, 1024, 1024) as plan:
+        got = _gpu.forward(plan, imgs)
+        pk, _ = _gpu.peaks(plan, got, 32)
+    for i in (0, 17, 63):
+        ref = oracle.funnel_ref(imgs[i], 1024, 1024)
+        assert _gpu.rel_l2(got[i], ref) <= TOL_MAP, i
+        # peaks of the same FP32 map: identical
+        assert pk[i] == oracle.peaks_ref(np.abs(got[i]).astype(np.float64), 32)
+        # peaks of the FP64 map: identical wherever the ranking is unambiguous
+        ref_pk = oracle.peaks_ref(np.abs(ref), 32)
+        tol = 2e-5 * np.abs(ref).max()
+        assert not _gpu.robust_rank_mismatches(ref, ref_pk, pk[i], tol), i
+
+
+# ------------------------------------------------------------------- peaks
+@pytest.mark.parametrize("Hp,S", [(2, 2), (4, 6), (8, 8), (48, 72), (64, 128), (96, 216)])
+@pytest.mark.parametrize("K", [1, 5, 64])
+def test_peaks_exact_with_ties(torch, Hp, S, K):
+    rng = np.random.default_rng(Hp * 1000 + S + K)
+    maps = rng.integers(-3, 4, size=(3, Hp, S)).astype(np.float32)   # many equal |values|
+    with make_plan(Hp, S, S, Hp) as plan:
+        for thr in (float("-inf"), 2.0):
+            got, _ = _gpu.peaks(plan, maps, K, thr)
+            for i in range(3):
+                ref = oracle.peaks_ref(np.abs(maps[i]).astype(np.float64), K, thr)
+                assert got[i] == ref, (i, thr)
+
+
+@pytest.mark.parametrize("K", [32, 513, 1024])
+def test_peaks_exact_large_k(torch, K):
+    rng = np.random.default_rng(K)
+    maps = rng.standard_normal((2, 256, 192)).astype(np.float32)
+    with make_plan(256, 192, 192, 256) as plan:
+        got, _ = _gpu.peaks(plan, maps, K)
+    for i in range(2):
+        ref = oracle.peaks_ref(np.abs(maps[i]).astype(np.float64), K)
+        assert got[i] == ref
+
+
+def test_peaks_fewer_than_k(torch):
+    maps = np.zeros((1, 16, 16), np.float32)
+    maps[0, 3, 4] = 5.0
+    maps[0, 10, 12] = -4.0
+    with make_plan(16, 16, 16, 16) as plan:
+        got, recs = _gpu.peaks(plan, maps, 10, threshold=1.0)
+    assert got[0] == [(3, 4, 5.0), (10, 12, 4.0)]
+    assert recs[0]["k"][0] == np.float32(2.0 * (4 - 8) / 16) and recs[0]["b"][0] == 3 - 8
+
+
+# ----------------------------------------------------------------- adjoint
+@pytest.mark.parametrize("H,W,S,Hp,interp", [(32, 32, 32, 32, "linear"), (48, 40, 64, 72, "linear"),
+                                             (48, 40, 64, 72, "cubic"), (256, 256, 256, 256, "linear"),
+                                             (100, 96, 96, 192, "cubic")])
+def test_backward_matches_oracle_adjoint(torch, H, W, S, Hp, interp):
+    rng = np.random.default_rng(H + W)
+    g = rng.standard_normal((2, Hp, S)).astype(np.float32)
+    x = rng.standard_normal((2, H, W)).astype(np.float32)
+    with make_plan(H, W, S, Hp, interp) as plan:
+        gi = _gpu.backward(plan, g)
+        px = _gpu.forward(plan, x)
+    for i in range(2):
+        ref = oracle.adjoint_ref(g[i].astype(np.float64), H, W, interp)
+        assert _gpu.rel_l2(gi[i], ref) <= TOL_MAP
+        lhs = float(np.sum(px[i].astype(np.float64) * g[i]))
+        rhs = float(np.sum(x[i].astype(np.float64) * gi[i]))
+        assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(px[i]) * np.linalg.norm(g[i])
