@@ -117,6 +117,32 @@ ft_status ft_peaks(ft_plan plan, const float* d_map, int batch, int top_k, float
 ft_status ft_detect_host(ft_plan plan, const float* h_img, int batch, int top_k, float threshold,
                          ft_peak* h_out, int32_t* h_count, void* stream);
 
+/* Peak detection without any device allocation.
+ *
+ * The paper has no counterpart to this call; it exists for callers that cannot
+ * allocate device memory when they detect peaks: code recording work into a
+ * CUDA graph by stream capture (allocation cannot be captured), services that
+ * reserve their device memory at start-up and allocate nothing afterwards, and
+ * hosts whose device memory belongs to another allocator.
+ *
+ * Same result as ft_peaks on |d_map| ([batch][n_intercept][n_slope], FP32),
+ * written to d_out ([batch][top_k]) and d_count ([batch]), but no plan is
+ * needed and nothing is allocated: the per-tile keys go to one fixed array of
+ * FT_NOALLOC_SCRATCH_BYTES bytes inside the library, which every GPU that loads
+ * libfunnel.so holds until the process exits.  A call whose keys would not fit
+ * (about batch x ceil(n_intercept/32) x ceil(n_slope/64) x min(top_k, 512) x 8
+ * bytes; 64 maps of 1024 x 1024 with top_k = 32 use 8 MiB) returns
+ * FT_ERR_UNSUPPORTED_SIZE and ft_last_error() says why.
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, under a lock); make that first call before any stream capture.  All
+ * calls share the one array, so calls whose work overlaps on the GPU (other
+ * streams, other threads) race on it; calls in order on one stream are safe.
+ * n_intercept, n_slope >= 2; 1 <= top_k <= FT_MAX_TOPK. */
+#define FT_NOALLOC_SCRATCH_BYTES (16u << 20)
+ft_status ft_peaks_noalloc(const float* d_map, int n_intercept, int n_slope, int batch, int top_k,
+                           float threshold, ft_peak* d_out, int32_t* d_count, void* stream);
+
 /* Bytes of plan-owned device workspace that a call with this batch needs. */
 size_t ft_workspace_bytes(ft_plan plan, int batch);
 
@@ -147,7 +173,8 @@ const char* ft_kernel_name(int id);
 /* Static text for a status; never NULL. */
 const char* ft_status_string(ft_status status);
 
-/* Text of the last CUDA error seen by any call in this thread ("" if none). */
+/* Text of the last error recorded by a call in this thread: the CUDA error of
+ * an FT_ERR_CUDA, or the reason ft_peaks_noalloc rejected a size ("" if none). */
 const char* ft_last_error(void);
 
 #ifdef __cplusplus

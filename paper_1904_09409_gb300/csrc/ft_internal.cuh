@@ -188,6 +188,11 @@ struct ft_plan_s {
     std::vector<int> prof_ids;      // kernel id of each recorded launch (events 2i, 2i+1)
 };
 
+// Record an error text for ft_last_error() in the calling thread and return the
+// status (FT_ERR_CUDA for the CUDA variant).
+ft_status ft_record_cuda(cudaError_t e, const char* where);
+ft_status ft_record_error(ft_status s, const char* text);
+
 // -------------------------------------------------------- kernel launchers
 // All return the cudaError_t of the launch.
 

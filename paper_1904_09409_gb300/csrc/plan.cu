@@ -17,6 +17,13 @@ static ft_status cuda_fail(cudaError_t e, const char* where) {
     return FT_ERR_CUDA;
 }
 
+ft_status ft_record_cuda(cudaError_t e, const char* where) { return cuda_fail(e, where); }
+
+ft_status ft_record_error(ft_status s, const char* text) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s", text);
+    return s;
+}
+
 #define FT_CUDA(call, where)                              \
     do {                                                  \
         cudaError_t e_ = (call);                          \

@@ -32,7 +32,9 @@ EXPORTED = (
     "ft_plan_create", "ft_plan_destroy", "ft_forward", "ft_backward", "ft_peaks",
     "ft_detect_host", "ft_workspace_bytes", "ft_forward_launches", "ft_peaks_launches",
     "ft_status_string", "ft_last_error", "ft_profile_enable", "ft_profile_read", "ft_kernel_name",
+    "ft_peaks_noalloc",
 )
+FT_NOALLOC_SCRATCH_BYTES = 16 << 20
 FT_KERNEL_COUNT = 6
 
 
@@ -82,7 +84,8 @@ def lib() -> ctypes.CDLL:
     L.ft_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32), ci]
     L.ft_kernel_name.argtypes = [ci]
     L.ft_kernel_name.restype = ctypes.c_char_p
-    for name in ("ft_profile_enable", "ft_profile_read", "ft_plan_create", "ft_plan_destroy", "ft_forward", "ft_backward", "ft_peaks",
+    L.ft_peaks_noalloc.argtypes = [vp, ci, ci, ci, ci, cf, vp, vp, vp]
+    for name in ("ft_peaks_noalloc", "ft_profile_enable", "ft_profile_read", "ft_plan_create", "ft_plan_destroy", "ft_forward", "ft_backward", "ft_peaks",
                  "ft_detect_host", "ft_forward_launches", "ft_peaks_launches"):
         getattr(L, name).restype = ci
     _lib = L
@@ -191,6 +194,28 @@ def ft_peaks(plan: Plan, fmap, top_k: int, threshold: float = float("-inf"), out
     cp = _dev_ptr(count, "int32", b, "count")
     _check(lib().ft_peaks(plan.handle, mp, b, int(top_k), float(threshold), op, cp,
                           _stream_ptr(stream)), "ft_peaks")
+    return out, count
+
+
+def ft_peaks_noalloc(fmap, top_k: int, threshold: float = float("-inf"), out=None, count=None,
+                     stream=None):
+    """ft_peaks without a plan and without any device allocation inside the
+    library (fixed scratch of FT_NOALLOC_SCRATCH_BYTES).  fmap: (batch, H', S)
+    CUDA float32.  Returns (peaks, count) like ft_peaks; pass preallocated
+    ``out``/``count`` to avoid allocations on the Python side too."""
+    import torch
+    b, Hp, S = (int(v) for v in fmap.shape)
+    mp = _dev_ptr(fmap, "float32", b * Hp * S, "map")
+    if out is None:
+        out = torch.empty(b * top_k * PEAK_DTYPE.itemsize, dtype=torch.uint8, device=fmap.device)
+    if count is None:
+        count = torch.empty(b, dtype=torch.int32, device=fmap.device)
+    op = _dev_ptr(out, "uint8", b * top_k * PEAK_DTYPE.itemsize, "out")
+    cp = _dev_ptr(count, "int32", b, "count")
+    st = lib().ft_peaks_noalloc(mp, Hp, S, b, int(top_k), float(threshold), op, cp, _stream_ptr(stream))
+    if st == FT_ERR_UNSUPPORTED_SIZE:
+        raise FunnelError(st, "ft_peaks_noalloc", ft_last_error())
+    _check(st, "ft_peaks_noalloc")
     return out, count
 
 
