@@ -1,0 +1,190 @@
+// Register-resident Stockham FFT with compile-time schedules.
+//
+// For the lengths below every thread of a transform holds E elements (16, or 12
+// when N has a factor 3) in registers; a transform of length N uses T = N / E
+// threads, and a block runs B transforms side by side (transform f's sample n
+// lives at smem[spos(n) * B + f]).  A pass with radix R and P = product of the
+// earlier radices does, for butterfly i in [0, N/R) with k = i mod P:
+//     inputs x[i + q N/R] * w^{q k N/(P R)},  q < R   (w = exp(SIGN 2 pi i / N))
+//     radix-R DFT in registers
+//     outputs y[(i - k) R + k + q P]
+// so the result comes out in natural order (self-sorting).  Each pass costs one
+// shared-memory round trip; the first pass loads and the last pass stores
+// through caller code, which lets the column and row kernels read and write
+// global memory directly.  All index arithmetic is by compile-time constants.
+//
+// Twiddles come from a per-length table (FP64 values rounded to FP32, built on
+// the host): for pass s >= 1, entry [k][q-1] = exp(-2 pi i q k / (P R)).
+#pragma once
+
+#include "ft_internal.cuh"
+
+__host__ __device__ constexpr bool fs_has(int N) {
+    return N == 128 || N == 256 || N == 512 || N == 1024 || N == 2048 || N == 4096 || N == 8192 ||
+           N == 192 || N == 384 || N == 768 || N == 1536;
+}
+__host__ __device__ constexpr int fs_E(int N) { return N % 3 == 0 ? 12 : 16; }
+__host__ __device__ constexpr int fs_T(int N) { return N / fs_E(N); }
+__host__ __device__ constexpr int fs_nst(int N) {
+    return N == 128 ? 2 : N == 256 ? 2 : N == 512 ? 3 : N == 1024 ? 3 : N == 2048 ? 3 : N == 4096 ? 3
+         : N == 8192 ? 4 : N == 192 ? 4 : N == 384 ? 5 : N == 768 ? 5 : N == 1536 ? 6 : 0;
+}
+__host__ __device__ constexpr int fs_radix(int N, int s) {
+    return N == 128 ? (s == 0 ? 16 : 8)
+         : N == 256 ? 16
+         : N == 512 ? (s == 0 ? 16 : s == 1 ? 8 : 4)
+         : N == 1024 ? (s < 2 ? 16 : 4)
+         : N == 2048 ? (s < 2 ? 16 : 8)
+         : N == 4096 ? 16
+         : N == 8192 ? (s < 3 ? 16 : 2)
+         : N == 192 ? (s < 3 ? 4 : 3)
+         : N == 384 ? (s < 3 ? 4 : s == 3 ? 2 : 3)
+         : N == 768 ? (s < 4 ? 4 : 3)
+         : N == 1536 ? (s < 4 ? 4 : s == 4 ? 2 : 3)
+         : 0;
+}
+__host__ __device__ constexpr int fs_P(int N, int s) {
+    int p = 1;
+    for (int j = 0; j < s; ++j) p *= fs_radix(N, j);
+    return p;
+}
+__host__ __device__ constexpr int fs_twoff(int N, int s) {
+    int o = 0;
+    for (int j = 1; j < s; ++j) o += fs_P(N, j) * (fs_radix(N, j) - 1);
+    return o;
+}
+__host__ __device__ constexpr int fs_twsize(int N) { return fs_twoff(N, fs_nst(N)); }
+// transforms per block for the column kernels (512 threads) and the row kernels (256)
+__host__ __device__ constexpr int fs_clampB(int v, int hi) { return v < 1 ? 1 : (v > hi ? hi : v); }
+__host__ __device__ constexpr int fs_Bcol(int N) { return fs_clampB(512 / fs_T(N), 32); }
+__host__ __device__ constexpr int fs_Brow(int N) { return fs_clampB(256 / fs_T(N), 16); }
+// padded shared-memory slot of sample n (one spare slot every 16 samples
+// spreads the strided stores of the first pass over the banks)
+__host__ __device__ constexpr int spos(int n) { return n + (n >> 4); }
+__host__ __device__ constexpr int fs_slots(int N) { return spos(N - 1) + 1; }
+
+template <int SIGN>
+__device__ __forceinline__ float2 tw_sign(float2 w) { return SIGN > 0 ? make_float2(w.x, -w.y) : w; }
+
+// radix-16 as 4 x 4 with the internal twiddles exp(SIGN 2 pi i m / 16)
+template <int SIGN>
+struct Dft<16, SIGN> {
+    __device__ __forceinline__ static void run(float2* u) {
+        const float c1 = 0.92387953251128675613f;   // cos(pi/8)
+        const float s1 = 0.38268343236508977173f;   // sin(pi/8)
+        const float r = 0.70710678118654752440f;    // sqrt(2)/2
+        float2 a[4][4];
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) {
+            float2 t[4] = {u[n2], u[4 + n2], u[8 + n2], u[12 + n2]};
+            Dft<4, SIGN>::run(t);
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1) a[n2][k1] = t[k1];
+        }
+        const float2 w1 = make_float2(c1, SIGN * s1), w2 = make_float2(r, SIGN * r);
+        const float2 w3 = make_float2(s1, SIGN * c1), w6 = make_float2(-r, SIGN * r);
+        const float2 w9 = make_float2(-c1, -SIGN * s1);
+        a[1][1] = cmul(a[1][1], w1);
+        a[1][2] = cmul(a[1][2], w2);
+        a[1][3] = cmul(a[1][3], w3);
+        a[2][1] = cmul(a[2][1], w2);
+        a[2][2] = cmul_si<SIGN>(a[2][2]);
+        a[2][3] = cmul(a[2][3], w6);
+        a[3][1] = cmul(a[3][1], w3);
+        a[3][2] = cmul(a[3][2], w6);
+        a[3][3] = cmul(a[3][3], w9);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            float2 t[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+            Dft<4, SIGN>::run(t);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) u[k1 + 4 * k2] = t[k2];
+        }
+    }
+};
+
+template <int N, int SIGN, int B>
+struct FastFft {
+    static constexpr int E = fs_E(N);
+    static constexpr int T = N / E;
+    static constexpr int NS = fs_nst(N);
+    static constexpr int SLOTS = fs_slots(N) * B;      // float2 slots of shared memory
+
+    // sample index of element (m, q) of pass s for thread t of a transform
+    template <int s>
+    __device__ __forceinline__ static int in_pos(int t, int m, int q) {
+        return t + m * T + q * (N / fs_radix(N, s));
+    }
+    // sample index of output element (m, q) of the last pass
+    __device__ __forceinline__ static int out_pos(int t, int m, int q) {
+        return t + m * T + q * (N / fs_radix(N, NS - 1));
+    }
+
+    template <int s>
+    __device__ __forceinline__ static void compute(float2 (&v)[E], int t, const float2* __restrict__ stw) {
+        constexpr int R = fs_radix(N, s), P = fs_P(N, s), G = E / R;
+#pragma unroll
+        for (int m = 0; m < G; ++m) {
+            if constexpr (P > 1) {
+                const int k = (t + m * T) % P;
+                const float2* w = stw + fs_twoff(N, s) + k * (R - 1);
+#pragma unroll
+                for (int q = 1; q < R; ++q) v[m * R + q] = cmul(v[m * R + q], tw_sign<SIGN>(__ldg(w + q - 1)));
+            }
+            Dft<R, SIGN>::run(&v[m * R]);
+        }
+    }
+
+    template <int s>
+    __device__ __forceinline__ static void store(const float2 (&v)[E], float2* sm, int t, int f) {
+        constexpr int R = fs_radix(N, s), P = fs_P(N, s), G = E / R;
+#pragma unroll
+        for (int m = 0; m < G; ++m) {
+            const int i = t + m * T;
+            const int k = i % P;
+            const int j = (i - k) * R + k;
+#pragma unroll
+            for (int q = 0; q < R; ++q) sm[spos(j + q * P) * B + f] = v[m * R + q];
+        }
+    }
+
+    template <int s>
+    __device__ __forceinline__ static void load(float2 (&v)[E], const float2* sm, int t, int f) {
+        constexpr int R = fs_radix(N, s), G = E / R;
+#pragma unroll
+        for (int m = 0; m < G; ++m)
+#pragma unroll
+            for (int q = 0; q < R; ++q) v[m * R + q] = sm[spos(in_pos<s>(t, m, q)) * B + f];
+    }
+
+    // Passes s .. NS-1.  On entry v holds the inputs of pass s in (m, q) order;
+    // on return it holds the outputs of the last pass, element (m, q) being the
+    // sample out_pos(t, m, q).  Every thread of the block must call it; it leaves
+    // shared memory free to reuse (the last barrier follows the last read).
+    template <int s>
+    __device__ __forceinline__ static void run(float2 (&v)[E], float2* sm, int t, int f,
+                                               const float2* __restrict__ stw) {
+        compute<s>(v, t, stw);
+        if constexpr (s + 1 < NS) {
+            store<s>(v, sm, t, f);
+            __syncthreads();
+            load<s + 1>(v, sm, t, f);
+            __syncthreads();
+            run<s + 1>(v, sm, t, f, stw);
+        }
+    }
+};
+
+// launchers of the fixed-length kernels (k_fast.cu); they return
+// cudaErrorNotSupported when N has no schedule
+cudaError_t launch_col_r2c_fast(const float* in, int rows_in, int ncols, int in_pitch, size_t in_img,
+                                int row0, const FftLen& f, float2* out, int out_pitch, size_t out_img,
+                                float end_scale, float mid_scale, int batch, cudaStream_t st);
+cudaError_t launch_col_c2r_fast(const float2* in, int ncols, int in_pitch, size_t in_img,
+                                const FftLen& f, float mid_scale, float* out, int row0, int rows_out,
+                                int out_pitch, size_t out_img, float out_scale, int batch,
+                                cudaStream_t st);
+cudaError_t launch_nvmt_rows_fast(float2* ws, int W, int Hp, int L, int interp, const FftLen& fx,
+                                  int batch, cudaStream_t st);
+cudaError_t launch_nvmt_rows_adjoint_fast(float2* ws, int W, int Hp, int L, int interp,
+                                          const FftLen& fx, int batch, cudaStream_t st);

@@ -20,6 +20,7 @@ struct FftLen {
     int nst;
     int radix[FT_MAX_STAGES];
     const float2* tw;
+    const float2* stw;      // per-pass twiddles of the fixed-length kernels (NULL: generic path)
 };
 
 // ------------------------------------------------------------ complex helpers
@@ -41,6 +42,32 @@ template <int SIGN>
 __device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int t) {
     float2 w = __ldg(tw + t);
     return SIGN > 0 ? make_float2(w.x, -w.y) : w;
+}
+
+// ----------------------------------------------------- NVMT index helpers
+__device__ __forceinline__ int floor_div(int a, int b) {   // b > 0
+    int q = a / b;
+    return (a % b != 0 && a < 0) ? q - 1 : q;
+}
+__device__ __forceinline__ int ceil_div(int a, int b) {    // b > 0
+    int q = a / b;
+    return (a % b != 0 && a > 0) ? q + 1 : q;
+}
+
+// Keys' cubic convolution kernel with a = -0.5.
+__device__ __forceinline__ float keys_w(float s) {
+    const float a = -0.5f;
+    s = fabsf(s);
+    if (s <= 1.f) return ((a + 2.f) * s - (a + 3.f)) * s * s + 1.f;
+    if (s < 2.f) return ((a * s - 5.f * a) * s + 8.f * a) * s - 4.f * a;
+    return 0.f;
+}
+
+// Weight of tap offset d (tap = floor + d) at fraction fr: linear uses d = 0, 1;
+// cubic d = -1 .. 2.
+__device__ __forceinline__ float tap_weight(int interp, int d, float fr) {
+    if (interp == FT_INTERP_LINEAR) return d == 0 ? 1.f - fr : fr;
+    return keys_w(fr - (float)d);
 }
 
 // ---------------------------------------------------------- radix-R kernels

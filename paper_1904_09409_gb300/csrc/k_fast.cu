@@ -1,0 +1,349 @@
+// Fixed-length versions of the column and row kernels (see k_cols.cu and
+// k_rows.cu for what each step computes) built on the register-resident FFT of
+// fft_fast.cuh.  Differences from the generic kernels:
+//  * the first FFT pass reads global memory directly (columns: B adjacent
+//    column pairs per row segment; C2R: the Hermitian half, mirrored on the fly;
+//    rows: the NVMT gather feeds the registers) and the last pass writes global
+//    memory directly where the output order allows it;
+//  * the NVMT sample x' H' / (2 l) of successive elements of a thread is stepped
+//    exactly by adding the precomputed quotient and remainder of
+//    (N / R0) H' / (2 l), so the inner loop has no integer division;
+//  * the interpolation fraction is remainder * (1 / (2 l)) in FP32 (within one
+//    rounding of the exact fraction).
+#include "fft_fast.cuh"
+
+template <int N>
+__global__ void __launch_bounds__(fs_T(N) * fs_Bcol(N))
+k_col_r2c_fast(const float* __restrict__ in, int rows_in, int ncols, int in_pitch, size_t in_img,
+               int row0, const float2* __restrict__ stw, float2* __restrict__ out, int out_pitch,
+               size_t out_img, float end_scale, float mid_scale) {
+    constexpr int B = fs_Bcol(N), E = fs_E(N), T = N / E;
+    constexpr int R0 = fs_radix(N, 0), G0 = E / R0;
+    constexpr int RL = fs_radix(N, fs_nst(N) - 1), GL = E / RL;
+    using F = FastFft<N, -1, B>;
+    extern __shared__ float2 sm[];
+    const int f = threadIdx.x % B;
+    const int t = threadIdx.x / B;
+    const int c = blockIdx.x * 2 * B + 2 * f;
+    const bool colok = c < ncols;
+    const float* src = in + (size_t)blockIdx.y * in_img + c;
+
+    float2 v[E];
+#pragma unroll
+    for (int m = 0; m < G0; ++m)
+#pragma unroll
+        for (int q = 0; q < R0; ++q) {
+            const int row = F::template in_pos<0>(t, m, q) - row0;
+            float2 x = make_float2(0.f, 0.f);
+            if (colok && row >= 0 && row < rows_in)
+                x = __ldg(reinterpret_cast<const float2*>(src + (size_t)row * in_pitch));
+            v[m * R0 + q] = x;
+        }
+    F::template run<0>(v, sm, t, f, stw);
+#pragma unroll
+    for (int m = 0; m < GL; ++m)
+#pragma unroll
+        for (int q = 0; q < RL; ++q) sm[spos(F::out_pos(t, m, q)) * B + f] = v[m * RL + q];
+    __syncthreads();
+
+    float2* dst = out + (size_t)blockIdx.y * out_img + c;
+    if (!colok) return;
+    for (int l = t; l <= N / 2; l += T) {
+        const float2 zl = sm[spos(l) * B + f];
+        const float2 zm = sm[spos(l == 0 ? 0 : N - l) * B + f];
+        const float s = (l == 0 || l == N / 2) ? end_scale : mid_scale;
+        float4 o;
+        o.x = 0.5f * s * (zl.x + zm.x);
+        o.y = 0.5f * s * (zl.y - zm.y);
+        o.z = 0.5f * s * (zl.y + zm.y);
+        o.w = -0.5f * s * (zl.x - zm.x);
+        *reinterpret_cast<float4*>(dst + (size_t)l * out_pitch) = o;
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(fs_T(N) * fs_Bcol(N))
+k_col_c2r_fast(const float2* __restrict__ in, int ncols, int in_pitch, size_t in_img,
+               const float2* __restrict__ stw, float mid_scale, float* __restrict__ out, int row0,
+               int rows_out, int out_pitch, size_t out_img, float out_scale) {
+    constexpr int B = fs_Bcol(N), E = fs_E(N);
+    constexpr int R0 = fs_radix(N, 0), G0 = E / R0;
+    constexpr int RL = fs_radix(N, fs_nst(N) - 1), GL = E / RL;
+    using F = FastFft<N, +1, B>;
+    extern __shared__ float2 sm[];
+    const int f = threadIdx.x % B;
+    const int t = threadIdx.x / B;
+    const int c = blockIdx.x * 2 * B + 2 * f;
+    const bool colok = c < ncols;
+    const float2* src = in + (size_t)blockIdx.y * in_img + c;
+
+    float2 v[E];
+#pragma unroll
+    for (int m = 0; m < G0; ++m)
+#pragma unroll
+        for (int q = 0; q < R0; ++q) {
+            const int n = F::template in_pos<0>(t, m, q);
+            const int r = n <= N / 2 ? n : N - n;
+            float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (colok) g = __ldg(reinterpret_cast<const float4*>(src + (size_t)r * in_pitch));
+            float2 z;
+            if (r == 0 || r == N / 2) {
+                z = make_float2(g.x, g.z);                               // Re A + i Re B
+            } else {
+                g.x *= mid_scale; g.y *= mid_scale; g.z *= mid_scale; g.w *= mid_scale;
+                z = (n <= N / 2) ? make_float2(g.x - g.w, g.y + g.z)      // A + i B
+                                 : make_float2(g.x + g.w, g.z - g.y);     // conj A + i conj B
+            }
+            v[m * R0 + q] = z;
+        }
+    F::template run<0>(v, sm, t, f, stw);
+    if (!colok) return;
+    float* dst = out + (size_t)blockIdx.y * out_img + c;
+#pragma unroll
+    for (int m = 0; m < GL; ++m)
+#pragma unroll
+        for (int q = 0; q < RL; ++q) {
+            const int rr = F::out_pos(t, m, q) - row0;
+            if (rr >= 0 && rr < rows_out)
+                *reinterpret_cast<float2*>(dst + (size_t)rr * out_pitch) =
+                    make_float2(v[m * RL + q].x * out_scale, v[m * RL + q].y * out_scale);
+        }
+}
+
+template <int N>
+__global__ void __launch_bounds__(fs_T(N) * fs_Brow(N))
+k_nvmt_rows_fast(float2* __restrict__ ws, int W, int Hp, int L, int interp,
+                 const float2* __restrict__ stw) {
+    constexpr int B = fs_Brow(N), E = fs_E(N), T = N / E;
+    constexpr int R0 = fs_radix(N, 0), G0 = E / R0;
+    constexpr int RL = fs_radix(N, fs_nst(N) - 1), GL = E / RL;
+    constexpr int STEPX = N / R0;                      // x' distance between a thread's elements
+    using F = FastFft<N, +1, B>;
+    extern __shared__ float2 sm[];
+    float2* srow = sm + F::SLOTS;                      // [W][B] input rows
+    const int f = threadIdx.x % B;
+    const int t = threadIdx.x / B;
+    const int l0 = blockIdx.x * B;
+    const int l = l0 + f;
+    float2* base = ws + (size_t)blockIdx.y * L * N;
+
+    for (int idx = threadIdx.x; idx < W * B; idx += blockDim.x) {
+        const int r = idx % B;
+        const int x = idx / B;
+        srow[idx] = (l0 + r < L) ? base[(size_t)(l0 + r) * N + x] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+
+    float2 v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = make_float2(0.f, 0.f);
+    if (l >= 1 && l < L) {
+        const int den = 2 * l;
+        const float inv = 1.f / (float)den;
+        const int step = STEPX * Hp;
+        const int sA = step / den, sB = step - sA * den;
+        const int halfW = W >> 1;
+        const int dlo = interp == FT_INTERP_LINEAR ? 0 : -1;
+        const int dhi = interp == FT_INTERP_LINEAR ? 1 : 2;
+#pragma unroll
+        for (int m = 0; m < G0; ++m) {
+            const int i = t + m * T;
+            const int num = (i - N / 2) * Hp;
+            int qf = floor_div(num, den);
+            int rem = num - qf * den;
+#pragma unroll
+            for (int q = 0; q < R0; ++q) {
+                const float fr = (float)rem * inv;
+                float2 acc = make_float2(0.f, 0.f);
+                for (int d = dlo; d <= dhi; ++d) {
+                    const int col = qf + d + halfW;
+                    if (col >= 0 && col < W) {
+                        const float w = tap_weight(interp, d, fr);
+                        const float2 s = srow[col * B + f];
+                        acc.x += w * s.x;
+                        acc.y += w * s.y;
+                    }
+                }
+                if ((i + q * STEPX) & 1) acc = make_float2(-acc.x, -acc.y);
+                v[m * R0 + q] = acc;
+                rem += sB;
+                qf += sA;
+                if (rem >= den) { rem -= den; qf += 1; }
+            }
+        }
+    }
+    F::template run<0>(v, sm, t, f, stw);
+    if (l >= L) return;
+    float2* row = base + (size_t)l * N;
+#pragma unroll
+    for (int m = 0; m < GL; ++m)
+#pragma unroll
+        for (int q = 0; q < RL; ++q) {
+            const int s = F::out_pos(t, m, q);
+            float2 val = v[m * RL + q];
+            if ((s + N / 2) & 1) val = make_float2(-val.x, -val.y);
+            row[s] = val;
+        }
+}
+
+template <int N>
+__global__ void __launch_bounds__(fs_T(N) * fs_Brow(N))
+k_nvmt_rows_adjoint_fast(float2* __restrict__ ws, int W, int Hp, int L, int interp,
+                         const float2* __restrict__ stw) {
+    constexpr int B = fs_Brow(N), E = fs_E(N), T = N / E;
+    constexpr int R0 = fs_radix(N, 0), G0 = E / R0;
+    constexpr int RL = fs_radix(N, fs_nst(N) - 1), GL = E / RL;
+    using F = FastFft<N, -1, B>;
+    extern __shared__ float2 sm[];
+    const int f = threadIdx.x % B;
+    const int t = threadIdx.x / B;
+    const int l = blockIdx.x * B + f;
+    float2* row = ws + (size_t)blockIdx.y * L * N + (size_t)l * N;
+
+    float2 v[E];
+#pragma unroll
+    for (int m = 0; m < G0; ++m)
+#pragma unroll
+        for (int q = 0; q < R0; ++q) {
+            const int s = F::template in_pos<0>(t, m, q);
+            float2 g = (l < L) ? row[s] : make_float2(0.f, 0.f);
+            if (s & 1) g = make_float2(-g.x, -g.y);
+            v[m * R0 + q] = g;
+        }
+    F::template run<0>(v, sm, t, f, stw);
+    // gV[x'] = (-1)^{i + N/2} z[i], i = x' + N/2
+#pragma unroll
+    for (int m = 0; m < GL; ++m)
+#pragma unroll
+        for (int q = 0; q < RL; ++q) {
+            const int i = F::out_pos(t, m, q);
+            float2 z = v[m * RL + q];
+            if ((i + N / 2) & 1) z = make_float2(-z.x, -z.y);
+            sm[spos(i) * B + f] = z;
+        }
+    __syncthreads();
+    if (l >= L) return;
+    const int halfW = W >> 1;
+    const int dlo = interp == FT_INTERP_LINEAR ? 0 : -1;
+    const int dhi = interp == FT_INTERP_LINEAR ? 1 : 2;
+    const int den = 2 * l;
+    const float inv = 1.f / (float)den;
+    for (int x = t; x < W; x += T) {
+        float2 acc = make_float2(0.f, 0.f);
+        if (l >= 1) {
+            const int xc = x - halfW;
+            for (int d = dlo; d <= dhi; ++d) {
+                // the sample x' whose floor(x' H' / (2 l)) equals xc - d, if any
+                const int q = xc - d;
+                const int xp = ceil_div(q * den, Hp);
+                const int num = xp * Hp;
+                if (num >= (q + 1) * den || xp < -N / 2 || xp >= N / 2) continue;
+                const float w = tap_weight(interp, d, (float)(num - q * den) * inv);
+                const float2 g = sm[spos(xp + N / 2) * B + f];
+                acc.x += w * g.x;
+                acc.y += w * g.y;
+            }
+        }
+        row[x] = acc;
+    }
+}
+
+// ------------------------------------------------------------------ dispatch
+#define FT_FAST_LENGTHS(X) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(8192) X(192) X(384) X(768) X(1536)
+
+template <int N>
+static cudaError_t go_r2c(const float* in, int rows_in, int ncols, int in_pitch, size_t in_img, int row0,
+                          const float2* stw, float2* out, int out_pitch, size_t out_img, float es, float ms,
+                          int batch, cudaStream_t st) {
+    constexpr int B = fs_Bcol(N);
+    const size_t sm = (size_t)FastFft<N, -1, B>::SLOTS * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_col_r2c_fast<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid((ncols + 2 * B - 1) / (2 * B), batch);
+    k_col_r2c_fast<N><<<grid, fs_T(N) * B, sm, st>>>(in, rows_in, ncols, in_pitch, in_img, row0, stw, out,
+                                                     out_pitch, out_img, es, ms);
+    return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t go_c2r(const float2* in, int ncols, int in_pitch, size_t in_img, const float2* stw,
+                          float mid, float* out, int row0, int rows_out, int out_pitch, size_t out_img,
+                          float os, int batch, cudaStream_t st) {
+    constexpr int B = fs_Bcol(N);
+    const size_t sm = (size_t)FastFft<N, +1, B>::SLOTS * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_col_c2r_fast<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid((ncols + 2 * B - 1) / (2 * B), batch);
+    k_col_c2r_fast<N><<<grid, fs_T(N) * B, sm, st>>>(in, ncols, in_pitch, in_img, stw, mid, out, row0,
+                                                     rows_out, out_pitch, out_img, os);
+    return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t go_rows(float2* ws, int W, int Hp, int L, int interp, const float2* stw, int batch,
+                           cudaStream_t st) {
+    constexpr int B = fs_Brow(N);
+    const size_t sm = ((size_t)FastFft<N, +1, B>::SLOTS + (size_t)W * B) * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_nvmt_rows_fast<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid((L + B - 1) / B, batch);
+    k_nvmt_rows_fast<N><<<grid, fs_T(N) * B, sm, st>>>(ws, W, Hp, L, interp, stw);
+    return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t go_rows_adj(float2* ws, int W, int Hp, int L, int interp, const float2* stw, int batch,
+                               cudaStream_t st) {
+    constexpr int B = fs_Brow(N);
+    const size_t sm = (size_t)FastFft<N, -1, B>::SLOTS * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_nvmt_rows_adjoint_fast<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid((L + B - 1) / B, batch);
+    k_nvmt_rows_adjoint_fast<N><<<grid, fs_T(N) * B, sm, st>>>(ws, W, Hp, L, interp, stw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_col_r2c_fast(const float* in, int rows_in, int ncols, int in_pitch, size_t in_img,
+                                int row0, const FftLen& f, float2* out, int out_pitch, size_t out_img,
+                                float end_scale, float mid_scale, int batch, cudaStream_t st) {
+    switch (f.N) {
+#define X(n) case n: return go_r2c<n>(in, rows_in, ncols, in_pitch, in_img, row0, f.stw, out, out_pitch, \
+                                      out_img, end_scale, mid_scale, batch, st);
+        FT_FAST_LENGTHS(X)
+#undef X
+    }
+    return cudaErrorNotSupported;
+}
+
+cudaError_t launch_col_c2r_fast(const float2* in, int ncols, int in_pitch, size_t in_img,
+                                const FftLen& f, float mid_scale, float* out, int row0, int rows_out,
+                                int out_pitch, size_t out_img, float out_scale, int batch,
+                                cudaStream_t st) {
+    switch (f.N) {
+#define X(n) case n: return go_c2r<n>(in, ncols, in_pitch, in_img, f.stw, mid_scale, out, row0, rows_out, \
+                                      out_pitch, out_img, out_scale, batch, st);
+        FT_FAST_LENGTHS(X)
+#undef X
+    }
+    return cudaErrorNotSupported;
+}
+
+cudaError_t launch_nvmt_rows_fast(float2* ws, int W, int Hp, int L, int interp, const FftLen& fx,
+                                  int batch, cudaStream_t st) {
+    switch (fx.N) {
+#define X(n) case n: return go_rows<n>(ws, W, Hp, L, interp, fx.stw, batch, st);
+        FT_FAST_LENGTHS(X)
+#undef X
+    }
+    return cudaErrorNotSupported;
+}
+
+cudaError_t launch_nvmt_rows_adjoint_fast(float2* ws, int W, int Hp, int L, int interp,
+                                          const FftLen& fx, int batch, cudaStream_t st) {
+    switch (fx.N) {
+#define X(n) case n: return go_rows_adj<n>(ws, W, Hp, L, interp, fx.stw, batch, st);
+        FT_FAST_LENGTHS(X)
+#undef X
+    }
+    return cudaErrorNotSupported;
+}

@@ -12,15 +12,23 @@
 //
 //  k_peak_tiles   one block per 32 x 64 tile: load the tile with a one-cell halo,
 //                 mark strict local maxima (at most one per 2 x 2 block, so at most
-//                 512 per tile), sort them and keep the best min(top_k, 512).
-//  k_peak_select  one block per image: radix select (8 passes of 8 bits) of the
-//                 top_k-th largest key among the tiles' keys, gather the keys at or
-//                 above it, sort them and write the ft_peak records.
+//                 512 per tile; neighbour indices are computed only to break exact
+//                 ties), and keep the best min(top_k, 512) by radix selection.
+//  k_peak_select  one block per image: radix selection of the top_k keys among
+//                 the tiles' keys, then a bitonic sort of those top_k and the
+//                 ft_peak records.
+//
+// Radix selection (cta_select): MSB-first passes over 8-bit digits of the
+// 64-bit keys; a pass histograms the digit of the keys that share the prefix
+// chosen so far, a warp scan finds the digit where the top_k boundary falls, and
+// the search stops as soon as that digit's bin is taken whole.  Keys are
+// distinct, so the selected set has exactly min(top_k, #keys) elements.
 #include "ft_internal.cuh"
 
 #define PK_TT 32
 #define PK_TS 64
 #define PK_CAND 512
+#define PK_TILE_THREADS 256
 #define PK_SEL_THREADS 1024
 
 typedef unsigned long long u64;
@@ -29,9 +37,10 @@ __device__ __forceinline__ u64 peak_key(float v, unsigned lin) {
     return ((u64)__float_as_uint(v) << 32) | (u64)(0xFFFFFFFFu - lin);
 }
 
-__device__ __forceinline__ int wrap_mod(int a, int n) {
-    int r = a % n;
-    return r < 0 ? r + n : r;
+__device__ __forceinline__ int wrap_into(int a, int n) {
+    if (a < 0) a += n;
+    if (a >= n) a %= n;
+    return a;
 }
 
 // Bitonic sort, descending, of n (power of two) keys in shared memory.
@@ -54,11 +63,88 @@ __device__ void bitonic_desc(u64* v, int n) {
     }
 }
 
-__global__ void __launch_bounds__(256)
+struct SelState {
+    unsigned hist[256];
+    u64 prefix, mask;
+    int remaining;
+    int done;
+    int count;
+};
+
+// Marks the top K non-zero keys of keys[0..n) (any address space): on return
+// every key k != 0 with (k & st.mask) >= st.prefix is selected and there are
+// exactly min(K, #non-zero keys) of them.  Called by the whole block.
+__device__ void cta_select(const u64* keys, int n, int K, SelState& st) {
+    if (threadIdx.x == 0) {
+        st.prefix = 0ull;
+        st.mask = 0ull;
+        st.remaining = K;
+        st.done = 0;
+    }
+    __syncthreads();
+    for (int pass = 0; pass < 8; ++pass) {
+        const int shift = 56 - 8 * pass;
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) st.hist[i] = 0u;
+        __syncthreads();
+        const u64 pf = st.prefix, mk = st.mask;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const u64 key = keys[i];
+            if (key != 0ull && (key & mk) == pf) atomicAdd(&st.hist[(key >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            // lane j owns digits 255-8j .. 248-8j (descending)
+            const int lane = threadIdx.x;
+            unsigned own = 0;
+#pragma unroll
+            for (int b = 0; b < 8; ++b) own += st.hist[255 - 8 * lane - b];
+            unsigned incl = own;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const unsigned rem = (unsigned)st.remaining;
+            const unsigned ballot = __ballot_sync(0xffffffffu, incl >= rem);
+            if (ballot == 0u) {
+                // fewer non-zero keys than K share the prefix: take them all (pass 0 only)
+                if (lane == 0) {
+                    st.done = 1;
+                    st.prefix = 1ull;
+                    st.mask = ~0ull;
+                }
+            } else if (lane == __ffs(ballot) - 1) {
+                unsigned cum = incl - own;
+                int d = 255 - 8 * lane;
+                for (int b = 0; b < 8; ++b, --d) {
+                    const unsigned h = st.hist[d];
+                    if (cum + h >= rem) break;
+                    cum += h;
+                }
+                const unsigned left = rem - cum;
+                const u64 np = st.prefix | ((u64)d << shift);
+                const u64 nm = st.mask | (0xFFull << shift);
+                st.prefix = np;
+                st.mask = nm;
+                st.remaining = (int)left;
+                if (st.hist[d] == left) st.done = 1;       // the whole bin is in
+            }
+        }
+        __syncthreads();
+        if (st.done) break;
+    }
+}
+
+__device__ __forceinline__ bool selected(u64 key, const SelState& st) {
+    return key != 0ull && (key & st.mask) >= st.prefix;
+}
+
+__global__ void __launch_bounds__(PK_TILE_THREADS)
 k_peak_tiles(const float* __restrict__ map, int Hp, int S, int KT, float thr, u64* __restrict__ keys) {
     __shared__ float tile[(PK_TT + 2) * (PK_TS + 2)];
     __shared__ u64 cand[PK_CAND];
     __shared__ int ncand;
+    __shared__ SelState st;
     const int img = blockIdx.z;
     const int t0 = blockIdx.y * PK_TT;
     const int s0 = blockIdx.x * PK_TS;
@@ -66,109 +152,82 @@ k_peak_tiles(const float* __restrict__ map, int Hp, int S, int KT, float thr, u6
 
     for (int idx = threadIdx.x; idx < (PK_TT + 2) * (PK_TS + 2); idx += blockDim.x) {
         const int r = idx / (PK_TS + 2);
-        const int c = idx % (PK_TS + 2);
-        const int t = wrap_mod(t0 + r - 1, Hp);
-        const int s = wrap_mod(s0 + c - 1, S);
-        tile[idx] = fabsf(m[(size_t)t * S + s]);
+        const int c = idx - r * (PK_TS + 2);
+        const int t = wrap_into(t0 + r - 1, Hp);
+        const int s = wrap_into(s0 + c - 1, S);
+        tile[idx] = fabsf(__ldg(m + (size_t)t * S + s));
     }
     if (threadIdx.x == 0) ncand = 0;
     __syncthreads();
 
     for (int idx = threadIdx.x; idx < PK_TT * PK_TS; idx += blockDim.x) {
         const int r = idx / PK_TS;
-        const int c = idx % PK_TS;
+        const int c = idx - r * PK_TS;
         const int t = t0 + r;
         const int s = s0 + c;
         if (t >= Hp || s >= S) continue;
-        const float v = tile[(r + 1) * (PK_TS + 2) + c + 1];
+        const float* cp = tile + (r + 1) * (PK_TS + 2) + c + 1;
+        const float v = *cp;
         if (!(v >= thr)) continue;
         const unsigned lin = (unsigned)t * (unsigned)S + (unsigned)s;
-        const u64 key = peak_key(v, lin);
         bool is_max = true;
 #pragma unroll
         for (int dr = -1; dr <= 1; ++dr) {
 #pragma unroll
             for (int dc = -1; dc <= 1; ++dc) {
                 if (dr == 0 && dc == 0) continue;
-                const unsigned nl = (unsigned)wrap_mod(t + dr, Hp) * (unsigned)S +
-                                    (unsigned)wrap_mod(s + dc, S);
-                if (nl == lin) continue;
-                const float nv = tile[(r + 1 + dr) * (PK_TS + 2) + c + 1 + dc];
-                if (peak_key(nv, nl) > key) is_max = false;
+                const float nv = cp[dr * (PK_TS + 2) + dc];
+                if (nv > v) {
+                    is_max = false;
+                } else if (nv == v) {
+                    // exact tie: the neighbour precedes iff its linear index is smaller
+                    const unsigned nl = (unsigned)wrap_into(t + dr, Hp) * (unsigned)S +
+                                        (unsigned)wrap_into(s + dc, S);
+                    if (nl != lin && nl < lin) is_max = false;
+                }
             }
         }
         if (is_max) {
             const int pos = atomicAdd(&ncand, 1);
-            if (pos < PK_CAND) cand[pos] = key;
+            if (pos < PK_CAND) cand[pos] = peak_key(v, lin);
         }
     }
     __syncthreads();
     const int n = min(ncand, PK_CAND);
-    for (int i = threadIdx.x; i < PK_CAND; i += blockDim.x)
-        if (i >= n) cand[i] = 0ull;
-    __syncthreads();
-    bitonic_desc(cand, PK_CAND);
     u64* out = keys + ((size_t)img * gridDim.y * gridDim.x + (size_t)blockIdx.y * gridDim.x + blockIdx.x) * KT;
-    for (int i = threadIdx.x; i < KT; i += blockDim.x) out[i] = cand[i];
+    if (n <= KT) {
+        for (int i = threadIdx.x; i < KT; i += blockDim.x) out[i] = i < n ? cand[i] : 0ull;
+        return;
+    }
+    cta_select(cand, n, KT, st);
+    if (threadIdx.x == 0) st.count = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const u64 key = cand[i];
+        if (selected(key, st)) out[atomicAdd(&st.count, 1)] = key;
+    }
 }
 
 __global__ void __launch_bounds__(PK_SEL_THREADS)
 k_peak_select(const u64* __restrict__ keys, int n, int K, int Hp, int S, ft_peak* __restrict__ out,
               int32_t* __restrict__ count) {
-    __shared__ unsigned hist[256];
     __shared__ u64 sel[FT_MAX_TOPK];
-    __shared__ u64 prefix, mask;
-    __shared__ int remaining, nsel, all_valid;
-    const int img = blockIdx.x;
-    const u64* kk = keys + (size_t)img * n;
-    if (threadIdx.x == 0) {
-        prefix = 0ull;
-        mask = 0ull;
-        remaining = K;
-        all_valid = 0;
-        nsel = 0;
-    }
+    __shared__ SelState st;
+    const u64* kk = keys + (size_t)blockIdx.x * n;
+    cta_select(kk, n, K, st);
+    if (threadIdx.x == 0) st.count = 0;
     __syncthreads();
-    for (int pass = 0; pass < 8; ++pass) {
-        const int shift = 56 - 8 * pass;
-        for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0u;
-        __syncthreads();
-        const u64 pf = prefix, mk = mask;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const u64 key = kk[i];
-            if (key != 0ull && (key & mk) == pf) atomicAdd(&hist[(key >> shift) & 255u], 1u);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned cum = 0;
-            int d = -1;
-            for (int dd = 255; dd >= 0; --dd) {
-                if (cum + hist[dd] >= (unsigned)remaining) { d = dd; break; }
-                cum += hist[dd];
-            }
-            if (d < 0) {
-                all_valid = 1;                      // fewer than K valid keys
-            } else {
-                remaining -= (int)cum;
-                prefix |= (u64)d << shift;
-                mask |= 0xFFull << shift;
-            }
-        }
-        __syncthreads();
-        if (all_valid) break;
-    }
-    const u64 thr_key = all_valid ? 1ull : prefix;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const u64 key = kk[i];
-        if (key != 0ull && key >= thr_key) {
-            const int pos = atomicAdd(&nsel, 1);
+        if (selected(key, st)) {
+            const int pos = atomicAdd(&st.count, 1);
             if (pos < FT_MAX_TOPK) sel[pos] = key;
         }
     }
     __syncthreads();
-    const int cnt = min(min(nsel, K), FT_MAX_TOPK);
+    const int cnt = min(min(st.count, K), FT_MAX_TOPK);
     int Kp = 1;
-    while (Kp < K) Kp <<= 1;
+    while (Kp < cnt) Kp <<= 1;
     for (int i = threadIdx.x; i < Kp; i += blockDim.x)
         if (i >= cnt) sel[i] = 0ull;
     __syncthreads();
@@ -186,9 +245,9 @@ k_peak_select(const u64* __restrict__ keys, int n, int K, int Hp, int S, ft_peak
         } else {
             p.t = 0; p.s = 0; p.value = 0.f; p.k = 0.f; p.b = 0.f;
         }
-        out[(size_t)img * K + i] = p;
+        out[(size_t)blockIdx.x * K + i] = p;
     }
-    if (threadIdx.x == 0) count[img] = cnt;
+    if (threadIdx.x == 0) count[blockIdx.x] = cnt;
 }
 
 static int kt_of(int top_k) { return top_k < PK_CAND ? top_k : PK_CAND; }
@@ -204,7 +263,7 @@ size_t peaks_key_bytes(int Hp, int S, int batch, int top_k) {
 
 cudaError_t launch_peak_tiles(const float* map, int Hp, int S, int batch, int top_k, float threshold,
                               unsigned long long* keys, cudaStream_t st) {
-    k_peak_tiles<<<tile_grid(Hp, S, batch), 256, 0, st>>>(map, Hp, S, kt_of(top_k), threshold, keys);
+    k_peak_tiles<<<tile_grid(Hp, S, batch), PK_TILE_THREADS, 0, st>>>(map, Hp, S, kt_of(top_k), threshold, keys);
     return cudaGetLastError();
 }
 

@@ -24,30 +24,6 @@
 // workspace row pitch is S >= W).
 #include "ft_internal.cuh"
 
-__device__ __forceinline__ int floor_div(int a, int b) {   // b > 0
-    int q = a / b;
-    return (a % b != 0 && a < 0) ? q - 1 : q;
-}
-__device__ __forceinline__ int ceil_div(int a, int b) {    // b > 0
-    int q = a / b;
-    return (a % b != 0 && a > 0) ? q + 1 : q;
-}
-
-// Keys' cubic kernel with a = -0.5.
-__device__ __forceinline__ float keys_w(float s) {
-    const float a = -0.5f;
-    s = fabsf(s);
-    if (s <= 1.f) return ((a + 2.f) * s - (a + 3.f)) * s * s + 1.f;
-    if (s < 2.f) return ((a * s - 5.f * a) * s + 8.f * a) * s - 4.f * a;
-    return 0.f;
-}
-
-// Weight of tap offset d (tap = floor + d) at fraction fr.
-__device__ __forceinline__ float tap_weight(int interp, int d, float fr) {
-    if (interp == FT_INTERP_LINEAR) return d == 0 ? 1.f - fr : fr;
-    return keys_w(fr - (float)d);
-}
-
 __global__ void __launch_bounds__(FT_THREADS)
 k_nvmt_rows(float2* __restrict__ ws, int W, int S, int Hp, int L, int interp, FftLen fx,
             int logRB) {

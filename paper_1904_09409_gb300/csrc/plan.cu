@@ -8,7 +8,9 @@
 #include <new>
 #include <vector>
 
-#include "ft_internal.cuh"
+#include <stdlib.h>
+
+#include "fft_fast.cuh"
 
 static thread_local char g_last_error[256] = "";
 
@@ -100,6 +102,18 @@ static void prof_end(ft_plan p, cudaStream_t st) { cudaEventRecord(p->prof_pool[
         if (e_ != cudaSuccess) return cuda_fail(e_, where);  \
     } while (0)
 
+// Per-pass twiddles of the fixed-length kernels: for pass s >= 1 with radix R and
+// P = product of the earlier radices, entry [k][q-1] = exp(-2 pi i q k / (P R)),
+// taken from the exact-index table tw of length N.
+static void stage_twiddles(int N, const float2* tw, float2* out) {
+    for (int s = 1; s < fs_nst(N); ++s) {
+        const int R = fs_radix(N, s), P = fs_P(N, s), step = N / (P * R);
+        float2* o = out + fs_twoff(N, s);
+        for (int k = 0; k < P; ++k)
+            for (int q = 1; q < R; ++q) o[k * (R - 1) + q - 1] = tw[q * k * step];
+    }
+}
+
 static int log2_floor(int v) {
     int l = 0;
     while ((2 << l) <= v) ++l;
@@ -131,6 +145,39 @@ static ft_status ensure(void** ptr, size_t* have, size_t need, const char* what)
 }
 
 static size_t spec_bytes(ft_plan p, int batch) { return (size_t)batch * p->L * p->S * sizeof(float2); }
+
+// Fixed-length kernels where the length has a schedule, generic ones otherwise.
+static cudaError_t col_r2c(ft_plan p, const float* in, int rows_in, int ncols, int in_pitch,
+                           size_t in_img, int row0, float2* out, float es, float ms, int batch,
+                           cudaStream_t st) {
+    const size_t out_img = (size_t)p->L * p->S;
+    if (p->fy.stw)
+        return launch_col_r2c_fast(in, rows_in, ncols, in_pitch, in_img, row0, p->fy, out, p->S, out_img,
+                                   es, ms, batch, st);
+    return launch_col_r2c(in, rows_in, ncols, in_pitch, in_img, row0, p->fy, p->col_logB_y, out, p->S,
+                          out_img, es, ms, batch, st);
+}
+
+static cudaError_t col_c2r(ft_plan p, const float2* in, int ncols, float mid, float* out, int row0,
+                           int rows_out, int out_pitch, size_t out_img, float os, int batch,
+                           cudaStream_t st) {
+    const size_t in_img = (size_t)p->L * p->S;
+    if (p->fy.stw)
+        return launch_col_c2r_fast(in, ncols, p->S, in_img, p->fy, mid, out, row0, rows_out, out_pitch,
+                                   out_img, os, batch, st);
+    return launch_col_c2r(in, ncols, p->S, in_img, p->fy, p->col_logB_y, mid, out, row0, rows_out,
+                          out_pitch, out_img, os, batch, st);
+}
+
+static cudaError_t nvmt_rows(ft_plan p, float2* ws, int batch, cudaStream_t st) {
+    if (p->fx.stw) return launch_nvmt_rows_fast(ws, p->W, p->Hp, p->L, p->interp, p->fx, batch, st);
+    return launch_nvmt_rows(ws, p->W, p->S, p->Hp, p->L, p->interp, p->fx, p->row_logB_x, batch, st);
+}
+
+static cudaError_t nvmt_rows_adj(ft_plan p, float2* ws, int batch, cudaStream_t st) {
+    if (p->fx.stw) return launch_nvmt_rows_adjoint_fast(ws, p->W, p->Hp, p->L, p->interp, p->fx, batch, st);
+    return launch_nvmt_rows_adjoint(ws, p->W, p->S, p->Hp, p->L, p->interp, p->fx, p->row_logB_x, batch, st);
+}
 
 extern "C" {
 
@@ -172,9 +219,15 @@ ft_status ft_plan_create(ft_plan* out, int H, int W, int n_slope, int n_intercep
         delete p;
         return cuda_fail(e, "cudaGetDevice");
     }
-    std::vector<float2> tw((size_t)fy.N + fx.N);
+    const char* force = getenv("FT_FORCE_GENERIC");
+    const bool generic = force && force[0] == '1';
+    const bool fast_y = !generic && fs_has(fy.N), fast_x = !generic && fs_has(fx.N);
+    const size_t sy = fast_y ? fs_twsize(fy.N) : 0, sx = fast_x ? fs_twsize(fx.N) : 0;
+    std::vector<float2> tw((size_t)fy.N + fx.N + sy + sx);
     twiddles(fy.N, tw.data());
     twiddles(fx.N, tw.data() + fy.N);
+    if (fast_y) stage_twiddles(fy.N, tw.data(), tw.data() + fy.N + fx.N);
+    if (fast_x) stage_twiddles(fx.N, tw.data() + fy.N, tw.data() + fy.N + fx.N + sy);
     e = cudaMalloc(&p->d_tw, tw.size() * sizeof(float2));
     if (e != cudaSuccess) {
         delete p;
@@ -189,6 +242,8 @@ ft_status ft_plan_create(ft_plan* out, int H, int W, int n_slope, int n_intercep
     }
     p->fy.tw = p->d_tw;
     p->fx.tw = p->d_tw + fy.N;
+    p->fy.stw = fast_y ? p->d_tw + fy.N + fx.N : nullptr;
+    p->fx.stw = fast_x ? p->d_tw + fy.N + fx.N + sy : nullptr;
     // transforms per block: 2 ping-pong buffers of N x B complex within 96 KB
     const int cap = 96 * 1024 / (int)(2 * sizeof(float2));
     p->col_logB_y = log2_floor(cap / fy.N > 0 ? cap / fy.N : 1);
@@ -235,15 +290,12 @@ ft_status ft_forward(ft_plan p, const float* d_img, float* d_map, int batch, voi
     float2* ws = (float2*)p->d_ws;
     const size_t ws_img = (size_t)p->L * p->S;
     FT_LAUNCH(p, FT_KERNEL_COL_R2C, st,
-              launch_col_r2c(d_img, p->H, p->W, p->W, (size_t)p->H * p->W, p->top, p->fy,
-                             p->col_logB_y, ws, p->S, ws_img, 1.f, 1.f, batch, st),
+              col_r2c(p, d_img, p->H, p->W, p->W, (size_t)p->H * p->W, p->top, ws, 1.f, 1.f, batch, st),
               "step 1 (column R2C)");
-    FT_LAUNCH(p, FT_KERNEL_NVMT_ROWS, st,
-              launch_nvmt_rows(ws, p->W, p->S, p->Hp, p->L, p->interp, p->fx, p->row_logB_x, batch, st),
-              "steps 2-3 (NVMT + row FFT)");
+    FT_LAUNCH(p, FT_KERNEL_NVMT_ROWS, st, nvmt_rows(p, ws, batch, st), "steps 2-3 (NVMT + row FFT)");
     FT_LAUNCH(p, FT_KERNEL_COL_C2R, st,
-              launch_col_c2r(ws, p->S, p->S, ws_img, p->fy, p->col_logB_y, 1.f, d_map, 0, p->Hp, p->S,
-                             (size_t)p->Hp * p->S, 1.f / (float)p->Hp, batch, st),
+              col_c2r(p, ws, p->S, 1.f, d_map, 0, p->Hp, p->S, (size_t)p->Hp * p->S, 1.f / (float)p->Hp,
+                      batch, st),
               "step 4 (column C2R)");
     return FT_OK;
 }
@@ -260,16 +312,11 @@ ft_status ft_backward(ft_plan p, const float* d_grad_map, float* d_grad_img, int
     const size_t ws_img = (size_t)p->L * p->S;
     const float inv = 1.f / (float)p->Hp;
     FT_LAUNCH(p, FT_KERNEL_COL_R2C, st,
-              launch_col_r2c(d_grad_map, p->Hp, p->S, p->S, (size_t)p->Hp * p->S, 0, p->fy,
-                             p->col_logB_y, ws, p->S, ws_img, inv, 2.f * inv, batch, st),
+              col_r2c(p, d_grad_map, p->Hp, p->S, p->S, (size_t)p->Hp * p->S, 0, ws, inv, 2.f * inv, batch, st),
               "adjoint of step 4");
-    FT_LAUNCH(p, FT_KERNEL_NVMT_ROWS_ADJ, st,
-              launch_nvmt_rows_adjoint(ws, p->W, p->S, p->Hp, p->L, p->interp, p->fx, p->row_logB_x,
-                                       batch, st),
-              "adjoint of steps 2-3");
+    FT_LAUNCH(p, FT_KERNEL_NVMT_ROWS_ADJ, st, nvmt_rows_adj(p, ws, batch, st), "adjoint of steps 2-3");
     FT_LAUNCH(p, FT_KERNEL_COL_C2R, st,
-              launch_col_c2r(ws, p->W, p->S, ws_img, p->fy, p->col_logB_y, 0.5f, d_grad_img, p->top,
-                             p->H, p->W, (size_t)p->H * p->W, 1.f, batch, st),
+              col_c2r(p, ws, p->W, 0.5f, d_grad_img, p->top, p->H, p->W, (size_t)p->H * p->W, 1.f, batch, st),
               "adjoint of step 1");
     return FT_OK;
 }

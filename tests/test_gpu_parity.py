@@ -182,3 +182,22 @@ def test_backward_matches_oracle_adjoint(torch, H, W, S, Hp, interp):
         lhs = float(np.sum(px[i].astype(np.float64) * g[i]))
         rhs = float(np.sum(x[i].astype(np.float64) * gi[i]))
         assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(px[i]) * np.linalg.norm(g[i])
+
+
+# ------------------------------------------- generic kernels on fast lengths
+@pytest.mark.parametrize("H,W,S,Hp,interp", [(256, 256, 256, 256, "linear"), (100, 96, 192, 384, "cubic"),
+                                             (128, 128, 128, 1024, "linear")])
+def test_generic_path_matches_oracle(torch, monkeypatch, H, W, S, Hp, interp):
+    """Lengths with a fixed schedule normally take the register-resident kernels;
+    FT_FORCE_GENERIC=1 at plan creation keeps the generic shared-memory kernels
+    reachable, and both must agree with the oracle (forward and adjoint)."""
+    monkeypatch.setenv("FT_FORCE_GENERIC", "1")
+    imgs = inputs(H, W, 2, seed=3)
+    rng = np.random.default_rng(4)
+    g = rng.standard_normal((2, Hp, S)).astype(np.float32)
+    with make_plan(H, W, S, Hp, interp) as plan:
+        got = _gpu.forward(plan, imgs)
+        gi = _gpu.backward(plan, g)
+    for i in range(2):
+        assert _gpu.rel_l2(got[i], oracle.funnel_ref(imgs[i], S, Hp, interp)) <= TOL_MAP
+        assert _gpu.rel_l2(gi[i], oracle.adjoint_ref(g[i].astype(np.float64), H, W, interp)) <= TOL_MAP
