@@ -110,6 +110,18 @@ k_col_c2r_fast(const float2* __restrict__ in, int ncols, int in_pitch, size_t in
         }
 }
 
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// row pitch (complex) of the staged spectrum rows: W + 2 keeps 16-byte
+// alignment for cp.async and shifts successive rows by 4 banks
+__host__ __device__ constexpr int srow_pitch(int W) { return W + 2; }
+
 template <int N>
 __global__ void __launch_bounds__(fs_T(N) * fs_Brow(N))
 k_nvmt_rows_fast(float2* __restrict__ ws, int W, int Hp, int L, int interp,
@@ -120,24 +132,35 @@ k_nvmt_rows_fast(float2* __restrict__ ws, int W, int Hp, int L, int interp,
     constexpr int STEPX = N / R0;                      // x' distance between a thread's elements
     using F = FastFft<N, +1, B>;
     extern __shared__ float2 sm[];
-    float2* srow = sm + F::SLOTS;                      // [W][B] input rows
+    float2* srow = sm + ((F::SLOTS + 1) & ~1);         // [B][W + 2] input rows (16-byte aligned)
+    const int WP = srow_pitch(W);
     const int f = threadIdx.x % B;
     const int t = threadIdx.x / B;
     const int l0 = blockIdx.x * B;
     const int l = l0 + f;
     float2* base = ws + (size_t)blockIdx.y * L * N;
 
-    for (int idx = threadIdx.x; idx < W * B; idx += blockDim.x) {
-        const int r = idx % B;
-        const int x = idx / B;
-        srow[idx] = (l0 + r < L) ? base[(size_t)(l0 + r) * N + x] : make_float2(0.f, 0.f);
+    // stage the block's B spectrum rows (W complex each) with 16-byte async copies
+    const int chunks = W >> 1;                         // two complex per 16 bytes
+    for (int idx = threadIdx.x; idx < B * chunks; idx += blockDim.x) {
+        const int r = idx / chunks;
+        const int c = idx - r * chunks;
+        float2* dst = srow + r * WP + 2 * c;
+        if (l0 + r < L) {
+            cp_async16(dst, base + (size_t)(l0 + r) * N + 2 * c);
+        } else {
+            dst[0] = make_float2(0.f, 0.f);
+            dst[1] = make_float2(0.f, 0.f);
+        }
     }
+    cp_async_wait_all();
     __syncthreads();
 
     float2 v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = make_float2(0.f, 0.f);
     if (l >= 1 && l < L) {
+        const float2* myrow = srow + f * WP;
         const int den = 2 * l;
         const float inv = 1.f / (float)den;
         const int step = STEPX * Hp;
@@ -159,7 +182,7 @@ k_nvmt_rows_fast(float2* __restrict__ ws, int W, int Hp, int L, int interp,
                     const int col = qf + d + halfW;
                     if (col >= 0 && col < W) {
                         const float w = tap_weight(interp, d, fr);
-                        const float2 s = srow[col * B + f];
+                        const float2 s = myrow[col];
                         acc.x += w * s.x;
                         acc.y += w * s.y;
                     }
@@ -283,7 +306,7 @@ template <int N>
 static cudaError_t go_rows(float2* ws, int W, int Hp, int L, int interp, const float2* stw, int batch,
                            cudaStream_t st) {
     constexpr int B = fs_Brow(N);
-    const size_t sm = ((size_t)FastFft<N, +1, B>::SLOTS + (size_t)W * B) * sizeof(float2);
+    const size_t sm = ((size_t)((FastFft<N, +1, B>::SLOTS + 1) & ~1) + (size_t)srow_pitch(W) * B) * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_nvmt_rows_fast<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     dim3 grid((L + B - 1) / B, batch);

@@ -14,6 +14,11 @@
 //                 mark strict local maxima (at most one per 2 x 2 block, so at most
 //                 512 per tile; neighbour indices are computed only to break exact
 //                 ties), and keep the best min(top_k, 512) by radix selection.
+//  k_peak_tiles_fast  the same for maps with S % 128 == 0 and H' % 32 == 0, one
+//                 block per 32 x 128 tile without a shared-memory copy: each lane
+//                 holds 4 columns of 6 rows (float4 loads), column neighbours come
+//                 from the adjacent lanes by shuffles, candidates are appended per
+//                 warp with one ballot (at most 1024 per tile).
 //  k_peak_select  one block per image: radix selection of the top_k keys among
 //                 the tiles' keys, then a bitonic sort of those top_k and the
 //                 ft_peak records.
@@ -250,9 +255,106 @@ k_peak_select(const u64* __restrict__ keys, int n, int K, int Hp, int S, ft_peak
     if (threadIdx.x == 0) count[blockIdx.x] = cnt;
 }
 
+#define PF_TT 32
+#define PF_TS 128
+#define PF_CAND 1024
+
+__global__ void __launch_bounds__(PK_TILE_THREADS)
+k_peak_tiles_fast(const float* __restrict__ map, int Hp, int S, int KT, float thr, u64* __restrict__ keys) {
+    __shared__ u64 cand[PF_CAND];
+    __shared__ int ncand;
+    __shared__ SelState st;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int img = blockIdx.z;
+    const int t0 = blockIdx.y * PF_TT + 4 * warp;          // first of this warp's 4 rows
+    const int s0 = blockIdx.x * PF_TS;
+    const float* m = map + (size_t)img * Hp * S;
+    if (threadIdx.x == 0) ncand = 0;
+
+    // rows t0-1 .. t0+4 (wrapped); lane holds columns s0 + 4 lane .. + 3
+    float4 a[6];
+    float lo[6], hi[6];
+    const int sl = s0 == 0 ? S - 1 : s0 - 1;
+    const int sr = s0 + PF_TS == S ? 0 : s0 + PF_TS;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const int t = wrap_into(t0 - 1 + k, Hp);
+        const float* rowp = m + (size_t)t * S;
+        float4 x = __ldg(reinterpret_cast<const float4*>(rowp + s0) + lane);
+        a[k] = make_float4(fabsf(x.x), fabsf(x.y), fabsf(x.z), fabsf(x.w));
+        float h = 0.f;
+        if (lane == 0) h = fabsf(__ldg(rowp + sl));
+        if (lane == 31) h = fabsf(__ldg(rowp + sr));
+        const float up = __shfl_up_sync(0xffffffffu, a[k].w, 1);
+        const float dn = __shfl_down_sync(0xffffffffu, a[k].x, 1);
+        lo[k] = lane == 0 ? h : up;
+        hi[k] = lane == 31 ? h : dn;
+    }
+    __syncthreads();
+
+#pragma unroll
+    for (int k = 1; k <= 4; ++k) {
+        const float rm[6] = {lo[k - 1], a[k - 1].x, a[k - 1].y, a[k - 1].z, a[k - 1].w, hi[k - 1]};
+        const float r0[6] = {lo[k], a[k].x, a[k].y, a[k].z, a[k].w, hi[k]};
+        const float rp[6] = {lo[k + 1], a[k + 1].x, a[k + 1].y, a[k + 1].z, a[k + 1].w, hi[k + 1]};
+        const int t = t0 + k - 1;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float v = r0[c + 1];
+            const int s = s0 + 4 * lane + c;
+            const unsigned lin = (unsigned)t * (unsigned)S + (unsigned)s;
+            const float nb[8] = {rm[c], rm[c + 1], rm[c + 2], r0[c], r0[c + 2], rp[c], rp[c + 1], rp[c + 2]};
+            bool is_max = v >= thr;
+            bool tie = false;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                is_max = is_max && !(nb[j] > v);
+                tie = tie || nb[j] == v;
+            }
+            if (is_max && tie) {
+                // exact tie: the neighbour precedes iff its linear index is smaller
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (nb[j] != v) continue;
+                    const int dr = j < 3 ? -1 : (j < 5 ? 0 : 1);
+                    const int dc = j < 3 ? j - 1 : (j == 3 ? -1 : (j == 4 ? 1 : j - 6));
+                    const unsigned nl = (unsigned)wrap_into(t + dr, Hp) * (unsigned)S +
+                                        (unsigned)wrap_into(s + dc, S);
+                    if (nl != lin && nl < lin) is_max = false;
+                }
+            }
+            const unsigned ballot = __ballot_sync(0xffffffffu, is_max);
+            if (ballot) {
+                int basepos = 0;
+                if (lane == 0) basepos = atomicAdd(&ncand, __popc(ballot));
+                basepos = __shfl_sync(0xffffffffu, basepos, 0);
+                if (is_max) cand[basepos + __popc(ballot & ((1u << lane) - 1u))] = peak_key(v, lin);
+            }
+        }
+    }
+    __syncthreads();
+    const int n = min(ncand, PF_CAND);
+    u64* out = keys + ((size_t)img * gridDim.y * gridDim.x + (size_t)blockIdx.y * gridDim.x + blockIdx.x) * KT;
+    if (n <= KT) {
+        for (int i = threadIdx.x; i < KT; i += blockDim.x) out[i] = i < n ? cand[i] : 0ull;
+        return;
+    }
+    cta_select(cand, n, KT, st);
+    if (threadIdx.x == 0) st.count = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const u64 key = cand[i];
+        if (selected(key, st)) out[atomicAdd(&st.count, 1)] = key;
+    }
+}
+
 static int kt_of(int top_k) { return top_k < PK_CAND ? top_k : PK_CAND; }
 
+static bool fast_tiles(int Hp, int S) { return S % PF_TS == 0 && Hp % PF_TT == 0; }
+
 static dim3 tile_grid(int Hp, int S, int batch) {
+    if (fast_tiles(Hp, S)) return dim3(S / PF_TS, Hp / PF_TT, batch);
     return dim3((S + PK_TS - 1) / PK_TS, (Hp + PK_TT - 1) / PK_TT, batch);
 }
 
@@ -263,7 +365,12 @@ size_t peaks_key_bytes(int Hp, int S, int batch, int top_k) {
 
 cudaError_t launch_peak_tiles(const float* map, int Hp, int S, int batch, int top_k, float threshold,
                               unsigned long long* keys, cudaStream_t st) {
-    k_peak_tiles<<<tile_grid(Hp, S, batch), PK_TILE_THREADS, 0, st>>>(map, Hp, S, kt_of(top_k), threshold, keys);
+    if (fast_tiles(Hp, S))
+        k_peak_tiles_fast<<<tile_grid(Hp, S, batch), PK_TILE_THREADS, 0, st>>>(map, Hp, S, kt_of(top_k),
+                                                                               threshold, keys);
+    else
+        k_peak_tiles<<<tile_grid(Hp, S, batch), PK_TILE_THREADS, 0, st>>>(map, Hp, S, kt_of(top_k), threshold,
+                                                                          keys);
     return cudaGetLastError();
 }
 

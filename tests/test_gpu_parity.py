@@ -131,7 +131,7 @@ def test_full_size_batch_sampled(torch):
 
 
 # ------------------------------------------------------------------- peaks
-@pytest.mark.parametrize("Hp,S", [(2, 2), (4, 6), (8, 8), (48, 72), (64, 128), (96, 216)])
+@pytest.mark.parametrize("Hp,S", [(2, 2), (4, 6), (8, 8), (48, 72), (64, 128), (96, 216), (32, 384), (128, 256)])
 @pytest.mark.parametrize("K", [1, 5, 64])
 def test_peaks_exact_with_ties(torch, Hp, S, K):
     rng = np.random.default_rng(Hp * 1000 + S + K)
@@ -145,10 +145,11 @@ def test_peaks_exact_with_ties(torch, Hp, S, K):
 
 
 @pytest.mark.parametrize("K", [32, 513, 1024])
-def test_peaks_exact_large_k(torch, K):
+@pytest.mark.parametrize("Hp,S", [(256, 192), (256, 256)])     # generic and register-only tiles
+def test_peaks_exact_large_k(torch, K, Hp, S):
     rng = np.random.default_rng(K)
-    maps = rng.standard_normal((2, 256, 192)).astype(np.float32)
-    with make_plan(256, 192, 192, 256) as plan:
+    maps = rng.standard_normal((2, Hp, S)).astype(np.float32)
+    with make_plan(Hp, S, S, Hp) as plan:
         got, _ = _gpu.peaks(plan, maps, K)
     for i in range(2):
         ref = oracle.peaks_ref(np.abs(maps[i]).astype(np.float64), K)
