@@ -14,7 +14,8 @@
 // global memory directly.  All index arithmetic is by compile-time constants.
 //
 // Twiddles come from a per-length table (FP64 values rounded to FP32, built on
-// the host): for pass s >= 1, entry [k][q-1] = exp(-2 pi i q k / (P R)).
+// the host): for pass s >= 1, row k holds exp(-2 pi i q k / (P R)) at column q
+// (q = 0 .. R-1, rows padded to an even length so pairs load as float4).
 #pragma once
 
 #include "ft_internal.cuh"
@@ -48,9 +49,11 @@ __host__ __device__ constexpr int fs_P(int N, int s) {
     for (int j = 0; j < s; ++j) p *= fs_radix(N, j);
     return p;
 }
+// twiddle row stride of a pass with radix R: R rounded up to even (16-byte rows)
+__host__ __device__ constexpr int fs_rs(int R) { return (R + 1) & ~1; }
 __host__ __device__ constexpr int fs_twoff(int N, int s) {
     int o = 0;
-    for (int j = 1; j < s; ++j) o += fs_P(N, j) * (fs_radix(N, j) - 1);
+    for (int j = 1; j < s; ++j) o += fs_P(N, j) * fs_rs(fs_radix(N, j));
     return o;
 }
 __host__ __device__ constexpr int fs_twsize(int N) { return fs_twoff(N, fs_nst(N)); }
@@ -62,6 +65,14 @@ __host__ __device__ constexpr int fs_Brow(int N) { return fs_clampB(256 / fs_T(N
 // spreads the strided stores of the first pass over the banks)
 __host__ __device__ constexpr int spos(int n) { return n + (n >> 4); }
 __host__ __device__ constexpr int fs_slots(int N) { return spos(N - 1) + 1; }
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
 
 template <int SIGN>
 __device__ __forceinline__ float2 tw_sign(float2 w) { return SIGN > 0 ? make_float2(w.x, -w.y) : w; }
@@ -126,10 +137,17 @@ struct FastFft {
 #pragma unroll
         for (int m = 0; m < G; ++m) {
             if constexpr (P > 1) {
+                constexpr int RS = fs_rs(R);
                 const int k = (t + m * T) % P;
-                const float2* w = stw + fs_twoff(N, s) + k * (R - 1);
+                const float4* w = reinterpret_cast<const float4*>(stw + fs_twoff(N, s) + k * RS);
 #pragma unroll
-                for (int q = 1; q < R; ++q) v[m * R + q] = cmul(v[m * R + q], tw_sign<SIGN>(__ldg(w + q - 1)));
+                for (int h = 0; h < RS / 2; ++h) {
+                    const float4 ww = __ldg(w + h);
+                    if (2 * h >= 1 && 2 * h < R)
+                        v[m * R + 2 * h] = cmul(v[m * R + 2 * h], tw_sign<SIGN>(make_float2(ww.x, ww.y)));
+                    if (2 * h + 1 < R)
+                        v[m * R + 2 * h + 1] = cmul(v[m * R + 2 * h + 1], tw_sign<SIGN>(make_float2(ww.z, ww.w)));
+                }
             }
             Dft<R, SIGN>::run(&v[m * R]);
         }
@@ -177,6 +195,9 @@ struct FastFft {
 
 // launchers of the fixed-length kernels (k_fast.cu); they return
 // cudaErrorNotSupported when N has no schedule
+// staging of the column kernels' inputs with cp.async needs 16-byte rows
+__host__ __device__ constexpr bool col_stage_ok(int ncols, int in_pitch) { return ncols % 4 == 0 && in_pitch % 4 == 0; }
+
 cudaError_t launch_col_r2c_fast(const float* in, int rows_in, int ncols, int in_pitch, size_t in_img,
                                 int row0, const FftLen& f, float2* out, int out_pitch, size_t out_img,
                                 float end_scale, float mid_scale, int batch, cudaStream_t st);

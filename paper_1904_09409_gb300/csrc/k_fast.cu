@@ -1,10 +1,11 @@
 // Fixed-length versions of the column and row kernels (see k_cols.cu and
 // k_rows.cu for what each step computes) built on the register-resident FFT of
 // fft_fast.cuh.  Differences from the generic kernels:
-//  * the first FFT pass reads global memory directly (columns: B adjacent
-//    column pairs per row segment; C2R: the Hermitian half, mirrored on the fly;
-//    rows: the NVMT gather feeds the registers) and the last pass writes global
-//    memory directly where the output order allows it;
+//  * inputs are staged into shared memory with 16-byte cp.async copies, all in
+//    flight at once (columns: the N x 2B image tile; C2R: the Hermitian half,
+//    each row read once for both n and N - n; rows: the B spectrum rows feeding
+//    the NVMT gather); the last pass writes global memory directly where the
+//    output order allows it;
 //  * the NVMT sample x' H' / (2 l) of successive elements of a thread is stepped
 //    exactly by adding the precomputed quotient and remainder of
 //    (N / R0) H' / (2 l), so the inner loop has no integer division;
@@ -29,16 +30,44 @@ k_col_r2c_fast(const float* __restrict__ in, int rows_in, int ncols, int in_pitc
     const float* src = in + (size_t)blockIdx.y * in_img + c;
 
     float2 v[E];
-#pragma unroll
-    for (int m = 0; m < G0; ++m)
-#pragma unroll
-        for (int q = 0; q < R0; ++q) {
-            const int row = F::template in_pos<0>(t, m, q) - row0;
-            float2 x = make_float2(0.f, 0.f);
-            if (colok && row >= 0 && row < rows_in)
-                x = __ldg(reinterpret_cast<const float2*>(src + (size_t)row * in_pitch));
-            v[m * R0 + q] = x;
+    if (B >= 2 && col_stage_ok(ncols, in_pitch)) {
+        // stage the N x 2B tile (zero rows outside the image) with 16-byte async
+        // copies, all in flight at once, then read the first pass from shared memory
+        constexpr int CPR = B >= 2 ? B / 2 : 1;         // 16-byte chunks per tile row
+        float* stg = reinterpret_cast<float*>(sm);      // [N][2B]
+        const int cb = blockIdx.x * 2 * B;
+        const float* img0 = in + (size_t)blockIdx.y * in_img;
+        for (int idx = threadIdx.x; idx < N * CPR; idx += blockDim.x) {
+            const int n = idx / CPR;
+            const int j = idx - n * CPR;
+            const int row = n - row0;
+            const int col = cb + 4 * j;
+            float* dst = stg + n * 2 * B + 4 * j;
+            if (row >= 0 && row < rows_in && col < ncols)
+                cp_async16(dst, img0 + (size_t)row * in_pitch + col);
+            else
+                *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
+        cp_async_wait_all();
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < G0; ++m)
+#pragma unroll
+            for (int q = 0; q < R0; ++q)
+                v[m * R0 + q] = *reinterpret_cast<const float2*>(stg + F::template in_pos<0>(t, m, q) * 2 * B + 2 * f);
+        __syncthreads();
+    } else {
+#pragma unroll
+        for (int m = 0; m < G0; ++m)
+#pragma unroll
+            for (int q = 0; q < R0; ++q) {
+                const int row = F::template in_pos<0>(t, m, q) - row0;
+                float2 x = make_float2(0.f, 0.f);
+                if (colok && row >= 0 && row < rows_in)
+                    x = __ldg(reinterpret_cast<const float2*>(src + (size_t)row * in_pitch));
+                v[m * R0 + q] = x;
+            }
+    }
     F::template run<0>(v, sm, t, f, stw);
 #pragma unroll
     for (int m = 0; m < GL; ++m)
@@ -77,6 +106,25 @@ k_col_c2r_fast(const float2* __restrict__ in, int ncols, int in_pitch, size_t in
     const bool colok = c < ncols;
     const float2* src = in + (size_t)blockIdx.y * in_img + c;
 
+    // stage the Hermitian half (rows 0 .. N/2, 2B complex each) with 16-byte async
+    // copies; every row is read once and serves both n and N - n
+    float2* stg = sm;                                  // [N/2 + 1][2B]
+    {
+        const int cb = blockIdx.x * 2 * B;
+        const float2* g0 = in + (size_t)blockIdx.y * in_img;
+        for (int idx = threadIdx.x; idx < (N / 2 + 1) * B; idx += blockDim.x) {
+            const int r = idx / B;
+            const int j = idx - r * B;
+            const int col = cb + 2 * j;
+            float2* dst = stg + r * 2 * B + 2 * j;
+            if (col < ncols)
+                cp_async16(dst, g0 + (size_t)r * in_pitch + col);
+            else
+                *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+    }
     float2 v[E];
 #pragma unroll
     for (int m = 0; m < G0; ++m)
@@ -84,8 +132,7 @@ k_col_c2r_fast(const float2* __restrict__ in, int ncols, int in_pitch, size_t in
         for (int q = 0; q < R0; ++q) {
             const int n = F::template in_pos<0>(t, m, q);
             const int r = n <= N / 2 ? n : N - n;
-            float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (colok) g = __ldg(reinterpret_cast<const float4*>(src + (size_t)r * in_pitch));
+            float4 g = *reinterpret_cast<const float4*>(stg + r * 2 * B + 2 * f);
             float2 z;
             if (r == 0 || r == N / 2) {
                 z = make_float2(g.x, g.z);                               // Re A + i Re B
@@ -96,6 +143,7 @@ k_col_c2r_fast(const float2* __restrict__ in, int ncols, int in_pitch, size_t in
             }
             v[m * R0 + q] = z;
         }
+    __syncthreads();
     F::template run<0>(v, sm, t, f, stw);
     if (!colok) return;
     float* dst = out + (size_t)blockIdx.y * out_img + c;
@@ -108,14 +156,6 @@ k_col_c2r_fast(const float2* __restrict__ in, int ncols, int in_pitch, size_t in
                 *reinterpret_cast<float2*>(dst + (size_t)rr * out_pitch) =
                     make_float2(v[m * RL + q].x * out_scale, v[m * RL + q].y * out_scale);
         }
-}
-
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 // row pitch (complex) of the staged spectrum rows: W + 2 keeps 16-byte

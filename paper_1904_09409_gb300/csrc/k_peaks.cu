@@ -260,9 +260,11 @@ k_peak_select(const u64* __restrict__ keys, int n, int K, int Hp, int S, ft_peak
 #define PF_CAND 1024
 
 __global__ void __launch_bounds__(PK_TILE_THREADS)
-k_peak_tiles_fast(const float* __restrict__ map, int Hp, int S, int KT, float thr, u64* __restrict__ keys) {
+k_peak_tiles_fast(const float* __restrict__ map, int Hp, int S, int KT, float thr, u64* __restrict__ keys,
+                  unsigned* __restrict__ tau) {
     __shared__ u64 cand[PF_CAND];
     __shared__ int ncand;
+    __shared__ unsigned kth_bits;
     __shared__ SelState st;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -270,7 +272,13 @@ k_peak_tiles_fast(const float* __restrict__ map, int Hp, int S, int KT, float th
     const int t0 = blockIdx.y * PF_TT + 4 * warp;          // first of this warp's 4 rows
     const int s0 = blockIdx.x * PF_TS;
     const float* m = map + (size_t)img * Hp * S;
-    if (threadIdx.x == 0) ncand = 0;
+    if (threadIdx.x == 0) {
+        ncand = 0;
+        kth_bits = 0xFFFFFFFFu;
+    }
+    // running lower bound of the image's top_k-th peak value (see launch_peak_tiles)
+    float lower = thr;
+    if (tau) lower = fmaxf(lower, __uint_as_float(__ldcg(tau + img)));
 
     // rows t0-1 .. t0+4 (wrapped); lane holds columns s0 + 4 lane .. + 3
     float4 a[6];
@@ -291,8 +299,8 @@ k_peak_tiles_fast(const float* __restrict__ map, int Hp, int S, int KT, float th
         lo[k] = lane == 0 ? h : up;
         hi[k] = lane == 31 ? h : dn;
     }
-    __syncthreads();
 
+    unsigned mask = 0u;                                    // bit 4 (k-1) + c: cell is a candidate
 #pragma unroll
     for (int k = 1; k <= 4; ++k) {
         const float rm[6] = {lo[k - 1], a[k - 1].x, a[k - 1].y, a[k - 1].z, a[k - 1].w, hi[k - 1]};
@@ -302,10 +310,8 @@ k_peak_tiles_fast(const float* __restrict__ map, int Hp, int S, int KT, float th
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const float v = r0[c + 1];
-            const int s = s0 + 4 * lane + c;
-            const unsigned lin = (unsigned)t * (unsigned)S + (unsigned)s;
             const float nb[8] = {rm[c], rm[c + 1], rm[c + 2], r0[c], r0[c + 2], rp[c], rp[c + 1], rp[c + 2]};
-            bool is_max = v >= thr;
+            bool is_max = v >= lower;
             bool tie = false;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
@@ -314,6 +320,8 @@ k_peak_tiles_fast(const float* __restrict__ map, int Hp, int S, int KT, float th
             }
             if (is_max && tie) {
                 // exact tie: the neighbour precedes iff its linear index is smaller
+                const int s = s0 + 4 * lane + c;
+                const unsigned lin = (unsigned)t * (unsigned)S + (unsigned)s;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     if (nb[j] != v) continue;
@@ -324,29 +332,60 @@ k_peak_tiles_fast(const float* __restrict__ map, int Hp, int S, int KT, float th
                     if (nl != lin && nl < lin) is_max = false;
                 }
             }
-            const unsigned ballot = __ballot_sync(0xffffffffu, is_max);
-            if (ballot) {
-                int basepos = 0;
-                if (lane == 0) basepos = atomicAdd(&ncand, __popc(ballot));
-                basepos = __shfl_sync(0xffffffffu, basepos, 0);
-                if (is_max) cand[basepos + __popc(ballot & ((1u << lane) - 1u))] = peak_key(v, lin);
+            if (is_max) mask |= 1u << (4 * (k - 1) + c);
+        }
+    }
+    __syncthreads();                                       // ncand initialised
+    // one append per warp: exclusive scan of the lanes' candidate counts
+    const int cnt = __popc(mask);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    int basepos = 0;
+    if (lane == 31 && incl > 0) basepos = atomicAdd(&ncand, incl);
+    basepos = __shfl_sync(0xffffffffu, basepos, 31) + incl - cnt;
+#pragma unroll
+    for (int k = 1; k <= 4; ++k) {
+        const float r0[4] = {a[k].x, a[k].y, a[k].z, a[k].w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (mask & (1u << (4 * (k - 1) + c))) {
+                const unsigned lin = (unsigned)(t0 + k - 1) * (unsigned)S + (unsigned)(s0 + 4 * lane + c);
+                cand[basepos++] = peak_key(r0[c], lin);
             }
         }
     }
     __syncthreads();
     const int n = min(ncand, PF_CAND);
     u64* out = keys + ((size_t)img * gridDim.y * gridDim.x + (size_t)blockIdx.y * gridDim.x + blockIdx.x) * KT;
-    if (n <= KT) {
+    if (n < KT) {
         for (int i = threadIdx.x; i < KT; i += blockDim.x) out[i] = i < n ? cand[i] : 0ull;
         return;
     }
-    cta_select(cand, n, KT, st);
-    if (threadIdx.x == 0) st.count = 0;
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const u64 key = cand[i];
-        if (selected(key, st)) out[atomicAdd(&st.count, 1)] = key;
+    if (n == KT) {
+        for (int i = threadIdx.x; i < KT; i += blockDim.x) {
+            out[i] = cand[i];
+            atomicMin(&kth_bits, (unsigned)(cand[i] >> 32));
+        }
+    } else {
+        cta_select(cand, n, KT, st);
+        if (threadIdx.x == 0) st.count = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const u64 key = cand[i];
+            if (selected(key, st)) {
+                out[atomicAdd(&st.count, 1)] = key;
+                atomicMin(&kth_bits, (unsigned)(key >> 32));
+            }
+        }
     }
+    // this tile alone has top_k candidates >= kth: the image's top_k-th peak is
+    // at least that bright, so later tiles may drop anything dimmer
+    __syncthreads();
+    if (tau && threadIdx.x == 0) atomicMax(tau + img, kth_bits);
 }
 
 static int kt_of(int top_k) { return top_k < PK_CAND ? top_k : PK_CAND; }
@@ -358,19 +397,37 @@ static dim3 tile_grid(int Hp, int S, int batch) {
     return dim3((S + PK_TS - 1) / PK_TS, (Hp + PK_TT - 1) / PK_TT, batch);
 }
 
-size_t peaks_key_bytes(int Hp, int S, int batch, int top_k) {
+static size_t key_bytes(int Hp, int S, int batch, int top_k) {
     const dim3 g = tile_grid(Hp, S, 1);
-    return (size_t)batch * g.x * g.y * kt_of(top_k) * sizeof(u64);
+    return ((size_t)batch * g.x * g.y * kt_of(top_k) * sizeof(u64) + 255) & ~(size_t)255;
 }
 
+// scratch: the tiles' keys, then one running bound per image
+size_t peaks_key_bytes(int Hp, int S, int batch, int top_k) {
+    return key_bytes(Hp, S, batch, top_k) + (size_t)batch * sizeof(unsigned);
+}
+
+// The register-only tile kernel keeps, per image, a running lower bound of the
+// top_k-th peak value (as float bits): a tile that finds top_k candidates raises
+// it to its own top_k-th value, and later tiles drop dimmer candidates before
+// selecting.  It only applies when every tile keeps top_k keys (top_k <= 512).
+// The bounds are cleared on the stream before the tiles run.
 cudaError_t launch_peak_tiles(const float* map, int Hp, int S, int batch, int top_k, float threshold,
                               unsigned long long* keys, cudaStream_t st) {
-    if (fast_tiles(Hp, S))
+    if (fast_tiles(Hp, S)) {
+        unsigned* tau = nullptr;
+        if (top_k <= PK_CAND) {
+            tau = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(keys) + key_bytes(Hp, S, batch, top_k));
+            cudaError_t e = cudaMemsetAsync(tau, 0, (size_t)batch * sizeof(unsigned), st);
+            if (e != cudaSuccess) return e;
+        }
         k_peak_tiles_fast<<<tile_grid(Hp, S, batch), PK_TILE_THREADS, 0, st>>>(map, Hp, S, kt_of(top_k),
-                                                                               threshold, keys);
-    else
+                                                                               threshold, keys, tau);
+    }
+    else {
         k_peak_tiles<<<tile_grid(Hp, S, batch), PK_TILE_THREADS, 0, st>>>(map, Hp, S, kt_of(top_k), threshold,
                                                                           keys);
+    }
     return cudaGetLastError();
 }
 

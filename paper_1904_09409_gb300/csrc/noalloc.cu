@@ -15,10 +15,11 @@
 
 #define FT_NOALLOC_MAX_DEVICES 64
 
-// Scratch for the per-tile keys.  Every call overwrites the part it uses before
-// reading it (each tile writes all of its key slots, padding included), so
-// nothing has to start at zero.  All calls share this one array: calls whose
-// work overlaps on the GPU (other streams, or other host threads) race on it.
+// Scratch for the per-tile keys and one running bound per map.  Every call
+// writes all the key slots it reads (padding included) and clears the bounds
+// with cudaMemsetAsync on its stream before use, so stale contents from an
+// earlier call never matter.  All calls share this one array: calls whose work
+// overlaps on the GPU (other streams, or other host threads) race on it.
 static __device__ __align__(256) unsigned char g_peak_scratch[FT_NOALLOC_SCRATCH_BYTES];
 
 static std::mutex g_setup_mutex;

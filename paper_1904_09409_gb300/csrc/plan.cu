@@ -103,14 +103,15 @@ static void prof_end(ft_plan p, cudaStream_t st) { cudaEventRecord(p->prof_pool[
     } while (0)
 
 // Per-pass twiddles of the fixed-length kernels: for pass s >= 1 with radix R and
-// P = product of the earlier radices, entry [k][q-1] = exp(-2 pi i q k / (P R)),
-// taken from the exact-index table tw of length N.
+// P = product of the earlier radices, row k (stride fs_rs(R)) holds
+// exp(-2 pi i q k / (P R)) at column q, taken from the exact-index table tw of
+// length N; padding entries are zero.
 static void stage_twiddles(int N, const float2* tw, float2* out) {
     for (int s = 1; s < fs_nst(N); ++s) {
-        const int R = fs_radix(N, s), P = fs_P(N, s), step = N / (P * R);
+        const int R = fs_radix(N, s), P = fs_P(N, s), step = N / (P * R), RS = fs_rs(R);
         float2* o = out + fs_twoff(N, s);
         for (int k = 0; k < P; ++k)
-            for (int q = 1; q < R; ++q) o[k * (R - 1) + q - 1] = tw[q * k * step];
+            for (int q = 0; q < RS; ++q) o[k * RS + q] = q < R ? tw[q * k * step] : make_float2(0.f, 0.f);
     }
 }
 
