@@ -1,17 +1,22 @@
 // Fixed-length versions of the column and row kernels (see k_cols.cu and
 // k_rows.cu for what each step computes) built on the register-resident FFT of
 // fft_fast.cuh.  Differences from the generic kernels:
-//  * inputs are staged into shared memory with 16-byte cp.async copies, all in
-//    flight at once (columns: the N x 2B image tile; C2R: the Hermitian half,
-//    each row read once for both n and N - n; rows: the B spectrum rows feeding
-//    the NVMT gather); the last pass writes global memory directly where the
-//    output order allows it;
+//  * the column kernel reads its first pass directly from global memory; the
+//    other two stage their inputs into shared memory with 16-byte cp.async
+//    copies, all in flight at once (C2R: the Hermitian half, each row read once
+//    for both n and N - n; rows: the B spectrum rows feeding the NVMT gather);
+//    the last pass writes global memory directly where the output order allows;
 //  * the NVMT sample x' H' / (2 l) of successive elements of a thread is stepped
 //    exactly by adding the precomputed quotient and remainder of
 //    (N / R0) H' / (2 l), so the inner loop has no integer division;
 //  * the interpolation fraction is remainder * (1 / (2 l)) in FP32 (within one
 //    rounding of the exact fraction).
 #include "fft_fast.cuh"
+
+// Staging the column kernel's image tile through shared memory measured slower
+// on GB300 than direct 8-byte loads into registers (60 vs 67 us for 32 images of
+// 1024^2), so it is compiled out; the C2R kernel keeps its staging.
+#define STAGE_R2C 0
 
 template <int N>
 __global__ void __launch_bounds__(fs_T(N) * fs_Bcol(N))
@@ -30,7 +35,7 @@ k_col_r2c_fast(const float* __restrict__ in, int rows_in, int ncols, int in_pitc
     const float* src = in + (size_t)blockIdx.y * in_img + c;
 
     float2 v[E];
-    if (B >= 2 && col_stage_ok(ncols, in_pitch)) {
+    if (STAGE_R2C && B >= 2 && col_stage_ok(ncols, in_pitch)) {
         // stage the N x 2B tile (zero rows outside the image) with 16-byte async
         // copies, all in flight at once, then read the first pass from shared memory
         constexpr int CPR = B >= 2 ? B / 2 : 1;         // 16-byte chunks per tile row

@@ -14,8 +14,9 @@
 //                 mark strict local maxima (at most one per 2 x 2 block, so at most
 //                 512 per tile; neighbour indices are computed only to break exact
 //                 ties), and keep the best min(top_k, 512) by radix selection.
-//  k_peak_tiles_fast  the same for maps with S % 128 == 0 and H' % 32 == 0, one
-//                 block per 32 x 128 tile without a shared-memory copy: each lane
+//  k_peak_tiles_fast  the same for maps with S % 128 == 0 and H' % 32 == 0, 32 x 128
+//                 tiles (16 blocks per map, each looping over its share of the
+//                 tiles) without a shared-memory copy of the map: each lane
 //                 holds 4 columns of 6 rows (float4 loads), column neighbours come
 //                 from the adjacent lanes by shuffles, candidates are appended per
 //                 warp with one ballot (at most 1024 per tile).
@@ -258,23 +259,27 @@ k_peak_select(const u64* __restrict__ keys, int n, int K, int Hp, int S, ft_peak
 #define PF_TT 32
 #define PF_TS 128
 #define PF_CAND 1024
+#define PF_BLOCKS_PER_MAP 16
 
-__global__ void __launch_bounds__(PK_TILE_THREADS)
-k_peak_tiles_fast(const float* __restrict__ map, int Hp, int S, int KT, float thr, u64* __restrict__ keys,
-                  unsigned* __restrict__ tau) {
-    __shared__ u64 cand[PF_CAND];
-    __shared__ int ncand;
-    __shared__ unsigned kth_bits;
-    __shared__ SelState st;
+struct TileShared {
+    u64 cand[PF_CAND];
+    int ncand;
+    unsigned kth_bits;
+    SelState st;
+};
+
+__device__ __forceinline__ void peak_tile_fast(const float* __restrict__ m, int Hp, int S, int KT, float thr,
+                                               int img, int ty, int tx, u64* __restrict__ out,
+                                               unsigned* __restrict__ tau, TileShared& sh) {
+    u64* cand = sh.cand;
+    SelState& st = sh.st;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int img = blockIdx.z;
-    const int t0 = blockIdx.y * PF_TT + 4 * warp;          // first of this warp's 4 rows
-    const int s0 = blockIdx.x * PF_TS;
-    const float* m = map + (size_t)img * Hp * S;
+    const int t0 = ty * PF_TT + 4 * warp;                  // first of this warp's 4 rows
+    const int s0 = tx * PF_TS;
     if (threadIdx.x == 0) {
-        ncand = 0;
-        kth_bits = 0xFFFFFFFFu;
+        sh.ncand = 0;
+        sh.kth_bits = 0xFFFFFFFFu;
     }
     // running lower bound of the image's top_k-th peak value (see launch_peak_tiles)
     float lower = thr;
@@ -345,7 +350,7 @@ k_peak_tiles_fast(const float* __restrict__ map, int Hp, int S, int KT, float th
         if (lane >= o) incl += y;
     }
     int basepos = 0;
-    if (lane == 31 && incl > 0) basepos = atomicAdd(&ncand, incl);
+    if (lane == 31 && incl > 0) basepos = atomicAdd(&sh.ncand, incl);
     basepos = __shfl_sync(0xffffffffu, basepos, 31) + incl - cnt;
 #pragma unroll
     for (int k = 1; k <= 4; ++k) {
@@ -359,16 +364,16 @@ k_peak_tiles_fast(const float* __restrict__ map, int Hp, int S, int KT, float th
         }
     }
     __syncthreads();
-    const int n = min(ncand, PF_CAND);
-    u64* out = keys + ((size_t)img * gridDim.y * gridDim.x + (size_t)blockIdx.y * gridDim.x + blockIdx.x) * KT;
+    const int n = min(sh.ncand, PF_CAND);
     if (n < KT) {
         for (int i = threadIdx.x; i < KT; i += blockDim.x) out[i] = i < n ? cand[i] : 0ull;
+        __syncthreads();                                   // cand / ncand reused by the next tile
         return;
     }
     if (n == KT) {
         for (int i = threadIdx.x; i < KT; i += blockDim.x) {
             out[i] = cand[i];
-            atomicMin(&kth_bits, (unsigned)(cand[i] >> 32));
+            atomicMin(&sh.kth_bits, (unsigned)(cand[i] >> 32));
         }
     } else {
         cta_select(cand, n, KT, st);
@@ -378,14 +383,30 @@ k_peak_tiles_fast(const float* __restrict__ map, int Hp, int S, int KT, float th
             const u64 key = cand[i];
             if (selected(key, st)) {
                 out[atomicAdd(&st.count, 1)] = key;
-                atomicMin(&kth_bits, (unsigned)(key >> 32));
+                atomicMin(&sh.kth_bits, (unsigned)(key >> 32));
             }
         }
     }
     // this tile alone has top_k candidates >= kth: the image's top_k-th peak is
     // at least that bright, so later tiles may drop anything dimmer
     __syncthreads();
-    if (tau && threadIdx.x == 0) atomicMax(tau + img, kth_bits);
+    if (tau && threadIdx.x == 0) atomicMax(tau + img, sh.kth_bits);
+    __syncthreads();                                       // cand / ncand reused by the next tile
+}
+
+// Blocks loop over the tiles of one image (tile = blockIdx.x + i * gridDim.x), so
+// that the running bound raised by a block's first tiles filters its later ones.
+__global__ void __launch_bounds__(PK_TILE_THREADS)
+k_peak_tiles_fast(const float* __restrict__ map, int Hp, int S, int KT, float thr, u64* __restrict__ keys,
+                  unsigned* __restrict__ tau) {
+    __shared__ TileShared sh;
+    const int img = blockIdx.y;
+    const int ntx = S / PF_TS, nty = Hp / PF_TT, ntiles = ntx * nty;
+    const float* m = map + (size_t)img * Hp * S;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int ty = tile / ntx, tx = tile - ty * ntx;
+        peak_tile_fast(m, Hp, S, KT, thr, img, ty, tx, keys + ((size_t)img * ntiles + tile) * KT, tau, sh);
+    }
 }
 
 static int kt_of(int top_k) { return top_k < PK_CAND ? top_k : PK_CAND; }
@@ -421,8 +442,9 @@ cudaError_t launch_peak_tiles(const float* map, int Hp, int S, int batch, int to
             cudaError_t e = cudaMemsetAsync(tau, 0, (size_t)batch * sizeof(unsigned), st);
             if (e != cudaSuccess) return e;
         }
-        k_peak_tiles_fast<<<tile_grid(Hp, S, batch), PK_TILE_THREADS, 0, st>>>(map, Hp, S, kt_of(top_k),
-                                                                               threshold, keys, tau);
+        const int ntiles = (S / PF_TS) * (Hp / PF_TT);
+        const dim3 grid(ntiles < PF_BLOCKS_PER_MAP ? ntiles : PF_BLOCKS_PER_MAP, batch);
+        k_peak_tiles_fast<<<grid, PK_TILE_THREADS, 0, st>>>(map, Hp, S, kt_of(top_k), threshold, keys, tau);
     }
     else {
         k_peak_tiles<<<tile_grid(Hp, S, batch), PK_TILE_THREADS, 0, st>>>(map, Hp, S, kt_of(top_k), threshold,
