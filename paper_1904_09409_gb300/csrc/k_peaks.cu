@@ -14,12 +14,13 @@
 //                 mark strict local maxima (at most one per 2 x 2 block, so at most
 //                 512 per tile; neighbour indices are computed only to break exact
 //                 ties), and keep the best min(top_k, 512) by radix selection.
-//  k_peak_tiles_fast  the same for maps with S % 128 == 0 and H' % 32 == 0, 32 x 128
-//                 tiles (16 blocks per map, each looping over its share of the
-//                 tiles) without a shared-memory copy of the map: each lane
+//  k_peak_tiles_fast  the same for maps with S % 128 == 0 and H' % 32 == 0, one
+//                 block per 32 x 128 tile without a shared-memory copy: each lane
 //                 holds 4 columns of 6 rows (float4 loads), column neighbours come
 //                 from the adjacent lanes by shuffles, candidates are appended per
-//                 warp with one ballot (at most 1024 per tile).
+//                 warp with one scan (at most 1024 per tile); a cell is tested
+//                 against the max of its 8 neighbours (a vertical max per column
+//                 first), exact ties alone take the index comparison.
 //  k_peak_select  one block per image: radix selection of the top_k keys among
 //                 the tiles' keys, then a bitonic sort of those top_k and the
 //                 ft_peak records.
@@ -259,7 +260,6 @@ k_peak_select(const u64* __restrict__ keys, int n, int K, int Hp, int S, ft_peak
 #define PF_TT 32
 #define PF_TS 128
 #define PF_CAND 1024
-#define PF_BLOCKS_PER_MAP 16
 
 struct TileShared {
     u64 cand[PF_CAND];
@@ -311,22 +311,20 @@ __device__ __forceinline__ void peak_tile_fast(const float* __restrict__ m, int 
         const float rm[6] = {lo[k - 1], a[k - 1].x, a[k - 1].y, a[k - 1].z, a[k - 1].w, hi[k - 1]};
         const float r0[6] = {lo[k], a[k].x, a[k].y, a[k].z, a[k].w, hi[k]};
         const float rp[6] = {lo[k + 1], a[k + 1].x, a[k + 1].y, a[k + 1].z, a[k + 1].w, hi[k + 1]};
+        float cm[6];                                       // max of the rows above and below
+#pragma unroll
+        for (int j = 0; j < 6; ++j) cm[j] = fmaxf(rm[j], rp[j]);
         const int t = t0 + k - 1;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const float v = r0[c + 1];
-            const float nb[8] = {rm[c], rm[c + 1], rm[c + 2], r0[c], r0[c + 2], rp[c], rp[c + 1], rp[c + 2]};
-            bool is_max = v >= lower;
-            bool tie = false;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                is_max = is_max && !(nb[j] > v);
-                tie = tie || nb[j] == v;
-            }
-            if (is_max && tie) {
-                // exact tie: the neighbour precedes iff its linear index is smaller
+            const float nmax = fmaxf(fmaxf(fmaxf(cm[c], cm[c + 1]), cm[c + 2]), fmaxf(r0[c], r0[c + 2]));
+            bool is_max = v >= lower && v >= nmax;
+            if (is_max && v == nmax) {
+                // exact tie: a tied neighbour precedes iff its linear index is smaller
                 const int s = s0 + 4 * lane + c;
                 const unsigned lin = (unsigned)t * (unsigned)S + (unsigned)s;
+                const float nb[8] = {rm[c], rm[c + 1], rm[c + 2], r0[c], r0[c + 2], rp[c], rp[c + 1], rp[c + 2]};
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     if (nb[j] != v) continue;
@@ -394,19 +392,19 @@ __device__ __forceinline__ void peak_tile_fast(const float* __restrict__ m, int 
     __syncthreads();                                       // cand / ncand reused by the next tile
 }
 
-// Blocks loop over the tiles of one image (tile = blockIdx.x + i * gridDim.x), so
-// that the running bound raised by a block's first tiles filters its later ones.
+// One block per tile; the image index runs fastest in the grid, so the blocks of
+// the first wave cover the first tiles of every image and the later waves find
+// each image's running bound already raised.
 __global__ void __launch_bounds__(PK_TILE_THREADS)
 k_peak_tiles_fast(const float* __restrict__ map, int Hp, int S, int KT, float thr, u64* __restrict__ keys,
                   unsigned* __restrict__ tau) {
     __shared__ TileShared sh;
-    const int img = blockIdx.y;
-    const int ntx = S / PF_TS, nty = Hp / PF_TT, ntiles = ntx * nty;
-    const float* m = map + (size_t)img * Hp * S;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int ty = tile / ntx, tx = tile - ty * ntx;
-        peak_tile_fast(m, Hp, S, KT, thr, img, ty, tx, keys + ((size_t)img * ntiles + tile) * KT, tau, sh);
-    }
+    const int img = blockIdx.x;
+    const int tile = blockIdx.y;
+    const int ntx = S / PF_TS, ntiles = ntx * (Hp / PF_TT);
+    const int ty = tile / ntx, tx = tile - ty * ntx;
+    peak_tile_fast(map + (size_t)img * Hp * S, Hp, S, KT, thr, img, ty, tx,
+                   keys + ((size_t)img * ntiles + tile) * KT, tau, sh);
 }
 
 static int kt_of(int top_k) { return top_k < PK_CAND ? top_k : PK_CAND; }
@@ -442,8 +440,7 @@ cudaError_t launch_peak_tiles(const float* map, int Hp, int S, int batch, int to
             cudaError_t e = cudaMemsetAsync(tau, 0, (size_t)batch * sizeof(unsigned), st);
             if (e != cudaSuccess) return e;
         }
-        const int ntiles = (S / PF_TS) * (Hp / PF_TT);
-        const dim3 grid(ntiles < PF_BLOCKS_PER_MAP ? ntiles : PF_BLOCKS_PER_MAP, batch);
+        const dim3 grid(batch, (S / PF_TS) * (Hp / PF_TT));
         k_peak_tiles_fast<<<grid, PK_TILE_THREADS, 0, st>>>(map, Hp, S, kt_of(top_k), threshold, keys, tau);
     }
     else {
