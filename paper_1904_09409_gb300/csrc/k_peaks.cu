@@ -44,6 +44,18 @@ __device__ __forceinline__ u64 peak_key(float v, unsigned lin) {
     return ((u64)__float_as_uint(v) << 32) | (u64)(0xFFFFFFFFu - lin);
 }
 
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 __device__ __forceinline__ int wrap_into(int a, int n) {
     if (a < 0) a += n;
     if (a >= n) a %= n;
@@ -261,7 +273,10 @@ k_peak_select(const u64* __restrict__ keys, int n, int K, int Hp, int S, ft_peak
 #define PF_TS 128
 #define PF_CAND 1024
 
+#define PF_PITCH (PF_TS + 8)
+
 struct TileShared {
+    float tile[(PF_TT + 2) * PF_PITCH];
     u64 cand[PF_CAND];
     int ncand;
     unsigned kth_bits;
@@ -285,24 +300,36 @@ __device__ __forceinline__ void peak_tile_fast(const float* __restrict__ m, int 
     float lower = thr;
     if (tau) lower = fmaxf(lower, __uint_as_float(__ldcg(tau + img)));
 
-    // rows t0-1 .. t0+4 (wrapped); lane holds columns s0 + 4 lane .. + 3
+    // the tile with its one-cell halo, |.| applied when read: PF_TT + 2 rows of
+    // PF_TS + 2 columns (interior at 16-byte aligned offset 4, halo at 3 and
+    // 4 + PF_TS), copied with cp.async (16 bytes interior, 4 bytes halo)
+    float* tl = sh.tile;
+    const int tb = ty * PF_TT;
+    for (int idx = threadIdx.x; idx < (PF_TT + 2) * (PF_TS / 4); idx += blockDim.x) {
+        const int r = idx / (PF_TS / 4);
+        const int j = idx - r * (PF_TS / 4);
+        const int t = wrap_into(tb - 1 + r, Hp);
+        cp_async16(tl + r * PF_PITCH + 4 + 4 * j, m + (size_t)t * S + s0 + 4 * j);
+    }
+    if (threadIdx.x < 2 * (PF_TT + 2)) {
+        const int r = threadIdx.x >> 1;
+        const int side = threadIdx.x & 1;
+        const int t = wrap_into(tb - 1 + r, Hp);
+        const int sc = side ? (s0 + PF_TS == S ? 0 : s0 + PF_TS) : (s0 == 0 ? S - 1 : s0 - 1);
+        cp_async4(tl + r * PF_PITCH + (side ? 4 + PF_TS : 3), m + (size_t)t * S + sc);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    // rows t0-1 .. t0+4 of this warp; lane holds columns s0 + 4 lane .. + 3
     float4 a[6];
     float lo[6], hi[6];
-    const int sl = s0 == 0 ? S - 1 : s0 - 1;
-    const int sr = s0 + PF_TS == S ? 0 : s0 + PF_TS;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-        const int t = wrap_into(t0 - 1 + k, Hp);
-        const float* rowp = m + (size_t)t * S;
-        float4 x = __ldg(reinterpret_cast<const float4*>(rowp + s0) + lane);
+        const float* rowp = tl + (4 * warp + k) * PF_PITCH + 4 + 4 * lane;
+        const float4 x = *reinterpret_cast<const float4*>(rowp);
         a[k] = make_float4(fabsf(x.x), fabsf(x.y), fabsf(x.z), fabsf(x.w));
-        float h = 0.f;
-        if (lane == 0) h = fabsf(__ldg(rowp + sl));
-        if (lane == 31) h = fabsf(__ldg(rowp + sr));
-        const float up = __shfl_up_sync(0xffffffffu, a[k].w, 1);
-        const float dn = __shfl_down_sync(0xffffffffu, a[k].x, 1);
-        lo[k] = lane == 0 ? h : up;
-        hi[k] = lane == 31 ? h : dn;
+        lo[k] = fabsf(rowp[-1]);
+        hi[k] = fabsf(rowp[4]);
     }
 
     unsigned mask = 0u;                                    // bit 4 (k-1) + c: cell is a candidate
