@@ -85,27 +85,24 @@ def kernel_bytes(name: str, H: int, W: int, S: int, Hp: int, K: int) -> float:
     }.get(name, 0.0)
 
 
-def source_digest() -> str:
+def sources_digest(files) -> str:
     h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_1904_09409_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel: str, batch: int):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled
-    to `batch` images, or None when absent or taken on other kernel sources."""
+    to `batch` images, or None when absent or when the kernel's sources have
+    changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
-        d = json.load(f)
-    if d.get("source_digest") != source_digest():
-        return None
-    k = d.get("kernels", {}).get(kernel)
-    if not k:
+        k = json.load(f).get("kernels", {}).get(kernel)
+    if not k or sources_digest(k["sources"]) != k["digest"]:
         return None
     return float(k["dram_bytes_per_image"]) * batch
 
