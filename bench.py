@@ -52,13 +52,69 @@ def parse():
 
 # ------------------------------------------------------------------ helpers
 def dist_info():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1904_09409_gb300 import replicas
+    return replicas.env_world()
 
 
-def make_batch(rank: int) -> np.ndarray:
+def make_batch(rank: int, world: int = 1, with_lines: bool = False):
+    """This rank's images: replicas.shard gives every rank its own BATCH images."""
+    from paper_1904_09409_gb300 import replicas, synth
+    idx = replicas.shard(rank, world, BATCH)
+    if not with_lines:
+        return synth.batch_1024(len(idx), start=idx.start, side=SIDE)
+    imgs = np.empty((len(idx), SIDE, SIDE), dtype=np.float32)
+    lines = []
+    for j, i in enumerate(idx):
+        si = synth.mixed_image(synth.WL_BATCH_1024, i, SIDE, SIDE)
+        imgs[j] = si.img
+        lines.append(si.lines)
+    return imgs, lines
+
+
+def line_cells(lines, H, W, n_slope, n_intercept):
+    """Map cells (t, s) of drawn lines (corner coordinates row = k col + b_c):
+    centred intercept b = b_c + k W/2 - H'/2 + (H'-H)/2, then eqs. (22)-(23)."""
+    top = (n_intercept - H) // 2
+    out = []
+    for ln in lines:
+        b = ln.b_c + ln.k * W / 2.0 - n_intercept / 2.0 + top
+        out.append(((b + n_intercept / 2.0) % n_intercept, (ln.k * n_slope / 2.0 + n_slope / 2.0) % n_slope))
+    return out
+
+
+def blob_targets(lines_list, side):
     from paper_1904_09409_gb300 import synth
-    return synth.batch_1024(BATCH, start=rank * BATCH, side=SIDE)
+    return np.stack([synth.blob_target(side, side, line_cells(ls, side, side, side, side)) for ls in lines_list])
+
+
+def time_fwd_bwd(f, plan, x, target, steps, stream, dev):
+    """Forward, loss mean((|P|/(W/2) - T)^2) with its gradient, adjoint: CUDA-event
+    time per step (ms) and per-kernel timing of the timed region."""
+    import torch
+    P = torch.empty((x.shape[0], plan.Hp, plan.S), dtype=torch.float32, device=dev)
+    dP = torch.empty_like(P)
+    loss = torch.empty(x.shape[0], dtype=torch.float32, device=dev)
+    gx = torch.empty_like(x)
+
+    def step():
+        f.ft_forward(plan, x, P, stream=stream)
+        f.ft_abs_mse_grad(plan, P, target, 2.0 / plan.W, loss=loss, grad=dP, stream=stream)
+        f.ft_backward(plan, dP, gx, stream=stream)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize(dev)
+    f.ft_profile_enable(plan, True)
+    f.ft_profile_read(plan)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    prof = f.ft_profile_read(plan)
+    f.ft_profile_enable(plan, False)
+    return e0.elapsed_time(e1) / steps, {k: v[0] / v[1] * 1e3 for k, v in prof.items()}
 
 
 def measured_peaks():
@@ -243,16 +299,15 @@ def run_ours(args):
     import torch
     from paper_1904_09409_gb300 import funnel as f
 
+    from paper_1904_09409_gb300 import replicas
     ws, rank, local = dist_info()
-    if ws > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local if ws > 1 else 0)
     torch.cuda.set_device(dev)
+    if ws > 1:
+        replicas.init("nccl", dev)
 
     # CPU baseline first (spawned pool, before any kernel of ours runs)
-    imgs = make_batch(rank)
+    imgs, lines = make_batch(rank, ws, with_lines=True)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(imgs)
@@ -278,9 +333,7 @@ def run_ours(args):
     time.sleep(0.5)
     f.ft_profile_enable(plan, True)
     f.ft_profile_read(plan)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    replicas.barrier()
     torch.cuda.synchronize(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -289,17 +342,13 @@ def run_ours(args):
         step()
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    if ws > 1:
-        dist.barrier()
+    replicas.barrier()
     ms = e0.elapsed_time(e1)
     clocks = sampler.stop()
     prof = f.ft_profile_read(plan)
     f.ft_profile_enable(plan, False)
 
-    if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replicas.max_over_ranks(ms, dev)
 
     # end to end through the public host-buffer call: H2D of the step's images
     # from pinned memory, forward + peaks, D2H of the peaks and counts
@@ -309,16 +358,27 @@ def run_ours(args):
     e2e_steps = max(3, min(args.steps, 30))
     for _ in range(2):
         f.ft_detect_host(plan, h_img, TOP_K, out_host=h_pk, count_host=h_cnt, stream=stream)
-    if ws > 1:
-        dist.barrier()
+    replicas.barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         f.ft_detect_host(plan, h_img, TOP_K, out_host=h_pk, count_host=h_cnt, stream=stream)
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = replicas.max_over_ranks(time.perf_counter() - t0, dev)
+
+    # forward + loss + adjoint on the same resident batch, and on 32 x 512^2
+    from paper_1904_09409_gb300 import synth
+    tgt = torch.from_numpy(blob_targets(lines, SIDE)).to(dev)
+    fb_steps = max(3, min(args.steps, 100))
+    fb_ms, fb_kernels = time_fwd_bwd(f, plan, x, tgt, fb_steps, stream, dev)
+    fb_ms = replicas.max_over_ranks(fb_ms, dev)
+    del tgt
+    g_imgs = synth.grad_batch_512(32, start=rank * 32)
+    plan512 = f.Plan(512, 512, 512, 512)
+    x512 = torch.from_numpy(np.stack([g.img for g in g_imgs])).to(dev)
+    t512 = torch.from_numpy(np.stack([synth.blob_target(512, 512, line_cells(g.lines, 512, 512, 512, 512))
+                                      for g in g_imgs])).to(dev)
+    fb512_ms, _ = time_fwd_bwd(f, plan512, x512, t512, fb_steps, stream, dev)
+    fb512_ms = replicas.max_over_ranks(fb512_ms, dev)
+    plan512.close()
 
     px_step = ws * BATCH * SIDE * SIDE
     value = args.steps * px_step / (ms / 1e3) / 1e6
@@ -358,13 +418,20 @@ def run_ours(args):
                     "h2d_bytes_per_step": ws * BATCH * SIDE * SIDE * 4,
                     "d2h_bytes_per_step": ws * (BATCH * TOP_K * f.PEAK_DTYPE.itemsize + BATCH * 4),
                     "call": "ft_detect_host", "steps": e2e_steps},
+            "fwd_bwd": {"value": px_step / (fb_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": fb_ms,
+                        "steps": fb_steps, "kernels_us": fb_kernels,
+                        "workload": "the same 64 x 1024^2 batch: ft_forward + ft_abs_mse_grad (loss "
+                                    "mean((|P|/(W/2) - T)^2), T Gaussian blobs of 2 cells at the drawn "
+                                    "lines) + ft_backward"},
+            "fwd_bwd_512": {"value": ws * 32 * 512 * 512 / (fb512_ms / 1e3) / 1e6, "unit": UNIT,
+                            "ms_per_step": fb512_ms, "steps": fb_steps,
+                            "workload": "32 x 512^2 gradient workload, same step"},
             "gpu_launches": args.steps * launches_per_step,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     plan.close()
-    if ws > 1:
-        dist.destroy_process_group()
+    replicas.finish()
     return 0
 
 

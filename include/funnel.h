@@ -110,6 +110,18 @@ ft_status ft_backward(ft_plan plan, const float* d_grad_map, float* d_grad_img, 
 ft_status ft_peaks(ft_plan plan, const float* d_map, int batch, int top_k, float threshold,
                    ft_peak* d_out, int32_t* d_count, void* stream);
 
+/* Loss for fitting by gradient through ft_backward (the paper fits nothing by
+ * gradient; this is the loss of the differentiable workload): with
+ * r = |d_map| * scale - d_target elementwise,
+ *   d_loss[b]     = mean over the H' x S cells of image b of r^2        ([batch], FP32)
+ *   d_grad_map    = d(mean of r^2 over all batch x H' x S cells) / d map
+ *                 = 2 r scale sign(map) / (batch H' S), sign(0) = 0
+ * d_target has the map's layout.  d_grad_map may be NULL (loss only).  The
+ * per-image sums are accumulated in a fixed order (FP32 with compensated
+ * summation), so repeated calls give identical results. */
+ft_status ft_abs_mse_grad(ft_plan plan, const float* d_map, const float* d_target, int batch, float scale,
+                          float* d_loss, float* d_grad_map, void* stream);
+
 /* End-to-end detection from host memory: copies h_img ([batch][H][W]) to a
  * plan-owned device buffer, runs ft_forward and ft_peaks, copies the peaks and
  * counts back to h_out ([batch][top_k]) and h_count ([batch]) and synchronises
@@ -158,7 +170,8 @@ typedef enum {
     FT_KERNEL_PEAK_TILES = 3,      /* Sec. 4.4, local maxima per tile */
     FT_KERNEL_PEAK_SELECT = 4,     /* Sec. 4.4, top_k per image */
     FT_KERNEL_NVMT_ROWS_ADJ = 5,   /* transpose of steps 2-3 */
-    FT_KERNEL_COUNT = 6
+    FT_KERNEL_LOSS = 6,            /* ft_abs_mse_grad */
+    FT_KERNEL_COUNT = 7
 } ft_kernel_id;
 
 /* Per-launch timing (a measurement aid, off by default).  While enabled, every

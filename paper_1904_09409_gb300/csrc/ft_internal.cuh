@@ -261,3 +261,9 @@ cudaError_t launch_peak_tiles(const float* map, int Hp, int S, int batch, int to
 cudaError_t launch_peak_select(const unsigned long long* keys, int Hp, int S, int batch, int top_k,
                                ft_peak* out, int32_t* count, cudaStream_t st);
 size_t peaks_key_bytes(int Hp, int S, int batch, int top_k);
+
+// Loss of the gradient workload and its gradient (k_loss.cu); partial needs
+// loss_partial_bytes(batch) bytes of scratch.
+cudaError_t launch_abs_mse_grad(const float* map, const float* target, int batch, size_t cells, float scale,
+                                float* loss, float* grad, float* partial, cudaStream_t st);
+size_t loss_partial_bytes(int batch);

@@ -345,6 +345,22 @@ ft_status ft_peaks(ft_plan p, const float* d_map, int batch, int top_k, float th
     return FT_OK;
 }
 
+ft_status ft_abs_mse_grad(ft_plan p, const float* d_map, const float* d_target, int batch, float scale,
+                          float* d_loss, float* d_grad_map, void* stream) {
+    if (!p || batch < 0 || batch > 65535) return FT_ERR_INVALID_ARG;
+    if (batch == 0) return FT_OK;
+    if (!d_map || !d_target || !d_loss) return FT_ERR_INVALID_ARG;
+    const size_t off = (spec_bytes(p, batch) + 255) & ~(size_t)255;
+    ft_status s = ensure(&p->d_ws, &p->ws_bytes, off + loss_partial_bytes(batch), "cudaMalloc(workspace)");
+    if (s != FT_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    FT_LAUNCH(p, FT_KERNEL_LOSS, st,
+              launch_abs_mse_grad(d_map, d_target, batch, (size_t)p->Hp * p->S, scale, d_loss, d_grad_map,
+                                  (float*)((char*)p->d_ws + off), st),
+              "loss");
+    return FT_OK;
+}
+
 ft_status ft_profile_enable(ft_plan p, int enable) {
     if (!p) return FT_ERR_INVALID_ARG;
     p->prof_on = enable ? 1 : 0;
@@ -386,6 +402,7 @@ const char* ft_kernel_name(int id) {
         case FT_KERNEL_PEAK_TILES: return "k_peak_tiles";
         case FT_KERNEL_PEAK_SELECT: return "k_peak_select";
         case FT_KERNEL_NVMT_ROWS_ADJ: return "k_nvmt_rows_adjoint";
+        case FT_KERNEL_LOSS: return "k_abs_mse_grad";
     }
     return "unknown";
 }

@@ -32,10 +32,10 @@ EXPORTED = (
     "ft_plan_create", "ft_plan_destroy", "ft_forward", "ft_backward", "ft_peaks",
     "ft_detect_host", "ft_workspace_bytes", "ft_forward_launches", "ft_peaks_launches",
     "ft_status_string", "ft_last_error", "ft_profile_enable", "ft_profile_read", "ft_kernel_name",
-    "ft_peaks_noalloc",
+    "ft_peaks_noalloc", "ft_abs_mse_grad",
 )
 FT_NOALLOC_SCRATCH_BYTES = 16 << 20
-FT_KERNEL_COUNT = 6
+FT_KERNEL_COUNT = 7
 
 
 class FtPeak(ctypes.Structure):
@@ -85,6 +85,8 @@ def lib() -> ctypes.CDLL:
     L.ft_kernel_name.argtypes = [ci]
     L.ft_kernel_name.restype = ctypes.c_char_p
     L.ft_peaks_noalloc.argtypes = [vp, ci, ci, ci, ci, cf, vp, vp, vp]
+    L.ft_abs_mse_grad.argtypes = [vp, vp, vp, ci, cf, vp, vp, vp]
+    L.ft_abs_mse_grad.restype = ci
     for name in ("ft_peaks_noalloc", "ft_profile_enable", "ft_profile_read", "ft_plan_create", "ft_plan_destroy", "ft_forward", "ft_backward", "ft_peaks",
                  "ft_detect_host", "ft_forward_launches", "ft_peaks_launches"):
         getattr(L, name).restype = ci
@@ -243,6 +245,24 @@ def ft_detect_host(plan: Plan, img_host, top_k: int, threshold: float = float("-
                                 out_host.data_ptr(), count_host.data_ptr(), _stream_ptr(stream)),
            "ft_detect_host")
     return out_host, count_host
+
+
+def ft_abs_mse_grad(plan: Plan, fmap, target, scale: float, loss=None, grad=None, stream=None):
+    """Per-image loss mean((|P| scale - T)^2) and the gradient of the batch mean
+    (pass grad=False for the loss only).  Returns (loss, grad)."""
+    import torch
+    b = fmap.shape[0]
+    n = b * plan.Hp * plan.S
+    mp = _dev_ptr(fmap, "float32", n, "map")
+    tp = _dev_ptr(target, "float32", n, "target")
+    if loss is None:
+        loss = torch.empty(b, dtype=torch.float32, device=fmap.device)
+    if grad is None:
+        grad = torch.empty_like(fmap)
+    gp = _dev_ptr(grad, "float32", n, "grad") if grad is not False else None
+    _check(lib().ft_abs_mse_grad(plan.handle, mp, tp, b, float(scale), _dev_ptr(loss, "float32", b, "loss"),
+                                 gp, _stream_ptr(stream)), "ft_abs_mse_grad")
+    return loss, (grad if grad is not False else None)
 
 
 def ft_workspace_bytes(plan: Plan, batch: int) -> int:

@@ -186,3 +186,16 @@ def varlen_shapes(count: int = 512) -> List[Tuple[int, int]]:
 
 def varlen_image(index: int, H: int, W: int) -> SynthImage:
     return mixed_image(WL_VARLEN, index, H, W)
+
+
+def blob_target(n_intercept: int, n_slope: int, cells, sigma: float = 2.0, amp: float = 1.0) -> np.ndarray:
+    """Target map of the gradient workload: Gaussian blobs (sigma in cells,
+    periodic in both axes) centred at the given (t, s) cells, summed."""
+    t = np.arange(n_intercept)[:, None]
+    s = np.arange(n_slope)[None, :]
+    out = np.zeros((n_intercept, n_slope), dtype=np.float64)
+    for (tc, sc) in cells:
+        dt = (t - tc + n_intercept / 2.0) % n_intercept - n_intercept / 2.0
+        ds = (s - sc + n_slope / 2.0) % n_slope - n_slope / 2.0
+        out += amp * np.exp(-(dt * dt + ds * ds) / (2.0 * sigma * sigma))
+    return out.astype(np.float32)

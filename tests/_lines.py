@@ -31,3 +31,15 @@ def ridge_image(H, W, n_intercept, lines, sigma=1.0, amp=1.0):
 def wrap_centred(v, period):
     """Wrap v into [-period/2, period/2)."""
     return (v + period / 2.0) % period - period / 2.0
+
+
+def true_cells(lines, H, W, n_slope, n_intercept):
+    """Map cells (t, s) where the drawn lines should peak: eqs. (22)-(23) with the
+    corner-to-centred conversion, slope and intercept wrapped into the map."""
+    cells = []
+    for ln in lines:
+        b = centred_intercept(ln.k, ln.b_c, H, W, n_intercept)
+        t = (b + n_intercept / 2.0) % n_intercept
+        s = (ln.k * n_slope / 2.0 + n_slope / 2.0) % n_slope
+        cells.append((t, s))
+    return cells
