@@ -86,6 +86,23 @@ typedef struct {
  * *out is set to NULL on failure. */
 ft_status ft_plan_create(ft_plan* out, int H, int W, int n_slope, int n_intercept, int interp);
 
+/* Parameter space of a plan (Sec. 4.1-4.3).  REGULAR: the funnel transform of
+ * Sec. 3.1 (slopes in (-1, 1], eqs. 22-23).  INVERSE: its dual form (Fourier
+ * transform along x, NVMT y' = (w1 / w_max) y, transform along y', inverse
+ * along w1), for slopes outside (-1, 1] (eqs. 24-25).  The inverse space is
+ * the regular transform of the transposed image: the map [n_intercept][n_slope]
+ * then has t = b_x + n_intercept/2 (x-intercept, centred) and
+ * s = n + n_slope/2 with 1/k = 2 n / n_slope; n_slope >= H and n_intercept >= W,
+ * H even; ft_peak.k holds 1/k and ft_peak.b holds b_x. */
+typedef enum {
+    FT_SPACE_REGULAR = 0,
+    FT_SPACE_INVERSE = 1
+} ft_space;
+
+/* ft_plan_create with an explicit space (ft_plan_create is the REGULAR case). */
+ft_status ft_plan_create_space(ft_plan* out, int H, int W, int n_slope, int n_intercept, int interp,
+                               int space);
+
 /* Release the plan's tables and workspace (synchronises the plan's device).
  * NULL is accepted. */
 ft_status ft_plan_destroy(ft_plan plan);

@@ -189,7 +189,9 @@ __device__ float2* cta_fft(float2* a, float2* b, const FftLen& L, int logB) {
 
 // -------------------------------------------------------------- plan object
 struct ft_plan_s {
-    int H, W, S, Hp, L, interp, top;
+    int H, W, S, Hp, L, interp, top;   // the transform's own sizes (transposed for the inverse space)
+    int space;              // FT_SPACE_REGULAR or FT_SPACE_INVERSE
+    int img_H, img_W;       // the caller's image sizes
     int device;
     FftLen fy;              // length H' (steps 1 and 4)
     FftLen fx;              // length S  (step 3)
@@ -261,6 +263,9 @@ cudaError_t launch_peak_tiles(const float* map, int Hp, int S, int batch, int to
 cudaError_t launch_peak_select(const unsigned long long* keys, int Hp, int S, int batch, int top_k,
                                ft_peak* out, int32_t* count, cudaStream_t st);
 size_t peaks_key_bytes(int Hp, int S, int batch, int top_k);
+
+// in[b][R][C] -> out[b][C][R] (k_transpose.cu)
+cudaError_t launch_transpose(const float* in, float* out, int R, int C, int batch, cudaStream_t st);
 
 // Loss of the gradient workload and its gradient (k_loss.cu); partial needs
 // loss_partial_bytes(batch) bytes of scratch.

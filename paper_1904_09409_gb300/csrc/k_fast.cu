@@ -167,10 +167,9 @@ k_col_c2r_fast(const float2* __restrict__ in, int ncols, int in_pitch, size_t in
 // alignment for cp.async and shifts successive rows by 4 banks
 __host__ __device__ constexpr int srow_pitch(int W) { return W + 2; }
 
-template <int N>
+template <int N, int INTERP>
 __global__ void __launch_bounds__(fs_T(N) * fs_Brow(N))
-k_nvmt_rows_fast(float2* __restrict__ ws, int W, int Hp, int L, int interp,
-                 const float2* __restrict__ stw) {
+k_nvmt_rows_fast(float2* __restrict__ ws, int W, int Hp, int L, const float2* __restrict__ stw) {
     constexpr int B = fs_Brow(N), E = fs_E(N), T = N / E;
     constexpr int R0 = fs_radix(N, 0), G0 = E / R0;
     constexpr int RL = fs_radix(N, fs_nst(N) - 1), GL = E / RL;
@@ -211,8 +210,7 @@ k_nvmt_rows_fast(float2* __restrict__ ws, int W, int Hp, int L, int interp,
         const int step = STEPX * Hp;
         const int sA = step / den, sB = step - sA * den;
         const int halfW = W >> 1;
-        const int dlo = interp == FT_INTERP_LINEAR ? 0 : -1;
-        const int dhi = interp == FT_INTERP_LINEAR ? 1 : 2;
+        const float2 zero = make_float2(0.f, 0.f);
 #pragma unroll
         for (int m = 0; m < G0; ++m) {
             const int i = t + m * T;
@@ -222,14 +220,20 @@ k_nvmt_rows_fast(float2* __restrict__ ws, int W, int Hp, int L, int interp,
 #pragma unroll
             for (int q = 0; q < R0; ++q) {
                 const float fr = (float)rem * inv;
-                float2 acc = make_float2(0.f, 0.f);
-                for (int d = dlo; d <= dhi; ++d) {
-                    const int col = qf + d + halfW;
-                    if (col >= 0 && col < W) {
-                        const float w = tap_weight(interp, d, fr);
-                        const float2 s = myrow[col];
-                        acc.x += w * s.x;
-                        acc.y += w * s.y;
+                const int c0 = qf + halfW;
+                float2 acc;
+                if constexpr (INTERP == FT_INTERP_LINEAR) {
+                    const float2 a0 = (unsigned)c0 < (unsigned)W ? myrow[c0] : zero;
+                    const float2 a1 = (unsigned)(c0 + 1) < (unsigned)W ? myrow[c0 + 1] : zero;
+                    acc = make_float2(fmaf(fr, a1.x - a0.x, a0.x), fmaf(fr, a1.y - a0.y, a0.y));
+                } else {
+                    acc = zero;
+#pragma unroll
+                    for (int d = -1; d <= 2; ++d) {
+                        const float2 a = (unsigned)(c0 + d) < (unsigned)W ? myrow[c0 + d] : zero;
+                        const float w = keys_w(fr - (float)d);
+                        acc.x = fmaf(w, a.x, acc.x);
+                        acc.y = fmaf(w, a.y, acc.y);
                     }
                 }
                 if ((i + q * STEPX) & 1) acc = make_float2(-acc.x, -acc.y);
@@ -254,10 +258,9 @@ k_nvmt_rows_fast(float2* __restrict__ ws, int W, int Hp, int L, int interp,
         }
 }
 
-template <int N>
+template <int N, int INTERP>
 __global__ void __launch_bounds__(fs_T(N) * fs_Brow(N))
-k_nvmt_rows_adjoint_fast(float2* __restrict__ ws, int W, int Hp, int L, int interp,
-                         const float2* __restrict__ stw) {
+k_nvmt_rows_adjoint_fast(float2* __restrict__ ws, int W, int Hp, int L, const float2* __restrict__ stw) {
     constexpr int B = fs_Brow(N), E = fs_E(N), T = N / E;
     constexpr int R0 = fs_radix(N, 0), G0 = E / R0;
     constexpr int RL = fs_radix(N, fs_nst(N) - 1), GL = E / RL;
@@ -291,25 +294,42 @@ k_nvmt_rows_adjoint_fast(float2* __restrict__ ws, int W, int Hp, int L, int inte
         }
     __syncthreads();
     if (l >= L) return;
+    // Column x receives from the sample x' with floor(x' H' / (2 l)) = x - W/2 - d
+    // (at most one, since H' >= 2 l), i.e. x' = ceil((x - W/2 - d) 2 l / H').  With
+    // num = (x - W/2 - d) 2 l + H' - 1 = x' H' + rem (0 <= rem < H') such an x'
+    // exists iff H' - 1 - rem < 2 l, and its fraction is (H' - 1 - rem) / (2 l).
+    // Successive columns of a thread differ by T, so (x', rem) are stepped exactly.
+    constexpr int DLO = INTERP == FT_INTERP_LINEAR ? 0 : -1;
+    constexpr int DHI = INTERP == FT_INTERP_LINEAR ? 1 : 2;
+    constexpr int ND = DHI - DLO + 1;
     const int halfW = W >> 1;
-    const int dlo = interp == FT_INTERP_LINEAR ? 0 : -1;
-    const int dhi = interp == FT_INTERP_LINEAR ? 1 : 2;
     const int den = 2 * l;
     const float inv = 1.f / (float)den;
+    const int step = T * den;
+    const int sA = step / Hp, sB = step - sA * Hp;
+    int xp[ND], rem[ND];
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+        const int num = (t - halfW - (DLO + j)) * den + Hp - 1;
+        xp[j] = floor_div(num, Hp);
+        rem[j] = num - xp[j] * Hp;
+    }
+    const int lim = Hp - 1 - den;                      // a sample exists iff rem > lim
     for (int x = t; x < W; x += T) {
         float2 acc = make_float2(0.f, 0.f);
         if (l >= 1) {
-            const int xc = x - halfW;
-            for (int d = dlo; d <= dhi; ++d) {
-                // the sample x' whose floor(x' H' / (2 l)) equals xc - d, if any
-                const int q = xc - d;
-                const int xp = ceil_div(q * den, Hp);
-                const int num = xp * Hp;
-                if (num >= (q + 1) * den || xp < -N / 2 || xp >= N / 2) continue;
-                const float w = tap_weight(interp, d, (float)(num - q * den) * inv);
-                const float2 g = sm[spos(xp + N / 2) * B + f];
-                acc.x += w * g.x;
-                acc.y += w * g.y;
+#pragma unroll
+            for (int j = 0; j < ND; ++j) {
+                if (rem[j] > lim && xp[j] >= -N / 2 && xp[j] < N / 2) {
+                    const float fr = (float)(Hp - 1 - rem[j]) * inv;
+                    const float w = INTERP == FT_INTERP_LINEAR ? (j == 0 ? 1.f - fr : fr) : keys_w(fr - (float)(DLO + j));
+                    const float2 g = sm[spos(xp[j] + N / 2) * B + f];
+                    acc.x = fmaf(w, g.x, acc.x);
+                    acc.y = fmaf(w, g.y, acc.y);
+                }
+                rem[j] += sB;
+                xp[j] += sA;
+                if (rem[j] >= Hp) { rem[j] -= Hp; xp[j] += 1; }
             }
         }
         row[x] = acc;
@@ -347,28 +367,40 @@ static cudaError_t go_c2r(const float2* in, int ncols, int in_pitch, size_t in_i
     return cudaGetLastError();
 }
 
+template <int N, int INTERP>
+static cudaError_t go_rows_i(float2* ws, int W, int Hp, int L, const float2* stw, int batch, cudaStream_t st) {
+    constexpr int B = fs_Brow(N);
+    const size_t sm = ((size_t)((FastFft<N, +1, B>::SLOTS + 1) & ~1) + (size_t)srow_pitch(W) * B) * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_nvmt_rows_fast<N, INTERP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid((L + B - 1) / B, batch);
+    k_nvmt_rows_fast<N, INTERP><<<grid, fs_T(N) * B, sm, st>>>(ws, W, Hp, L, stw);
+    return cudaGetLastError();
+}
+
 template <int N>
 static cudaError_t go_rows(float2* ws, int W, int Hp, int L, int interp, const float2* stw, int batch,
                            cudaStream_t st) {
+    return interp == FT_INTERP_LINEAR ? go_rows_i<N, FT_INTERP_LINEAR>(ws, W, Hp, L, stw, batch, st)
+                                      : go_rows_i<N, FT_INTERP_CUBIC>(ws, W, Hp, L, stw, batch, st);
+}
+
+template <int N, int INTERP>
+static cudaError_t go_rows_adj_i(float2* ws, int W, int Hp, int L, const float2* stw, int batch, cudaStream_t st) {
     constexpr int B = fs_Brow(N);
-    const size_t sm = ((size_t)((FastFft<N, +1, B>::SLOTS + 1) & ~1) + (size_t)srow_pitch(W) * B) * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(k_nvmt_rows_fast<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const size_t sm = (size_t)FastFft<N, -1, B>::SLOTS * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_nvmt_rows_adjoint_fast<N, INTERP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     dim3 grid((L + B - 1) / B, batch);
-    k_nvmt_rows_fast<N><<<grid, fs_T(N) * B, sm, st>>>(ws, W, Hp, L, interp, stw);
+    k_nvmt_rows_adjoint_fast<N, INTERP><<<grid, fs_T(N) * B, sm, st>>>(ws, W, Hp, L, stw);
     return cudaGetLastError();
 }
 
 template <int N>
 static cudaError_t go_rows_adj(float2* ws, int W, int Hp, int L, int interp, const float2* stw, int batch,
                                cudaStream_t st) {
-    constexpr int B = fs_Brow(N);
-    const size_t sm = (size_t)FastFft<N, -1, B>::SLOTS * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(k_nvmt_rows_adjoint_fast<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    dim3 grid((L + B - 1) / B, batch);
-    k_nvmt_rows_adjoint_fast<N><<<grid, fs_T(N) * B, sm, st>>>(ws, W, Hp, L, interp, stw);
-    return cudaGetLastError();
+    return interp == FT_INTERP_LINEAR ? go_rows_adj_i<N, FT_INTERP_LINEAR>(ws, W, Hp, L, stw, batch, st)
+                                      : go_rows_adj_i<N, FT_INTERP_CUBIC>(ws, W, Hp, L, stw, batch, st);
 }
 
 cudaError_t launch_col_r2c_fast(const float* in, int rows_in, int ncols, int in_pitch, size_t in_img,

@@ -146,6 +146,13 @@ static ft_status ensure(void** ptr, size_t* have, size_t need, const char* what)
 }
 
 static size_t spec_bytes(ft_plan p, int batch) { return (size_t)batch * p->L * p->S * sizeof(float2); }
+static size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
+// workspace: [half spectra][transposed image (inverse space only)][aux: peak keys or loss partials]
+static size_t tposed_off(ft_plan p, int batch) { return al256(spec_bytes(p, batch)); }
+static size_t tposed_bytes(ft_plan p, int batch) {
+    return p->space == FT_SPACE_INVERSE ? al256((size_t)batch * p->H * p->W * sizeof(float)) : 0;
+}
+static size_t aux_off(ft_plan p, int batch) { return tposed_off(p, batch) + tposed_bytes(p, batch); }
 
 // Fixed-length kernels where the length has a schedule, generic ones otherwise.
 static cudaError_t col_r2c(ft_plan p, const float* in, int rows_in, int ncols, int in_pitch,
@@ -197,9 +204,18 @@ const char* ft_status_string(ft_status s) {
 const char* ft_last_error(void) { return g_last_error; }
 
 ft_status ft_plan_create(ft_plan* out, int H, int W, int n_slope, int n_intercept, int interp) {
+    return ft_plan_create_space(out, H, W, n_slope, n_intercept, interp, FT_SPACE_REGULAR);
+}
+
+ft_status ft_plan_create_space(ft_plan* out, int img_H, int img_W, int n_slope, int n_intercept, int interp,
+                               int space) {
     if (!out) return FT_ERR_INVALID_ARG;
     *out = nullptr;
     if (interp != FT_INTERP_LINEAR && interp != FT_INTERP_CUBIC) return FT_ERR_INVALID_ARG;
+    if (space != FT_SPACE_REGULAR && space != FT_SPACE_INVERSE) return FT_ERR_INVALID_ARG;
+    // the inverse space is the regular transform of the transposed image
+    const int H = space == FT_SPACE_INVERSE ? img_W : img_H;
+    const int W = space == FT_SPACE_INVERSE ? img_H : img_W;
     if (H < 1 || W < 2 || (W & 1) || n_slope < W || n_intercept < H) return FT_ERR_UNSUPPORTED_SIZE;
     FftLen fy = {}, fx = {};
     if (!factorize(n_intercept, &fy) || !factorize(n_slope, &fx)) return FT_ERR_UNSUPPORTED_SIZE;
@@ -208,6 +224,9 @@ ft_status ft_plan_create(ft_plan* out, int H, int W, int n_slope, int n_intercep
     if (!p) return FT_ERR_OOM;
     p->H = H;
     p->W = W;
+    p->space = space;
+    p->img_H = img_H;
+    p->img_W = img_W;
     p->S = n_slope;
     p->Hp = n_intercept;
     p->L = n_intercept / 2 + 1;
@@ -275,23 +294,28 @@ ft_status ft_plan_destroy(ft_plan p) {
 
 size_t ft_workspace_bytes(ft_plan p, int batch) {
     if (!p || batch <= 0) return 0;
-    return spec_bytes(p, batch);
+    return aux_off(p, batch);
 }
 
-int ft_forward_launches(ft_plan p) { return p ? 3 : 0; }
+int ft_forward_launches(ft_plan p) { return p ? (p->space == FT_SPACE_INVERSE ? 4 : 3) : 0; }
 int ft_peaks_launches(ft_plan p) { return p ? 2 : 0; }
 
 ft_status ft_forward(ft_plan p, const float* d_img, float* d_map, int batch, void* stream) {
     if (!p || batch < 0 || batch > 65535) return FT_ERR_INVALID_ARG;
     if (batch == 0) return FT_OK;
     if (!d_img || !d_map || ((uintptr_t)d_img & 7) || ((uintptr_t)d_map & 7)) return FT_ERR_INVALID_ARG;
-    ft_status s = ensure(&p->d_ws, &p->ws_bytes, spec_bytes(p, batch), "cudaMalloc(workspace)");
+    ft_status s = ensure(&p->d_ws, &p->ws_bytes, aux_off(p, batch), "cudaMalloc(workspace)");
     if (s != FT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     float2* ws = (float2*)p->d_ws;
-    const size_t ws_img = (size_t)p->L * p->S;
+    const float* src = d_img;
+    if (p->space == FT_SPACE_INVERSE) {
+        float* tp = (float*)((char*)p->d_ws + tposed_off(p, batch));
+        FT_CUDA(launch_transpose(d_img, tp, p->img_H, p->img_W, batch, st), "transpose (inverse space)");
+        src = tp;
+    }
     FT_LAUNCH(p, FT_KERNEL_COL_R2C, st,
-              col_r2c(p, d_img, p->H, p->W, p->W, (size_t)p->H * p->W, p->top, ws, 1.f, 1.f, batch, st),
+              col_r2c(p, src, p->H, p->W, p->W, (size_t)p->H * p->W, p->top, ws, 1.f, 1.f, batch, st),
               "step 1 (column R2C)");
     FT_LAUNCH(p, FT_KERNEL_NVMT_ROWS, st, nvmt_rows(p, ws, batch, st), "steps 2-3 (NVMT + row FFT)");
     FT_LAUNCH(p, FT_KERNEL_COL_C2R, st,
@@ -306,19 +330,22 @@ ft_status ft_backward(ft_plan p, const float* d_grad_map, float* d_grad_img, int
     if (batch == 0) return FT_OK;
     if (!d_grad_map || !d_grad_img || ((uintptr_t)d_grad_map & 7) || ((uintptr_t)d_grad_img & 7))
         return FT_ERR_INVALID_ARG;
-    ft_status s = ensure(&p->d_ws, &p->ws_bytes, spec_bytes(p, batch), "cudaMalloc(workspace)");
+    ft_status s = ensure(&p->d_ws, &p->ws_bytes, aux_off(p, batch), "cudaMalloc(workspace)");
     if (s != FT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     float2* ws = (float2*)p->d_ws;
-    const size_t ws_img = (size_t)p->L * p->S;
     const float inv = 1.f / (float)p->Hp;
+    float* gdst = d_grad_img;
+    if (p->space == FT_SPACE_INVERSE) gdst = (float*)((char*)p->d_ws + tposed_off(p, batch));
     FT_LAUNCH(p, FT_KERNEL_COL_R2C, st,
               col_r2c(p, d_grad_map, p->Hp, p->S, p->S, (size_t)p->Hp * p->S, 0, ws, inv, 2.f * inv, batch, st),
               "adjoint of step 4");
     FT_LAUNCH(p, FT_KERNEL_NVMT_ROWS_ADJ, st, nvmt_rows_adj(p, ws, batch, st), "adjoint of steps 2-3");
     FT_LAUNCH(p, FT_KERNEL_COL_C2R, st,
-              col_c2r(p, ws, p->W, 0.5f, d_grad_img, p->top, p->H, p->W, (size_t)p->H * p->W, 1.f, batch, st),
+              col_c2r(p, ws, p->W, 0.5f, gdst, p->top, p->H, p->W, (size_t)p->H * p->W, 1.f, batch, st),
               "adjoint of step 1");
+    if (p->space == FT_SPACE_INVERSE)
+        FT_CUDA(launch_transpose(gdst, d_grad_img, p->H, p->W, batch, st), "transpose back (inverse space)");
     return FT_OK;
 }
 
@@ -329,9 +356,8 @@ ft_status ft_peaks(ft_plan p, const float* d_map, int batch, int top_k, float th
     if (batch == 0) return FT_OK;
     if (!d_map || !d_out || !d_count) return FT_ERR_INVALID_ARG;
     // the key buffer lives after the spectrum workspace of this batch
-    const size_t spec = spec_bytes(p, batch);
     const size_t keys = peaks_key_bytes(p->Hp, p->S, batch, top_k);
-    const size_t off = (spec + 255) & ~(size_t)255;
+    const size_t off = aux_off(p, batch);
     ft_status s = ensure(&p->d_ws, &p->ws_bytes, off + keys, "cudaMalloc(workspace)");
     if (s != FT_OK) return s;
     unsigned long long* kbuf = (unsigned long long*)((char*)p->d_ws + off);
@@ -350,7 +376,7 @@ ft_status ft_abs_mse_grad(ft_plan p, const float* d_map, const float* d_target, 
     if (!p || batch < 0 || batch > 65535) return FT_ERR_INVALID_ARG;
     if (batch == 0) return FT_OK;
     if (!d_map || !d_target || !d_loss) return FT_ERR_INVALID_ARG;
-    const size_t off = (spec_bytes(p, batch) + 255) & ~(size_t)255;
+    const size_t off = aux_off(p, batch);
     ft_status s = ensure(&p->d_ws, &p->ws_bytes, off + loss_partial_bytes(batch), "cudaMalloc(workspace)");
     if (s != FT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
@@ -412,7 +438,7 @@ ft_status ft_detect_host(ft_plan p, const float* h_img, int batch, int top_k, fl
     if (!p || batch < 0 || batch > 65535 || top_k < 1 || top_k > FT_MAX_TOPK) return FT_ERR_INVALID_ARG;
     if (batch == 0) return FT_OK;
     if (!h_img || !h_out || !h_count) return FT_ERR_INVALID_ARG;
-    const size_t img_b = (size_t)batch * p->H * p->W * sizeof(float);
+    const size_t img_b = (size_t)batch * p->img_H * p->img_W * sizeof(float);
     const size_t map_b = (size_t)batch * p->Hp * p->S * sizeof(float);
     const size_t pk_b = (size_t)batch * top_k * sizeof(ft_peak);
     const size_t cnt_off = (pk_b + 255) & ~(size_t)255;

@@ -32,8 +32,11 @@ EXPORTED = (
     "ft_plan_create", "ft_plan_destroy", "ft_forward", "ft_backward", "ft_peaks",
     "ft_detect_host", "ft_workspace_bytes", "ft_forward_launches", "ft_peaks_launches",
     "ft_status_string", "ft_last_error", "ft_profile_enable", "ft_profile_read", "ft_kernel_name",
-    "ft_peaks_noalloc", "ft_abs_mse_grad",
+    "ft_peaks_noalloc", "ft_abs_mse_grad", "ft_plan_create_space",
 )
+FT_SPACE_REGULAR = 0
+FT_SPACE_INVERSE = 1
+SPACE_NAMES = {"regular": FT_SPACE_REGULAR, "inverse": FT_SPACE_INVERSE}
 FT_NOALLOC_SCRATCH_BYTES = 16 << 20
 FT_KERNEL_COUNT = 7
 
@@ -67,6 +70,8 @@ def lib() -> ctypes.CDLL:
     L = ctypes.CDLL(LIB_PATH)
     vp, ci, cf = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
     L.ft_plan_create.argtypes = [ctypes.POINTER(vp), ci, ci, ci, ci, ci]
+    L.ft_plan_create_space.argtypes = [ctypes.POINTER(vp), ci, ci, ci, ci, ci, ci]
+    L.ft_plan_create_space.restype = ci
     L.ft_plan_destroy.argtypes = [vp]
     L.ft_forward.argtypes = [vp, vp, vp, ci, vp]
     L.ft_backward.argtypes = [vp, vp, vp, ci, vp]
@@ -123,15 +128,19 @@ def _dev_ptr(t, dtype_name: str, numel: int, what: str) -> int:
 
 
 class Plan:
-    """Owns an ft_plan handle; sizes as in ft_plan_create."""
+    """Owns an ft_plan handle; sizes as in ft_plan_create_space.  H, W are the
+    image's sizes; the map is (n_intercept, n_slope), by default (H, W) for the
+    regular space and (W, H) for the inverse space."""
 
     def __init__(self, H: int, W: int, n_slope: Optional[int] = None,
-                 n_intercept: Optional[int] = None, interp="linear"):
+                 n_intercept: Optional[int] = None, interp="linear", space="regular"):
         self.H, self.W = int(H), int(W)
-        self.S = self.W if n_slope is None else int(n_slope)
-        self.Hp = self.H if n_intercept is None else int(n_intercept)
+        self.space = SPACE_NAMES[space] if isinstance(space, str) else int(space)
+        inv = self.space == FT_SPACE_INVERSE
+        self.S = (self.H if inv else self.W) if n_slope is None else int(n_slope)
+        self.Hp = (self.W if inv else self.H) if n_intercept is None else int(n_intercept)
         self.interp = INTERP_NAMES[interp] if isinstance(interp, str) else int(interp)
-        self.handle = ft_plan_create(self.H, self.W, self.S, self.Hp, self.interp)
+        self.handle = ft_plan_create_space(self.H, self.W, self.S, self.Hp, self.interp, self.space)
 
     def close(self):
         if self.handle:
@@ -160,6 +169,14 @@ def ft_plan_create(H: int, W: int, n_slope: int, n_intercept: int, interp: int =
     h = ctypes.c_void_p()
     _check(lib().ft_plan_create(ctypes.byref(h), int(H), int(W), int(n_slope), int(n_intercept),
                                 int(interp)), "ft_plan_create")
+    return h
+
+
+def ft_plan_create_space(H: int, W: int, n_slope: int, n_intercept: int, interp: int = FT_INTERP_LINEAR,
+                         space: int = FT_SPACE_REGULAR):
+    h = ctypes.c_void_p()
+    _check(lib().ft_plan_create_space(ctypes.byref(h), int(H), int(W), int(n_slope), int(n_intercept),
+                                      int(interp), int(space)), "ft_plan_create_space")
     return h
 
 

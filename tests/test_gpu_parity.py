@@ -202,3 +202,45 @@ def test_generic_path_matches_oracle(torch, monkeypatch, H, W, S, Hp, interp):
     for i in range(2):
         assert _gpu.rel_l2(got[i], oracle.funnel_ref(imgs[i], S, Hp, interp)) <= TOL_MAP
         assert _gpu.rel_l2(gi[i], oracle.adjoint_ref(g[i].astype(np.float64), H, W, interp)) <= TOL_MAP
+
+
+# ------------------------------------------------------------ inverse space
+@pytest.mark.parametrize("H,W,S,Hp,interp", [(64, 48, 64, 96, "linear"), (256, 256, 256, 256, "linear"),
+                                             (100, 96, 128, 192, "cubic")])
+def test_inverse_space_matches_oracle(torch, H, W, S, Hp, interp):
+    """The dual transform of Sec. 3.1 (eqs. 24-25): the oracle's inverse_funnel_ref."""
+    from paper_1904_09409_gb300 import funnel as f
+    imgs = inputs(H, W, 2, seed=H + 1)
+    rng = np.random.default_rng(11)
+    g = rng.standard_normal((2, Hp, S)).astype(np.float32)
+    with f.Plan(H, W, S, Hp, interp, space="inverse") as plan:
+        got = _gpu.forward(plan, imgs)
+        gi = _gpu.backward(plan, g)
+    for i in range(2):
+        ref = oracle.inverse_funnel_ref(imgs[i], S, Hp, interp)
+        assert _gpu.rel_l2(got[i], ref) <= TOL_MAP
+        # the adjoint of the inverse space is the transposed regular adjoint
+        ref_adj = oracle.adjoint_ref(g[i].astype(np.float64), W, H, interp).T
+        assert _gpu.rel_l2(gi[i], ref_adj) <= TOL_MAP
+
+
+def test_fig9_inverse_peak_on_gpu(torch):
+    """Fig. 9: slope 3.27 in a 170 x 428 image; the inverse space recovers it at
+    (b_x, n) = (18, 65).  n_slope = 428 = 4 * 107 is not 2^a 3^b, so the map uses
+    432 = 16 * 27 slope cells and the printed cell scales to 65 * 432 / 428."""
+    import json
+    import os
+    from paper_1904_09409_gb300 import funnel as f
+    from tests._lines import ridge_image
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "fig9_wrapped_peak.json")))
+    W, H, k = g["width_M"], g["height_N"], g["slope_k"]
+    img = ridge_image(H, W, W + H, [(k, float(g["regular_peak_mn"][1]))])[None].astype(np.float32)
+    S, Hp = 432, 648                             # >= 428 and >= 170 + 428, both 2^a 3^b
+    with f.Plan(H, W, S, Hp, space="inverse") as plan:
+        m = _gpu.forward(plan, img)
+        _, recs = _gpu.peaks(plan, m, 1)
+    inv_k, b_x = float(recs[0]["k"][0]), float(recs[0]["b"][0])
+    assert abs(b_x - g["inverse_peak_mn"][0]) <= g["tolerance_cells"]
+    assert abs(1.0 / inv_k - k) < 0.1
+    ref = oracle.inverse_funnel_ref(img[0], S, Hp)
+    assert _gpu.rel_l2(m[0], ref) <= TOL_MAP
