@@ -172,6 +172,55 @@ ft_status ft_detect_host(ft_plan plan, const float* h_img, int batch, int top_k,
 ft_status ft_peaks_noalloc(const float* d_map, int n_intercept, int n_slope, int batch, int top_k,
                            float threshold, ft_peak* d_out, int32_t* d_count, void* stream);
 
+/* Kernel variants of a plan, the autotuner's knob (results are identical up to
+ * FP32 rounding order): 0 = the fixed-length register-resident kernels where
+ * the length has a schedule (the default), generic shared-memory kernels
+ * elsewhere; 1..4 = the generic kernels everywhere with the largest column /
+ * row blocks (1), half-size column blocks (2), half-size row blocks (3), both
+ * halved (4).  FT_FORCE_GENERIC=1 in the environment at plan creation selects 1. */
+int ft_plan_variant_count(ft_plan plan);
+ft_status ft_plan_set_variant(ft_plan plan, int variant);
+int ft_plan_get_variant(ft_plan plan);
+
+/* ------------------------------------------------------------------------
+ * Mixed-size batches (the paper's Sec. I remark that rows and columns are
+ * independent, taken across images of uneven sizes).  A batch of n images of
+ * sizes H[i] x W[i] (maps n_intercept = H[i], n_slope = W[i]) groups equal shapes
+ * and keeps one plan per shape.  It fixes a packed layout: the caller stores
+ * the images back to back in the order ft_batch_layout reports (order[j] = the
+ * caller's index of packed image j, img_off[j] / map_off[j] = its element
+ * offset in the packed image / map buffers, totals = {image elements, map
+ * elements}); peaks are written as [n][top_k] rows and counts as [n] in the same
+ * packed order.  Equal shapes are contiguous, largest first.
+ *
+ * ft_batch_run enqueues every group's ft_forward (and ft_peaks when top_k > 0)
+ * on up to 8 side streams forked from and joined back into `stream`.
+ *   FT_BATCH_GRAPH: capture that sequence once into a CUDA graph (after an
+ *     uncaptured run that allocates every workspace and synchronises `stream`)
+ *     and replay it while all arguments stay the same; `stream` must not be the
+ *     legacy default stream.
+ *   FT_BATCH_TUNE: before running, time every kernel variant of every group's
+ *     plan (ft_plan_set_variant) on the caller's buffers (synchronous) and keep
+ *     the fastest; with a tune_cache path the choices are merged into that JSON
+ *     file (keys "GPU name|HxW|interp") and ft_batch_create applies cached choices.
+ * The batch owns its plans, streams and graph; one batch may be used by one host
+ * thread at a time. */
+typedef struct ft_batch_s* ft_batch;
+#define FT_BATCH_GRAPH 1
+#define FT_BATCH_TUNE 2
+ft_status ft_batch_create(ft_batch* out, int n, const int32_t* H, const int32_t* W, int interp,
+                          const char* tune_cache);
+ft_status ft_batch_destroy(ft_batch batch);
+ft_status ft_batch_layout(ft_batch batch, int32_t* order, int64_t* img_off, int64_t* map_off,
+                          int64_t* totals);
+int ft_batch_group_count(ft_batch batch);
+/* info = {H, W, first packed position, count, variant} of group g */
+ft_status ft_batch_group_info(ft_batch batch, int g, int32_t* info);
+/* mean ms of one tuned forward (+ peaks) of group g alone, -1 before tuning */
+float ft_batch_group_tuned_ms(ft_batch batch, int g);
+ft_status ft_batch_run(ft_batch batch, const float* d_imgs, float* d_maps, int top_k, float threshold,
+                       ft_peak* d_out, int32_t* d_count, void* stream, int flags);
+
 /* Bytes of plan-owned device workspace that a call with this batch needs. */
 size_t ft_workspace_bytes(ft_plan plan, int batch);
 

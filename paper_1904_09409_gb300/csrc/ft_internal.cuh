@@ -208,8 +208,11 @@ struct ft_plan_s {
     int32_t* d_count_host;
     size_t peaks_host_bytes;
     // launch shapes
-    int col_logB_y;         // transforms per CTA (log2) for length H'
-    int row_logB_x;         // rows per CTA (log2) for length S
+    int col_logB_y;         // transforms per CTA (log2) for length H' (generic kernels)
+    int row_logB_x;         // rows per CTA (log2) for length S (generic kernels)
+    int col_logB_max, row_logB_max;  // the largest that fit the shared-memory budget
+    int use_fast_y, use_fast_x;      // fixed-length kernels in use for H' / S
+    int variant;            // see ft_plan_set_variant
     // per-launch timing (ft_profile_enable / ft_profile_read)
     int prof_on;
     size_t prof_used;

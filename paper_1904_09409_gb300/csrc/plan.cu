@@ -159,7 +159,7 @@ static cudaError_t col_r2c(ft_plan p, const float* in, int rows_in, int ncols, i
                            size_t in_img, int row0, float2* out, float es, float ms, int batch,
                            cudaStream_t st) {
     const size_t out_img = (size_t)p->L * p->S;
-    if (p->fy.stw)
+    if (p->use_fast_y)
         return launch_col_r2c_fast(in, rows_in, ncols, in_pitch, in_img, row0, p->fy, out, p->S, out_img,
                                    es, ms, batch, st);
     return launch_col_r2c(in, rows_in, ncols, in_pitch, in_img, row0, p->fy, p->col_logB_y, out, p->S,
@@ -170,7 +170,7 @@ static cudaError_t col_c2r(ft_plan p, const float2* in, int ncols, float mid, fl
                            int rows_out, int out_pitch, size_t out_img, float os, int batch,
                            cudaStream_t st) {
     const size_t in_img = (size_t)p->L * p->S;
-    if (p->fy.stw)
+    if (p->use_fast_y)
         return launch_col_c2r_fast(in, ncols, p->S, in_img, p->fy, mid, out, row0, rows_out, out_pitch,
                                    out_img, os, batch, st);
     return launch_col_c2r(in, ncols, p->S, in_img, p->fy, p->col_logB_y, mid, out, row0, rows_out,
@@ -178,12 +178,12 @@ static cudaError_t col_c2r(ft_plan p, const float2* in, int ncols, float mid, fl
 }
 
 static cudaError_t nvmt_rows(ft_plan p, float2* ws, int batch, cudaStream_t st) {
-    if (p->fx.stw) return launch_nvmt_rows_fast(ws, p->W, p->Hp, p->L, p->interp, p->fx, batch, st);
+    if (p->use_fast_x) return launch_nvmt_rows_fast(ws, p->W, p->Hp, p->L, p->interp, p->fx, batch, st);
     return launch_nvmt_rows(ws, p->W, p->S, p->Hp, p->L, p->interp, p->fx, p->row_logB_x, batch, st);
 }
 
 static cudaError_t nvmt_rows_adj(ft_plan p, float2* ws, int batch, cudaStream_t st) {
-    if (p->fx.stw) return launch_nvmt_rows_adjoint_fast(ws, p->W, p->Hp, p->L, p->interp, p->fx, batch, st);
+    if (p->use_fast_x) return launch_nvmt_rows_adjoint_fast(ws, p->W, p->Hp, p->L, p->interp, p->fx, batch, st);
     return launch_nvmt_rows_adjoint(ws, p->W, p->S, p->Hp, p->L, p->interp, p->fx, p->row_logB_x, batch, st);
 }
 
@@ -241,7 +241,7 @@ ft_status ft_plan_create_space(ft_plan* out, int img_H, int img_W, int n_slope, 
     }
     const char* force = getenv("FT_FORCE_GENERIC");
     const bool generic = force && force[0] == '1';
-    const bool fast_y = !generic && fs_has(fy.N), fast_x = !generic && fs_has(fx.N);
+    const bool fast_y = fs_has(fy.N), fast_x = fs_has(fx.N);
     const size_t sy = fast_y ? fs_twsize(fy.N) : 0, sx = fast_x ? fs_twsize(fx.N) : 0;
     std::vector<float2> tw((size_t)fy.N + fx.N + sy + sx);
     twiddles(fy.N, tw.data());
@@ -271,6 +271,11 @@ ft_status ft_plan_create_space(ft_plan* out, int img_H, int img_W, int n_slope, 
     const int rcap = 96 * 1024 / (int)sizeof(float2) / (W + 2 * n_slope);
     p->row_logB_x = log2_floor(rcap > 0 ? rcap : 1);
     if (p->row_logB_x > 4) p->row_logB_x = 4;
+    p->col_logB_max = p->col_logB_y;
+    p->row_logB_max = p->row_logB_x;
+    p->use_fast_y = fast_y && !generic;
+    p->use_fast_x = fast_x && !generic;
+    p->variant = generic ? 1 : 0;
     *out = p;
     return FT_OK;
 }
@@ -291,6 +296,29 @@ ft_status ft_plan_destroy(ft_plan p) {
     delete p;
     return FT_OK;
 }
+
+int ft_plan_variant_count(ft_plan p) { return p ? 5 : 0; }
+
+ft_status ft_plan_set_variant(ft_plan p, int variant) {
+    if (!p || variant < 0 || variant > 4) return FT_ERR_INVALID_ARG;
+    const bool fy = p->fy.stw != nullptr, fx = p->fx.stw != nullptr;
+    if (variant == 0) {
+        p->use_fast_y = fy;
+        p->use_fast_x = fx;
+        p->col_logB_y = p->col_logB_max;
+        p->row_logB_x = p->row_logB_max;
+    } else {
+        const int v = variant - 1;              // generic kernels, 1 or 2x fewer transforms per block
+        p->use_fast_y = 0;
+        p->use_fast_x = 0;
+        p->col_logB_y = p->col_logB_max - ((v & 1) && p->col_logB_max > 0 ? 1 : 0);
+        p->row_logB_x = p->row_logB_max - ((v & 2) && p->row_logB_max > 0 ? 1 : 0);
+    }
+    p->variant = variant;
+    return FT_OK;
+}
+
+int ft_plan_get_variant(ft_plan p) { return p ? p->variant : -1; }
 
 size_t ft_workspace_bytes(ft_plan p, int batch) {
     if (!p || batch <= 0) return 0;

@@ -33,7 +33,12 @@ EXPORTED = (
     "ft_detect_host", "ft_workspace_bytes", "ft_forward_launches", "ft_peaks_launches",
     "ft_status_string", "ft_last_error", "ft_profile_enable", "ft_profile_read", "ft_kernel_name",
     "ft_peaks_noalloc", "ft_abs_mse_grad", "ft_plan_create_space",
+    "ft_plan_variant_count", "ft_plan_set_variant", "ft_plan_get_variant",
+    "ft_batch_create", "ft_batch_destroy", "ft_batch_layout", "ft_batch_group_count",
+    "ft_batch_group_info", "ft_batch_group_tuned_ms", "ft_batch_run",
 )
+FT_BATCH_GRAPH = 1
+FT_BATCH_TUNE = 2
 FT_SPACE_REGULAR = 0
 FT_SPACE_INVERSE = 1
 SPACE_NAMES = {"regular": FT_SPACE_REGULAR, "inverse": FT_SPACE_INVERSE}
@@ -92,6 +97,21 @@ def lib() -> ctypes.CDLL:
     L.ft_peaks_noalloc.argtypes = [vp, ci, ci, ci, ci, cf, vp, vp, vp]
     L.ft_abs_mse_grad.argtypes = [vp, vp, vp, ci, cf, vp, vp, vp]
     L.ft_abs_mse_grad.restype = ci
+    L.ft_plan_variant_count.argtypes = [vp]
+    L.ft_plan_set_variant.argtypes = [vp, ci]
+    L.ft_plan_get_variant.argtypes = [vp]
+    L.ft_batch_create.argtypes = [ctypes.POINTER(vp), ci, vp, vp, ci, ctypes.c_char_p]
+    L.ft_batch_destroy.argtypes = [vp]
+    L.ft_batch_layout.argtypes = [vp, vp, vp, vp, vp]
+    L.ft_batch_group_count.argtypes = [vp]
+    L.ft_batch_group_info.argtypes = [vp, ci, vp]
+    L.ft_batch_group_tuned_ms.argtypes = [vp, ci]
+    L.ft_batch_group_tuned_ms.restype = cf
+    L.ft_batch_run.argtypes = [vp, vp, vp, ci, cf, vp, vp, vp, ci]
+    for name in ("ft_plan_variant_count", "ft_plan_set_variant", "ft_plan_get_variant", "ft_batch_create",
+                 "ft_batch_destroy", "ft_batch_layout", "ft_batch_group_count", "ft_batch_group_info",
+                 "ft_batch_run"):
+        getattr(L, name).restype = ci
     for name in ("ft_peaks_noalloc", "ft_profile_enable", "ft_profile_read", "ft_plan_create", "ft_plan_destroy", "ft_forward", "ft_backward", "ft_peaks",
                  "ft_detect_host", "ft_forward_launches", "ft_peaks_launches"):
         getattr(L, name).restype = ci
@@ -317,6 +337,94 @@ def ft_status_string(status: int) -> str:
 
 def ft_last_error() -> str:
     return lib().ft_last_error().decode()
+
+
+def ft_plan_set_variant(plan: Plan, variant: int) -> None:
+    _check(lib().ft_plan_set_variant(plan.handle, int(variant)), "ft_plan_set_variant")
+
+
+def ft_plan_get_variant(plan: Plan) -> int:
+    return int(lib().ft_plan_get_variant(plan.handle))
+
+
+class Batch:
+    """A mixed-size batch (ft_batch_*): shapes is a list of (H, W); maps are
+    n_intercept = H, n_slope = W.  Images, maps and peak rows live in one packed
+    buffer each, in the batch's packed order (``order[j]`` = caller index)."""
+
+    def __init__(self, shapes, interp="linear", tune_cache: Optional[str] = None):
+        self.shapes = [(int(h), int(w)) for h, w in shapes]
+        n = len(self.shapes)
+        H = (ctypes.c_int32 * n)(*[h for h, _ in self.shapes])
+        W = (ctypes.c_int32 * n)(*[w for _, w in self.shapes])
+        h = ctypes.c_void_p()
+        ip = INTERP_NAMES[interp] if isinstance(interp, str) else int(interp)
+        _check(lib().ft_batch_create(ctypes.byref(h), n, ctypes.cast(H, ctypes.c_void_p),
+                                     ctypes.cast(W, ctypes.c_void_p), ip,
+                                     tune_cache.encode() if tune_cache else None), "ft_batch_create")
+        self.handle = h
+        self.n = n
+        order = np.zeros(n, np.int32)
+        ioff = np.zeros(n, np.int64)
+        moff = np.zeros(n, np.int64)
+        tot = np.zeros(2, np.int64)
+        _check(lib().ft_batch_layout(h, order.ctypes.data, ioff.ctypes.data, moff.ctypes.data, tot.ctypes.data),
+               "ft_batch_layout")
+        self.order, self.img_off, self.map_off = order, ioff, moff
+        self.img_total, self.map_total = int(tot[0]), int(tot[1])
+
+    def groups(self):
+        out = []
+        info = np.zeros(5, np.int32)
+        for g in range(int(lib().ft_batch_group_count(self.handle))):
+            _check(lib().ft_batch_group_info(self.handle, g, info.ctypes.data), "ft_batch_group_info")
+            out.append(dict(H=int(info[0]), W=int(info[1]), start=int(info[2]), count=int(info[3]),
+                            variant=int(info[4]),
+                            tuned_ms=float(lib().ft_batch_group_tuned_ms(self.handle, g))))
+        return out
+
+    def pack(self, images):
+        """List of (H, W) arrays in caller order -> packed float32 numpy buffer."""
+        buf = np.empty(self.img_total, np.float32)
+        for j, i in enumerate(self.order):
+            h, w = self.shapes[i]
+            buf[self.img_off[j]:self.img_off[j] + h * w] = np.asarray(images[i], np.float32).ravel()
+        return buf
+
+    def unpack_maps(self, maps):
+        """Packed map buffer (numpy) -> list of (H, W) maps in caller order."""
+        out = [None] * self.n
+        for j, i in enumerate(self.order):
+            h, w = self.shapes[i]
+            out[i] = maps[self.map_off[j]:self.map_off[j] + h * w].reshape(h, w)
+        return out
+
+    def run(self, imgs, maps, top_k=0, threshold=float("-inf"), out=None, count=None, stream=None,
+            graph=False, tune=False):
+        ip = _dev_ptr(imgs, "float32", self.img_total, "imgs")
+        mp = _dev_ptr(maps, "float32", self.map_total, "maps")
+        op = _dev_ptr(out, "uint8", self.n * top_k * PEAK_DTYPE.itemsize, "out") if top_k else None
+        cp = _dev_ptr(count, "int32", self.n, "count") if top_k else None
+        flags = (FT_BATCH_GRAPH if graph else 0) | (FT_BATCH_TUNE if tune else 0)
+        _check(lib().ft_batch_run(self.handle, ip, mp, int(top_k), float(threshold), op, cp,
+                                  _stream_ptr(stream), flags), "ft_batch_run")
+
+    def close(self):
+        if self.handle:
+            lib().ft_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 # ------------------------------------------------------------ autograd wrapper
