@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-varlen", action="store_true", help="skip the mixed-size batch measurement")
     ap.add_argument("--images", type=int, default=64,
                     help="images per GPU (64 = the benchmark workload; smaller only for ncu captures)")
     return ap.parse_args()
@@ -241,6 +242,60 @@ def time_oracle_sample(pool, imgs):
     return time.perf_counter() - t, per
 
 
+def _varlen_img(args):
+    from paper_1904_09409_gb300 import synth
+    idx, h, w = args
+    return synth.varlen_image(idx, h, w).img
+
+
+def varlen_images(pool, shapes):
+    return pool.map(_varlen_img, [(i, h, w) for i, (h, w) in enumerate(shapes)], chunksize=4)
+
+
+def time_varlen(f, imgs, shapes, steps, dev):
+    """512 mixed-size images (H, W from {128 ... 2048}), forward + top-32 peaks in
+    one captured graph after autotuning; returns the JSON record."""
+    import torch
+    cache = os.path.join(ROOT, "paper_1904_09409_gb300", "tune_cache.json")
+    b = f.Batch(shapes, tune_cache=cache)
+    x = torch.from_numpy(b.pack(imgs)).to(dev)
+    m = torch.empty(b.map_total, dtype=torch.float32, device=dev)
+    out = torch.empty(b.n * TOP_K * f.PEAK_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    cnt = torch.empty(b.n, dtype=torch.int32, device=dev)
+    s = torch.cuda.Stream(dev)
+    with torch.cuda.stream(s):
+        t0 = time.perf_counter()
+        b.run(x, m, TOP_K, out=out, count=cnt, stream=s, tune=True)
+        s.synchronize()
+        tune_s = time.perf_counter() - t0
+        for _ in range(3):
+            b.run(x, m, TOP_K, out=out, count=cnt, stream=s, graph=True)
+        s.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(steps):
+            b.run(x, m, TOP_K, out=out, count=cnt, stream=s, graph=True)
+        e1.record(s)
+        s.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    groups = b.groups()
+    px = sum(h * w for h, w in shapes)
+    per = {f"{g['H']}x{g['W']}": round(g["count"] * g["H"] * g["W"] / (g["tuned_ms"] / 1e3) / 1e6, 1)
+           for g in groups if g["tuned_ms"] > 0}
+    variants = {}
+    for g in groups:
+        variants[str(g["variant"])] = variants.get(str(g["variant"]), 0) + 1
+    b.close()
+    return {"images_per_s": len(shapes) / (ms / 1e3), "value": px / (ms / 1e3) / 1e6, "unit": UNIT,
+            "ms_per_step": ms, "steps": steps, "images": len(shapes), "megapixels": px / 1e6,
+            "shape_groups": len(groups), "tune_s": tune_s, "variants_chosen": variants,
+            "per_size_mpx_s": per,
+            "workload": "512 images, H and W i.i.d. from {128,192,256,384,512,768,1024,1536,2048}, content as "
+                        "the 1024^2 batch, maps H x W, top-32; forward + peaks of all shape groups in one "
+                        "CUDA graph launch (8 forked streams), variants chosen by the autotuner; per-size "
+                        "figures are the tuned group timed alone"}
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -307,8 +362,13 @@ def run_ours(args):
         replicas.init("nccl", dev)
 
     # CPU baseline first (spawned pool, before any kernel of ours runs)
+    from paper_1904_09409_gb300 import synth
     imgs, lines = make_batch(rank, ws, with_lines=True)
     cpu = None
+    vl_shapes = synth.varlen_shapes(512)
+    cores = host_cores()
+    with oracle_pool(min(cores, 32)) as pool:
+        vl_imgs = varlen_images(pool, vl_shapes) if not args.no_varlen else None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(imgs)
 
@@ -380,6 +440,23 @@ def run_ours(args):
     fb512_ms = replicas.max_over_ranks(fb512_ms, dev)
     plan512.close()
 
+    varlen = None
+    if vl_imgs is not None:
+        varlen = time_varlen(f, vl_imgs, vl_shapes, max(3, min(args.steps, 50)), dev)
+        del vl_imgs
+
+    # host -> device copy rate of the pinned image buffer (context for e2e)
+    hd = torch.empty_like(x)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    hd.copy_(h_img, non_blocking=True)
+    c0.record(stream)
+    for _ in range(5):
+        hd.copy_(h_img, non_blocking=True)
+    c1.record(stream)
+    torch.cuda.synchronize(dev)
+    h2d_gbs = 5 * h_img.numel() * 4 / (c0.elapsed_time(c1) / 1e3) / 1e9
+    del hd
+
     px_step = ws * BATCH * SIDE * SIDE
     value = args.steps * px_step / (ms / 1e3) / 1e6
     e2e_value = e2e_steps * px_step / e2e_s / 1e6
@@ -417,7 +494,8 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": ws * BATCH * SIDE * SIDE * 4,
                     "d2h_bytes_per_step": ws * (BATCH * TOP_K * f.PEAK_DTYPE.itemsize + BATCH * 4),
-                    "call": "ft_detect_host", "steps": e2e_steps},
+                    "call": "ft_detect_host", "steps": e2e_steps, "h2d_copy_gbs": h2d_gbs},
+            "varlen": varlen,
             "fwd_bwd": {"value": px_step / (fb_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": fb_ms,
                         "steps": fb_steps, "kernels_us": fb_kernels,
                         "workload": "the same 64 x 1024^2 batch: ft_forward + ft_abs_mse_grad (loss "
