@@ -142,7 +142,9 @@ ft_status ft_abs_mse_grad(ft_plan plan, const float* d_map, const float* d_targe
 /* End-to-end detection from host memory: copies h_img ([batch][H][W]) to a
  * plan-owned device buffer, runs ft_forward and ft_peaks, copies the peaks and
  * counts back to h_out ([batch][top_k]) and h_count ([batch]) and synchronises
- * `stream` before returning. */
+ * `stream` before returning.  The batch is processed in chunks of 8 images: a
+ * plan-owned copy stream uploads the next chunk while `stream` transforms the
+ * current one (pinned h_img lets the copies run asynchronously). */
 ft_status ft_detect_host(ft_plan plan, const float* h_img, int batch, int top_k, float threshold,
                          ft_peak* h_out, int32_t* h_count, void* stream);
 

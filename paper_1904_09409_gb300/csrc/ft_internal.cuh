@@ -213,6 +213,10 @@ struct ft_plan_s {
     int col_logB_max, row_logB_max;  // the largest that fit the shared-memory budget
     int use_fast_y, use_fast_x;      // fixed-length kernels in use for H' / S
     int variant;            // see ft_plan_set_variant
+    // ft_detect_host pipeline: a copy stream and one event per chunk
+    cudaStream_t copy_stream;
+    std::vector<cudaEvent_t> chunk_events;
+    cudaEvent_t start_event;
     // per-launch timing (ft_profile_enable / ft_profile_read)
     int prof_on;
     size_t prof_used;

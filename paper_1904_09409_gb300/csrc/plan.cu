@@ -14,6 +14,8 @@
 
 static thread_local char g_last_error[256] = "";
 
+#define FT_DETECT_CHUNK 8   // images per chunk of the ft_detect_host pipeline
+
 static ft_status cuda_fail(cudaError_t e, const char* where) {
     snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
     return FT_ERR_CUDA;
@@ -292,6 +294,9 @@ ft_status ft_plan_destroy(ft_plan p) {
     if (p->d_map_host) cudaFree(p->d_map_host);
     if (p->d_peaks_host) cudaFree(p->d_peaks_host);
     for (cudaEvent_t e : p->prof_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : p->chunk_events) cudaEventDestroy(e);
+    if (p->start_event) cudaEventDestroy(p->start_event);
+    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     cudaSetDevice(cur);
     delete p;
     return FT_OK;
@@ -466,8 +471,10 @@ ft_status ft_detect_host(ft_plan p, const float* h_img, int batch, int top_k, fl
     if (!p || batch < 0 || batch > 65535 || top_k < 1 || top_k > FT_MAX_TOPK) return FT_ERR_INVALID_ARG;
     if (batch == 0) return FT_OK;
     if (!h_img || !h_out || !h_count) return FT_ERR_INVALID_ARG;
-    const size_t img_b = (size_t)batch * p->img_H * p->img_W * sizeof(float);
-    const size_t map_b = (size_t)batch * p->Hp * p->S * sizeof(float);
+    const size_t img_px = (size_t)p->img_H * p->img_W;
+    const size_t map_px = (size_t)p->Hp * p->S;
+    const size_t img_b = (size_t)batch * img_px * sizeof(float);
+    const size_t map_b = (size_t)batch * map_px * sizeof(float);
     const size_t pk_b = (size_t)batch * top_k * sizeof(ft_peak);
     const size_t cnt_off = (pk_b + 255) & ~(size_t)255;
     ft_status s;
@@ -477,13 +484,42 @@ ft_status ft_detect_host(ft_plan p, const float* h_img, int batch, int top_k, fl
                     "cudaMalloc(peaks)")) != FT_OK)
         return s;
     p->d_count_host = (int32_t*)((char*)p->d_peaks_host + cnt_off);
+    // Chunks of images: the copy stream uploads chunk c + 1 while the caller's
+    // stream transforms chunk c; peaks and counts come back per chunk.
+    const int chunk = batch < FT_DETECT_CHUNK ? batch : FT_DETECT_CHUNK;
+    const int nchunks = (batch + chunk - 1) / chunk;
+    if (!p->copy_stream) FT_CUDA(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking), "copy stream");
+    if (!p->start_event) FT_CUDA(cudaEventCreateWithFlags(&p->start_event, cudaEventDisableTiming), "event");
+    while ((int)p->chunk_events.size() < nchunks) {
+        cudaEvent_t e;
+        FT_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+        p->chunk_events.push_back(e);
+    }
+    // size the workspace for one chunk before any copy is in flight
+    const size_t need = aux_off(p, chunk) + peaks_key_bytes(p->Hp, p->S, chunk, top_k);
+    if ((s = ensure(&p->d_ws, &p->ws_bytes, need, "cudaMalloc(workspace)")) != FT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    FT_CUDA(cudaMemcpyAsync(p->d_img_host, h_img, img_b, cudaMemcpyHostToDevice, st), "copy image in");
-    if ((s = ft_forward(p, p->d_img_host, p->d_map_host, batch, stream)) != FT_OK) return s;
-    if ((s = ft_peaks(p, p->d_map_host, batch, top_k, threshold, p->d_peaks_host, p->d_count_host,
-                      stream)) != FT_OK)
-        return s;
-    FT_CUDA(cudaMemcpyAsync(h_out, p->d_peaks_host, pk_b, cudaMemcpyDeviceToHost, st), "copy peaks out");
+    FT_CUDA(cudaEventRecord(p->start_event, st), "event");
+    FT_CUDA(cudaStreamWaitEvent(p->copy_stream, p->start_event, 0), "copy stream wait");
+    for (int c = 0; c < nchunks; ++c) {
+        const int b0 = c * chunk, nb = (batch - b0) < chunk ? (batch - b0) : chunk;
+        FT_CUDA(cudaMemcpyAsync(p->d_img_host + b0 * img_px, h_img + b0 * img_px, nb * img_px * sizeof(float),
+                                cudaMemcpyHostToDevice, p->copy_stream),
+                "copy image in");
+        FT_CUDA(cudaEventRecord(p->chunk_events[c], p->copy_stream), "event");
+    }
+    for (int c = 0; c < nchunks; ++c) {
+        const int b0 = c * chunk, nb = (batch - b0) < chunk ? (batch - b0) : chunk;
+        FT_CUDA(cudaStreamWaitEvent(st, p->chunk_events[c], 0), "wait for chunk");
+        if ((s = ft_forward(p, p->d_img_host + b0 * img_px, p->d_map_host + b0 * map_px, nb, stream)) != FT_OK)
+            return s;
+        if ((s = ft_peaks(p, p->d_map_host + b0 * map_px, nb, top_k, threshold, p->d_peaks_host + (size_t)b0 * top_k,
+                          p->d_count_host + b0, stream)) != FT_OK)
+            return s;
+        FT_CUDA(cudaMemcpyAsync(h_out + (size_t)b0 * top_k, p->d_peaks_host + (size_t)b0 * top_k,
+                                (size_t)nb * top_k * sizeof(ft_peak), cudaMemcpyDeviceToHost, st),
+                "copy peaks out");
+    }
     FT_CUDA(cudaMemcpyAsync(h_count, p->d_count_host, batch * sizeof(int32_t), cudaMemcpyDeviceToHost, st),
             "copy counts out");
     FT_CUDA(cudaStreamSynchronize(st), "synchronise");

@@ -244,3 +244,19 @@ def test_fig9_inverse_peak_on_gpu(torch):
     assert abs(1.0 / inv_k - k) < 0.1
     ref = oracle.inverse_funnel_ref(img[0], S, Hp)
     assert _gpu.rel_l2(m[0], ref) <= TOL_MAP
+
+
+def test_detect_host_pipeline_matches_device_calls(torch):
+    """ft_detect_host (chunked uploads overlapped with compute) returns exactly
+    the peaks of ft_forward + ft_peaks on device buffers; 20 images = 3 chunks."""
+    from paper_1904_09409_gb300 import funnel as f
+    imgs = np.stack([synth.mixed_image(synth.WL_BATCH_1024, 300 + i, 128, 192).img for i in range(20)])
+    with f.Plan(128, 192, 192, 128) as plan:
+        m = _gpu.forward(plan, imgs)
+        ref, _ = _gpu.peaks(plan, m, 16)
+        h_img = torch.from_numpy(imgs).pin_memory()
+        for _ in range(2):                                  # second call reuses the pipeline objects
+            out, cnt = f.ft_detect_host(plan, h_img, 16)
+            got = [[(int(p["t"]), int(p["s"]), float(p["value"])) for p in r]
+                   for r in f.peaks_to_numpy(out, cnt, 16)]
+            assert got == ref
