@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-varlen", action="store_true", help="skip the mixed-size batch measurement")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="time only the main step (no e2e, forward+backward or mixed-size legs), for ncu captures")
     ap.add_argument("--images", type=int, default=64,
                     help="images per GPU (64 = the benchmark workload; smaller only for ncu captures)")
     return ap.parse_args()
@@ -366,9 +368,10 @@ def run_ours(args):
     imgs, lines = make_batch(rank, ws, with_lines=True)
     cpu = None
     vl_shapes = synth.varlen_shapes(512)
-    cores = host_cores()
-    with oracle_pool(min(cores, 32)) as pool:
-        vl_imgs = varlen_images(pool, vl_shapes) if not args.no_varlen else None
+    vl_imgs = None
+    if not (args.no_varlen or args.no_extras):
+        with oracle_pool(min(host_cores(), 32)) as pool:
+            vl_imgs = varlen_images(pool, vl_shapes)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(imgs)
 
@@ -410,56 +413,11 @@ def run_ours(args):
 
     ms = replicas.max_over_ranks(ms, dev)
 
-    # end to end through the public host-buffer call: H2D of the step's images
-    # from pinned memory, forward + peaks, D2H of the peaks and counts
-    h_img = torch.from_numpy(imgs).pin_memory()
-    h_pk = torch.empty(BATCH * TOP_K * f.PEAK_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
-    h_cnt = torch.empty(BATCH, dtype=torch.int32).pin_memory()
-    e2e_steps = max(3, min(args.steps, 30))
-    for _ in range(2):
-        f.ft_detect_host(plan, h_img, TOP_K, out_host=h_pk, count_host=h_cnt, stream=stream)
-    replicas.barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        f.ft_detect_host(plan, h_img, TOP_K, out_host=h_pk, count_host=h_cnt, stream=stream)
-    e2e_s = replicas.max_over_ranks(time.perf_counter() - t0, dev)
-
-    # forward + loss + adjoint on the same resident batch, and on 32 x 512^2
-    from paper_1904_09409_gb300 import synth
-    tgt = torch.from_numpy(blob_targets(lines, SIDE)).to(dev)
-    fb_steps = max(3, min(args.steps, 100))
-    fb_ms, fb_kernels = time_fwd_bwd(f, plan, x, tgt, fb_steps, stream, dev)
-    fb_ms = replicas.max_over_ranks(fb_ms, dev)
-    del tgt
-    g_imgs = synth.grad_batch_512(32, start=rank * 32)
-    plan512 = f.Plan(512, 512, 512, 512)
-    x512 = torch.from_numpy(np.stack([g.img for g in g_imgs])).to(dev)
-    t512 = torch.from_numpy(np.stack([synth.blob_target(512, 512, line_cells(g.lines, 512, 512, 512, 512))
-                                      for g in g_imgs])).to(dev)
-    fb512_ms, _ = time_fwd_bwd(f, plan512, x512, t512, fb_steps, stream, dev)
-    fb512_ms = replicas.max_over_ranks(fb512_ms, dev)
-    plan512.close()
-
-    varlen = None
-    if vl_imgs is not None:
-        varlen = time_varlen(f, vl_imgs, vl_shapes, max(3, min(args.steps, 50)), dev)
-        del vl_imgs
-
-    # host -> device copy rate of the pinned image buffer (context for e2e)
-    hd = torch.empty_like(x)
-    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    hd.copy_(h_img, non_blocking=True)
-    c0.record(stream)
-    for _ in range(5):
-        hd.copy_(h_img, non_blocking=True)
-    c1.record(stream)
-    torch.cuda.synchronize(dev)
-    h2d_gbs = 5 * h_img.numel() * 4 / (c0.elapsed_time(c1) / 1e3) / 1e9
-    del hd
+    extra = {} if args.no_extras else run_extras(f, args, plan, imgs, lines, x, stream, dev, rank, ws,
+                                                  vl_imgs, vl_shapes)
 
     px_step = ws * BATCH * SIDE * SIDE
     value = args.steps * px_step / (ms / 1e3) / 1e6
-    e2e_value = e2e_steps * px_step / e2e_s / 1e6
 
     # roofline of the dominant kernel
     kernels = {}
@@ -491,19 +449,7 @@ def run_ours(args):
             "roofline": roof,
             "kernels": kernels,
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": UNIT,
-                    "h2d_bytes_per_step": ws * BATCH * SIDE * SIDE * 4,
-                    "d2h_bytes_per_step": ws * (BATCH * TOP_K * f.PEAK_DTYPE.itemsize + BATCH * 4),
-                    "call": "ft_detect_host", "steps": e2e_steps, "h2d_copy_gbs": h2d_gbs},
-            "varlen": varlen,
-            "fwd_bwd": {"value": px_step / (fb_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": fb_ms,
-                        "steps": fb_steps, "kernels_us": fb_kernels,
-                        "workload": "the same 64 x 1024^2 batch: ft_forward + ft_abs_mse_grad (loss "
-                                    "mean((|P|/(W/2) - T)^2), T Gaussian blobs of 2 cells at the drawn "
-                                    "lines) + ft_backward"},
-            "fwd_bwd_512": {"value": ws * 32 * 512 * 512 / (fb512_ms / 1e3) / 1e6, "unit": UNIT,
-                            "ms_per_step": fb512_ms, "steps": fb_steps,
-                            "workload": "32 x 512^2 gradient workload, same step"},
+            **extra,
             "gpu_launches": args.steps * launches_per_step,
             "clocks": clocks,
         }
@@ -511,6 +457,72 @@ def run_ours(args):
     plan.close()
     replicas.finish()
     return 0
+
+
+def run_extras(f, args, plan, imgs, lines, x, stream, dev, rank, ws, vl_imgs, vl_shapes):
+    """e2e through ft_detect_host, forward+backward legs, the mixed-size batch and
+    the host-to-device copy rate; returns the extra JSON keys."""
+    import torch
+    from paper_1904_09409_gb300 import replicas, synth
+    px_step = ws * BATCH * SIDE * SIDE
+    # end to end through the public host-buffer call: H2D of the step's images
+    # from pinned memory, forward + peaks, D2H of the peaks and counts
+    h_img = torch.from_numpy(imgs).pin_memory()
+    h_pk = torch.empty(BATCH * TOP_K * f.PEAK_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    h_cnt = torch.empty(BATCH, dtype=torch.int32).pin_memory()
+    e2e_steps = max(3, min(args.steps, 30))
+    for _ in range(2):
+        f.ft_detect_host(plan, h_img, TOP_K, out_host=h_pk, count_host=h_cnt, stream=stream)
+    replicas.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        f.ft_detect_host(plan, h_img, TOP_K, out_host=h_pk, count_host=h_cnt, stream=stream)
+    e2e_s = replicas.max_over_ranks(time.perf_counter() - t0, dev)
+
+    # forward + loss + adjoint on the same resident batch, and on 32 x 512^2
+    tgt = torch.from_numpy(blob_targets(lines, SIDE)).to(dev)
+    fb_steps = max(3, min(args.steps, 100))
+    fb_ms, fb_kernels = time_fwd_bwd(f, plan, x, tgt, fb_steps, stream, dev)
+    fb_ms = replicas.max_over_ranks(fb_ms, dev)
+    del tgt
+    g_imgs = synth.grad_batch_512(32, start=rank * 32)
+    plan512 = f.Plan(512, 512, 512, 512)
+    x512 = torch.from_numpy(np.stack([g.img for g in g_imgs])).to(dev)
+    t512 = torch.from_numpy(np.stack([synth.blob_target(512, 512, line_cells(g.lines, 512, 512, 512, 512))
+                                      for g in g_imgs])).to(dev)
+    fb512_ms, _ = time_fwd_bwd(f, plan512, x512, t512, fb_steps, stream, dev)
+    fb512_ms = replicas.max_over_ranks(fb512_ms, dev)
+    plan512.close()
+
+    varlen = None
+    if vl_imgs is not None:
+        varlen = time_varlen(f, vl_imgs, vl_shapes, max(3, min(args.steps, 50)), dev)
+
+    # host -> device copy rate of the pinned image buffer (context for e2e)
+    hd = torch.empty_like(x)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    hd.copy_(h_img, non_blocking=True)
+    c0.record(stream)
+    for _ in range(5):
+        hd.copy_(h_img, non_blocking=True)
+    c1.record(stream)
+    torch.cuda.synchronize(dev)
+    h2d_gbs = 5 * h_img.numel() * 4 / (c0.elapsed_time(c1) / 1e3) / 1e9
+    return {
+        "e2e": {"value": e2e_steps * px_step / e2e_s / 1e6, "unit": UNIT,
+                "h2d_bytes_per_step": ws * BATCH * SIDE * SIDE * 4,
+                "d2h_bytes_per_step": ws * (BATCH * TOP_K * f.PEAK_DTYPE.itemsize + BATCH * 4),
+                "call": "ft_detect_host", "steps": e2e_steps, "h2d_copy_gbs": h2d_gbs},
+        "varlen": varlen,
+        "fwd_bwd": {"value": px_step / (fb_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": fb_ms,
+                    "steps": fb_steps, "kernels_us": fb_kernels,
+                    "workload": "the same 64 x 1024^2 batch: ft_forward + ft_abs_mse_grad (loss "
+                                "mean((|P|/(W/2) - T)^2), T Gaussian blobs of 2 cells at the drawn "
+                                "lines) + ft_backward"},
+        "fwd_bwd_512": {"value": ws * 32 * 512 * 512 / (fb512_ms / 1e3) / 1e6, "unit": UNIT,
+                        "ms_per_step": fb512_ms, "steps": fb_steps,
+                        "workload": "32 x 512^2 gradient workload, same step"},
+    }
 
 
 def main():
