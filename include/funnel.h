@@ -226,9 +226,12 @@ ft_status ft_batch_run(ft_batch batch, const float* d_imgs, float* d_maps, int t
 /* Bytes of plan-owned device workspace that a call with this batch needs. */
 size_t ft_workspace_bytes(ft_plan plan, int batch);
 
-/* Number of kernel launches ft_forward / ft_peaks issue per call. */
-int ft_forward_launches(ft_plan plan);
-int ft_peaks_launches(ft_plan plan);
+/* Number of kernel launches ft_forward / ft_peaks issue for a call with this
+ * batch (a batch of 4 or more images is split over 2 plan-owned streams forked
+ * from and joined back into the caller's stream: same kernels, same results;
+ * FT_LANES=1 in the environment at plan creation turns the split off). */
+int ft_forward_launches(ft_plan plan, int batch);
+int ft_peaks_launches(ft_plan plan, int batch);
 
 /* Kernel identifiers of the per-launch timing below. */
 typedef enum {

@@ -213,6 +213,10 @@ struct ft_plan_s {
     int col_logB_max, row_logB_max;  // the largest that fit the shared-memory budget
     int use_fast_y, use_fast_x;      // fixed-length kernels in use for H' / S
     int variant;            // see ft_plan_set_variant
+    // lanes: the batch split over FT_LANES plan-owned streams forked from the caller's
+    cudaStream_t lane_streams[2];
+    cudaEvent_t lane_fork, lane_join[2];
+    int lanes;
     // ft_detect_host pipeline: a copy stream and one event per chunk
     cudaStream_t copy_stream;
     std::vector<cudaEvent_t> chunk_events;
@@ -266,7 +270,11 @@ cudaError_t launch_nvmt_rows_adjoint(float2* ws, int W, int S, int Hp, int L, in
 // keys (launch_peak_tiles), then per-image selection of the top_k keys in order
 // (launch_peak_select).  keys must hold peaks_key_bytes() bytes.
 cudaError_t launch_peak_tiles(const float* map, int Hp, int S, int batch, int top_k, float threshold,
-                              unsigned long long* keys, cudaStream_t st);
+                              unsigned long long* keys, unsigned* bounds, cudaStream_t st);
+// keys per image, and the running bounds (one per image) inside a key buffer
+// of peaks_key_bytes(Hp, S, batch, top_k) bytes
+size_t peaks_tile_keys(int Hp, int S, int top_k);
+unsigned* peaks_bounds(unsigned long long* keys, int Hp, int S, int batch, int top_k);
 cudaError_t launch_peak_select(const unsigned long long* keys, int Hp, int S, int batch, int top_k,
                                ft_peak* out, int32_t* count, cudaStream_t st);
 size_t peaks_key_bytes(int Hp, int S, int batch, int top_k);

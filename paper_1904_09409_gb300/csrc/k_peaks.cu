@@ -443,14 +443,22 @@ static dim3 tile_grid(int Hp, int S, int batch) {
     return dim3((S + PK_TS - 1) / PK_TS, (Hp + PK_TT - 1) / PK_TT, batch);
 }
 
-static size_t key_bytes(int Hp, int S, int batch, int top_k) {
+size_t peaks_tile_keys(int Hp, int S, int top_k) {
     const dim3 g = tile_grid(Hp, S, 1);
-    return ((size_t)batch * g.x * g.y * kt_of(top_k) * sizeof(u64) + 255) & ~(size_t)255;
+    return (size_t)g.x * g.y * kt_of(top_k);
+}
+
+static size_t key_bytes(int Hp, int S, int batch, int top_k) {
+    return ((size_t)batch * peaks_tile_keys(Hp, S, top_k) * sizeof(u64) + 255) & ~(size_t)255;
 }
 
 // scratch: the tiles' keys, then one running bound per image
 size_t peaks_key_bytes(int Hp, int S, int batch, int top_k) {
     return key_bytes(Hp, S, batch, top_k) + (size_t)batch * sizeof(unsigned);
+}
+
+unsigned* peaks_bounds(unsigned long long* keys, int Hp, int S, int batch, int top_k) {
+    return reinterpret_cast<unsigned*>(reinterpret_cast<char*>(keys) + key_bytes(Hp, S, batch, top_k));
 }
 
 // The register-only tile kernel keeps, per image, a running lower bound of the
@@ -459,11 +467,11 @@ size_t peaks_key_bytes(int Hp, int S, int batch, int top_k) {
 // selecting.  It only applies when every tile keeps top_k keys (top_k <= 512).
 // The bounds are cleared on the stream before the tiles run.
 cudaError_t launch_peak_tiles(const float* map, int Hp, int S, int batch, int top_k, float threshold,
-                              unsigned long long* keys, cudaStream_t st) {
+                              unsigned long long* keys, unsigned* bounds, cudaStream_t st) {
     if (fast_tiles(Hp, S)) {
         unsigned* tau = nullptr;
         if (top_k <= PK_CAND) {
-            tau = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(keys) + key_bytes(Hp, S, batch, top_k));
+            tau = bounds;
             cudaError_t e = cudaMemsetAsync(tau, 0, (size_t)batch * sizeof(unsigned), st);
             if (e != cudaSuccess) return e;
         }

@@ -15,6 +15,7 @@
 static thread_local char g_last_error[256] = "";
 
 #define FT_DETECT_CHUNK 8   // images per chunk of the ft_detect_host pipeline
+#define FT_LANES 2          // streams a large batch is split over (see lanes_fork)
 
 static ft_status cuda_fail(cudaError_t e, const char* where) {
     snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
@@ -147,6 +148,7 @@ static ft_status ensure(void** ptr, size_t* have, size_t need, const char* what)
     return FT_OK;
 }
 
+static int use_lanes(ft_plan p, int batch);
 static size_t spec_bytes(ft_plan p, int batch) { return (size_t)batch * p->L * p->S * sizeof(float2); }
 static size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
 // workspace: [half spectra][transposed image (inverse space only)][aux: peak keys or loss partials]
@@ -278,6 +280,8 @@ ft_status ft_plan_create_space(ft_plan* out, int img_H, int img_W, int n_slope, 
     p->use_fast_y = fast_y && !generic;
     p->use_fast_x = fast_x && !generic;
     p->variant = generic ? 1 : 0;
+    const char* lanes = getenv("FT_LANES");
+    p->lanes = lanes ? (atoi(lanes) > 1 ? FT_LANES : 1) : FT_LANES;
     *out = p;
     return FT_OK;
 }
@@ -295,6 +299,11 @@ ft_status ft_plan_destroy(ft_plan p) {
     if (p->d_peaks_host) cudaFree(p->d_peaks_host);
     for (cudaEvent_t e : p->prof_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : p->chunk_events) cudaEventDestroy(e);
+    if (p->lane_fork) cudaEventDestroy(p->lane_fork);
+    for (int j = 0; j < FT_LANES; ++j) {
+        if (p->lane_streams[j]) cudaStreamDestroy(p->lane_streams[j]);
+        if (p->lane_join[j]) cudaEventDestroy(p->lane_join[j]);
+    }
     if (p->start_event) cudaEventDestroy(p->start_event);
     if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     cudaSetDevice(cur);
@@ -330,8 +339,55 @@ size_t ft_workspace_bytes(ft_plan p, int batch) {
     return aux_off(p, batch);
 }
 
-int ft_forward_launches(ft_plan p) { return p ? (p->space == FT_SPACE_INVERSE ? 4 : 3) : 0; }
-int ft_peaks_launches(ft_plan p) { return p ? 2 : 0; }
+int ft_forward_launches(ft_plan p, int batch) {
+    if (!p || batch <= 0) return 0;
+    return (p->space == FT_SPACE_INVERSE ? 1 : 0) + 3 * (use_lanes(p, batch) ? FT_LANES : 1);
+}
+int ft_peaks_launches(ft_plan p, int batch) {
+    if (!p || batch <= 0) return 0;
+    return 2 * (use_lanes(p, batch) ? FT_LANES : 1);
+}
+
+// Lanes: a batch of at least 2 FT_LANES images is split into FT_LANES contiguous
+// parts run on plan-owned streams forked from and joined back into the caller's
+// stream, so that one part's compute-bound kernels share the SMs with another
+// part's memory-bound ones.  The parts use disjoint slices of the workspace and
+// the same kernels, so results do not depend on the split.  FT_LANES=1 in the
+// environment at plan creation keeps everything on the caller's stream.
+
+static ft_status lanes_fork(ft_plan p, cudaStream_t st) {
+    if (!p->lane_fork) {
+        FT_CUDA(cudaEventCreateWithFlags(&p->lane_fork, cudaEventDisableTiming), "lane event");
+        for (int j = 0; j < FT_LANES; ++j) {
+            FT_CUDA(cudaStreamCreateWithFlags(&p->lane_streams[j], cudaStreamNonBlocking), "lane stream");
+            FT_CUDA(cudaEventCreateWithFlags(&p->lane_join[j], cudaEventDisableTiming), "lane event");
+        }
+    }
+    FT_CUDA(cudaEventRecord(p->lane_fork, st), "lane fork");
+    for (int j = 0; j < FT_LANES; ++j) FT_CUDA(cudaStreamWaitEvent(p->lane_streams[j], p->lane_fork, 0), "lane wait");
+    return FT_OK;
+}
+
+static ft_status lanes_join(ft_plan p, cudaStream_t st) {
+    for (int j = 0; j < FT_LANES; ++j) {
+        FT_CUDA(cudaEventRecord(p->lane_join[j], p->lane_streams[j]), "lane join");
+        FT_CUDA(cudaStreamWaitEvent(st, p->lane_join[j], 0), "lane join wait");
+    }
+    return FT_OK;
+}
+
+static int use_lanes(ft_plan p, int batch) { return p->lanes > 1 && batch >= 2 * FT_LANES; }
+
+static ft_status forward_part(ft_plan p, const float* src, float* d_map, float2* ws, int nb, cudaStream_t st) {
+    FT_LAUNCH(p, FT_KERNEL_COL_R2C, st,
+              col_r2c(p, src, p->H, p->W, p->W, (size_t)p->H * p->W, p->top, ws, 1.f, 1.f, nb, st),
+              "step 1 (column R2C)");
+    FT_LAUNCH(p, FT_KERNEL_NVMT_ROWS, st, nvmt_rows(p, ws, nb, st), "steps 2-3 (NVMT + row FFT)");
+    FT_LAUNCH(p, FT_KERNEL_COL_C2R, st,
+              col_c2r(p, ws, p->S, 1.f, d_map, 0, p->Hp, p->S, (size_t)p->Hp * p->S, 1.f / (float)p->Hp, nb, st),
+              "step 4 (column C2R)");
+    return FT_OK;
+}
 
 ft_status ft_forward(ft_plan p, const float* d_img, float* d_map, int batch, void* stream) {
     if (!p || batch < 0 || batch > 65535) return FT_ERR_INVALID_ARG;
@@ -347,15 +403,15 @@ ft_status ft_forward(ft_plan p, const float* d_img, float* d_map, int batch, voi
         FT_CUDA(launch_transpose(d_img, tp, p->img_H, p->img_W, batch, st), "transpose (inverse space)");
         src = tp;
     }
-    FT_LAUNCH(p, FT_KERNEL_COL_R2C, st,
-              col_r2c(p, src, p->H, p->W, p->W, (size_t)p->H * p->W, p->top, ws, 1.f, 1.f, batch, st),
-              "step 1 (column R2C)");
-    FT_LAUNCH(p, FT_KERNEL_NVMT_ROWS, st, nvmt_rows(p, ws, batch, st), "steps 2-3 (NVMT + row FFT)");
-    FT_LAUNCH(p, FT_KERNEL_COL_C2R, st,
-              col_c2r(p, ws, p->S, 1.f, d_map, 0, p->Hp, p->S, (size_t)p->Hp * p->S, 1.f / (float)p->Hp,
-                      batch, st),
-              "step 4 (column C2R)");
-    return FT_OK;
+    if (!use_lanes(p, batch)) return forward_part(p, src, d_map, ws, batch, st);
+    if ((s = lanes_fork(p, st)) != FT_OK) return s;
+    for (int j = 0; j < FT_LANES; ++j) {
+        const int b0 = batch * j / FT_LANES, b1 = batch * (j + 1) / FT_LANES;
+        s = forward_part(p, src + (size_t)b0 * p->H * p->W, d_map + (size_t)b0 * p->Hp * p->S,
+                         ws + (size_t)b0 * p->L * p->S, b1 - b0, p->lane_streams[j]);
+        if (s != FT_OK) return s;
+    }
+    return lanes_join(p, st);
 }
 
 ft_status ft_backward(ft_plan p, const float* d_grad_map, float* d_grad_img, int batch, void* stream) {
@@ -395,12 +451,23 @@ ft_status ft_peaks(ft_plan p, const float* d_map, int batch, int top_k, float th
     if (s != FT_OK) return s;
     unsigned long long* kbuf = (unsigned long long*)((char*)p->d_ws + off);
     cudaStream_t st = (cudaStream_t)stream;
-    FT_LAUNCH(p, FT_KERNEL_PEAK_TILES, st,
-              launch_peak_tiles(d_map, p->Hp, p->S, batch, top_k, threshold, kbuf, st),
-              "peak detection (tiles)");
-    FT_LAUNCH(p, FT_KERNEL_PEAK_SELECT, st,
-              launch_peak_select(kbuf, p->Hp, p->S, batch, top_k, d_out, d_count, st),
-              "peak detection (select)");
+    unsigned* bounds = peaks_bounds(kbuf, p->Hp, p->S, batch, top_k);
+    const size_t kpi = peaks_tile_keys(p->Hp, p->S, top_k);
+    const int lanes = use_lanes(p, batch) ? FT_LANES : 1;
+    if (lanes > 1 && (s = lanes_fork(p, st)) != FT_OK) return s;
+    for (int j = 0; j < lanes; ++j) {
+        const int b0 = batch * j / lanes, b1 = batch * (j + 1) / lanes;
+        cudaStream_t ls = lanes > 1 ? p->lane_streams[j] : st;
+        const float* m = d_map + (size_t)b0 * p->Hp * p->S;
+        FT_LAUNCH(p, FT_KERNEL_PEAK_TILES, ls,
+                  launch_peak_tiles(m, p->Hp, p->S, b1 - b0, top_k, threshold, kbuf + b0 * kpi, bounds + b0, ls),
+                  "peak detection (tiles)");
+        FT_LAUNCH(p, FT_KERNEL_PEAK_SELECT, ls,
+                  launch_peak_select(kbuf + b0 * kpi, p->Hp, p->S, b1 - b0, top_k, d_out + (size_t)b0 * top_k,
+                                     d_count + b0, ls),
+                  "peak detection (select)");
+    }
+    if (lanes > 1) return lanes_join(p, st);
     return FT_OK;
 }
 

@@ -84,8 +84,8 @@ def lib() -> ctypes.CDLL:
     L.ft_detect_host.argtypes = [vp, vp, ci, ci, cf, vp, vp, vp]
     L.ft_workspace_bytes.argtypes = [vp, ci]
     L.ft_workspace_bytes.restype = ctypes.c_size_t
-    L.ft_forward_launches.argtypes = [vp]
-    L.ft_peaks_launches.argtypes = [vp]
+    L.ft_forward_launches.argtypes = [vp, ci]
+    L.ft_peaks_launches.argtypes = [vp, ci]
     L.ft_status_string.argtypes = [ci]
     L.ft_status_string.restype = ctypes.c_char_p
     L.ft_last_error.argtypes = []
@@ -306,12 +306,12 @@ def ft_workspace_bytes(plan: Plan, batch: int) -> int:
     return int(lib().ft_workspace_bytes(plan.handle, int(batch)))
 
 
-def ft_forward_launches(plan: Plan) -> int:
-    return int(lib().ft_forward_launches(plan.handle))
+def ft_forward_launches(plan: Plan, batch: int) -> int:
+    return int(lib().ft_forward_launches(plan.handle, int(batch)))
 
 
-def ft_peaks_launches(plan: Plan) -> int:
-    return int(lib().ft_peaks_launches(plan.handle))
+def ft_peaks_launches(plan: Plan, batch: int) -> int:
+    return int(lib().ft_peaks_launches(plan.handle, int(batch)))
 
 
 def ft_profile_enable(plan: Plan, enable: bool = True) -> None:

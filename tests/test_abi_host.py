@@ -79,7 +79,7 @@ def test_invalid_arguments(L):
     assert L.ft_detect_host(None, None, 1, 3, 0.0, None, None, None) == f.FT_ERR_INVALID_ARG
     assert L.ft_plan_destroy(None) == f.FT_OK
     assert L.ft_workspace_bytes(None, 4) == 0
-    assert L.ft_forward_launches(None) == 0
+    assert L.ft_forward_launches(None, 4) == 0
 
 
 def test_python_binding_raises_without_gpu_work(L):
