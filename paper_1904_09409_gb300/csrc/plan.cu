@@ -148,7 +148,6 @@ static ft_status ensure(void** ptr, size_t* have, size_t need, const char* what)
     return FT_OK;
 }
 
-static int use_lanes(ft_plan p, int batch);
 static size_t spec_bytes(ft_plan p, int batch) { return (size_t)batch * p->L * p->S * sizeof(float2); }
 static size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
 // workspace: [half spectra][transposed image (inverse space only)][aux: peak keys or loss partials]
@@ -339,14 +338,6 @@ size_t ft_workspace_bytes(ft_plan p, int batch) {
     return aux_off(p, batch);
 }
 
-int ft_forward_launches(ft_plan p, int batch) {
-    if (!p || batch <= 0) return 0;
-    return (p->space == FT_SPACE_INVERSE ? 1 : 0) + 3 * (use_lanes(p, batch) ? FT_LANES : 1);
-}
-int ft_peaks_launches(ft_plan p, int batch) {
-    if (!p || batch <= 0) return 0;
-    return 2 * (use_lanes(p, batch) ? FT_LANES : 1);
-}
 
 // Lanes: a batch of at least 2 FT_LANES images is split into FT_LANES contiguous
 // parts run on plan-owned streams forked from and joined back into the caller's
@@ -377,6 +368,15 @@ static ft_status lanes_join(ft_plan p, cudaStream_t st) {
 }
 
 static int use_lanes(ft_plan p, int batch) { return p->lanes > 1 && batch >= 2 * FT_LANES; }
+
+int ft_forward_launches(ft_plan p, int batch) {
+    if (!p || batch <= 0) return 0;
+    return (p->space == FT_SPACE_INVERSE ? 1 : 0) + 3 * (use_lanes(p, batch) ? FT_LANES : 1);
+}
+int ft_peaks_launches(ft_plan p, int batch) {
+    if (!p || batch <= 0) return 0;
+    return 2 * (use_lanes(p, batch) ? FT_LANES : 1);
+}
 
 static ft_status forward_part(ft_plan p, const float* src, float* d_map, float2* ws, int nb, cudaStream_t st) {
     FT_LAUNCH(p, FT_KERNEL_COL_R2C, st,
