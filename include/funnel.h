@@ -63,10 +63,16 @@ typedef enum {
 /* Step 2 interpolator.  Sec. IV adopts a chirp-z (band-limited) interpolator,
  * Sec. V a linear one.  LINEAR: rows are zero outside the image columns, the
  * sample x' H' / (2 l) is split exactly into its integer floor and remainder and
- * the fraction is one FP32 division.  CUBIC: Keys' kernel, a = -0.5. */
+ * the fraction is remainder * (1 / (2 l)) in FP32.  CUBIC: Keys' kernel,
+ * a = -0.5.  FOURIER: the trigonometric interpolant of the row (Nyquist term as
+ * a cosine) evaluated at the samples by a chirp-z (Bluestein) convolution of
+ * length M = the smallest 2^a 3^b >= W + S, zero outside p in [-W/2, W/2-1];
+ * W must then be 2^a 3^b and M <= FT_MAX_LENGTH; ft_backward is not available
+ * for it (FT_ERR_UNSUPPORTED_SIZE). */
 typedef enum {
     FT_INTERP_LINEAR = 0,
-    FT_INTERP_CUBIC = 1
+    FT_INTERP_CUBIC = 1,
+    FT_INTERP_FOURIER = 2
 } ft_interp;
 
 /* One detected peak (Sec. 4.4) with its line (eqs. 22-23):

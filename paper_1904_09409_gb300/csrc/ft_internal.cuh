@@ -213,6 +213,9 @@ struct ft_plan_s {
     int col_logB_max, row_logB_max;  // the largest that fit the shared-memory budget
     int use_fast_y, use_fast_x;      // fixed-length kernels in use for H' / S
     int variant;            // see ft_plan_set_variant
+    // band-limited (chirp-z) interpolator: lengths W and M >= W + S, chirp tables
+    FftLen fw, fm;
+    float2* d_chirp;        // [L][W+1] pre-chirps, [L][S] post-chirps, [L][M] chirp spectra
     // lanes: the batch split over FT_LANES plan-owned streams forked from the caller's
     cudaStream_t lane_streams[2];
     cudaEvent_t lane_fork, lane_join[2];
@@ -278,6 +281,12 @@ unsigned* peaks_bounds(unsigned long long* keys, int Hp, int S, int batch, int t
 cudaError_t launch_peak_select(const unsigned long long* keys, int Hp, int S, int batch, int top_k,
                                ft_peak* out, int32_t* count, cudaStream_t st);
 size_t peaks_key_bytes(int Hp, int S, int batch, int top_k);
+
+// the band-limited NVMT fused with step 3 (k_fourier.cu)
+cudaError_t launch_chirp_fft(float2* hc, int L, const FftLen& fm, cudaStream_t st);
+cudaError_t launch_nvmt_rows_fourier(float2* ws, int W, int S, int Hp, int L, const FftLen& fw,
+                                     const FftLen& fm, const FftLen& fs, const float2* chirp_u,
+                                     const float2* chirp_x, const float2* hc, int batch, cudaStream_t st);
 
 // in[b][R][C] -> out[b][C][R] (k_transpose.cu)
 cudaError_t launch_transpose(const float* in, float* out, int R, int C, int batch, cudaStream_t st);

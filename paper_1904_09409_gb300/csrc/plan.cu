@@ -105,6 +105,44 @@ static void prof_end(ft_plan p, cudaStream_t st) { cudaEventRecord(p->prof_pool[
         if (e_ != cudaSuccess) return cuda_fail(e_, where);  \
     } while (0)
 
+// exp(sign * j * pi * Hp * n^2 / (2 l W)) with the phase reduced exactly:
+// pi Hp n^2 / (2 l W) = 2 pi r / (4 l W), r = Hp n^2 mod 4 l W
+static float2 chirp(long long n, int Hp, int l, int W, int sign) {
+    const long long den = 4ll * l * W;
+    long long r = ((long long)Hp * ((n * n) % den)) % den;
+    const double th = 6.283185307179586476925286766559 * (double)r / (double)den;
+    return make_float2((float)cos(th), (float)(sign * sin(th)));
+}
+
+// Chirp tables of the band-limited interpolator (see k_fourier.cu): per row
+// l >= 1, pre-chirps exp(+j pi b u^2) (u = -W/2 .. W/2), post-chirps
+// exp(+j pi b x'^2) (x' = -S/2 .. S/2-1) and the spectrum of the convolution
+// chirp h[j mod M] = exp(-j pi b (j + W/2 - S/2)^2), j = -W .. S-1, b = Hp/(2 l W).
+static ft_status build_chirps(ft_plan p) {
+    const int W = p->W, S = p->S, L = p->L, M = p->fm.N;
+    const size_t nu = (size_t)L * (W + 1), nx = (size_t)L * S, nh = (size_t)L * M;
+    std::vector<float2> h(nu + nx + nh, make_float2(0.f, 0.f));
+    float2* cu = h.data();
+    float2* cx = cu + nu;
+    float2* hc = cx + nx;
+    for (int l = 1; l < L; ++l) {
+        for (int i = 0; i <= W; ++i) cu[(size_t)l * (W + 1) + i] = chirp(i - W / 2, p->Hp, l, W, +1);
+        for (int k = 0; k < S; ++k) cx[(size_t)l * S + k] = chirp(k - S / 2, p->Hp, l, W, +1);
+        for (int j = -W; j < S; ++j)
+            hc[(size_t)l * M + ((j % M) + M) % M] = chirp(j + W / 2 - S / 2, p->Hp, l, W, -1);
+    }
+    cudaError_t e = cudaMalloc(&p->d_chirp, h.size() * sizeof(float2));
+    if (e != cudaSuccess) {
+        p->d_chirp = nullptr;
+        cuda_fail(e, "cudaMalloc(chirps)");
+        return FT_ERR_OOM;
+    }
+    e = cudaMemcpy(p->d_chirp, h.data(), h.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_chirp_fft(p->d_chirp + nu + nx, L, p->fm, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    return e == cudaSuccess ? FT_OK : cuda_fail(e, "chirp tables");
+}
+
 // Per-pass twiddles of the fixed-length kernels: for pass s >= 1 with radix R and
 // P = product of the earlier radices, row k (stride fs_rs(R)) holds
 // exp(-2 pi i q k / (P R)) at column q, taken from the exact-index table tw of
@@ -181,6 +219,11 @@ static cudaError_t col_c2r(ft_plan p, const float2* in, int ncols, float mid, fl
 }
 
 static cudaError_t nvmt_rows(ft_plan p, float2* ws, int batch, cudaStream_t st) {
+    if (p->interp == FT_INTERP_FOURIER) {
+        const size_t nu = (size_t)p->L * (p->W + 1), nx = (size_t)p->L * p->S;
+        return launch_nvmt_rows_fourier(ws, p->W, p->S, p->Hp, p->L, p->fw, p->fm, p->fx, p->d_chirp,
+                                        p->d_chirp + nu, p->d_chirp + nu + nx, batch, st);
+    }
     if (p->use_fast_x) return launch_nvmt_rows_fast(ws, p->W, p->Hp, p->L, p->interp, p->fx, batch, st);
     return launch_nvmt_rows(ws, p->W, p->S, p->Hp, p->L, p->interp, p->fx, p->row_logB_x, batch, st);
 }
@@ -214,14 +257,20 @@ ft_status ft_plan_create_space(ft_plan* out, int img_H, int img_W, int n_slope, 
                                int space) {
     if (!out) return FT_ERR_INVALID_ARG;
     *out = nullptr;
-    if (interp != FT_INTERP_LINEAR && interp != FT_INTERP_CUBIC) return FT_ERR_INVALID_ARG;
+    if (interp != FT_INTERP_LINEAR && interp != FT_INTERP_CUBIC && interp != FT_INTERP_FOURIER)
+        return FT_ERR_INVALID_ARG;
     if (space != FT_SPACE_REGULAR && space != FT_SPACE_INVERSE) return FT_ERR_INVALID_ARG;
     // the inverse space is the regular transform of the transposed image
     const int H = space == FT_SPACE_INVERSE ? img_W : img_H;
     const int W = space == FT_SPACE_INVERSE ? img_H : img_W;
     if (H < 1 || W < 2 || (W & 1) || n_slope < W || n_intercept < H) return FT_ERR_UNSUPPORTED_SIZE;
-    FftLen fy = {}, fx = {};
+    FftLen fy = {}, fx = {}, fw = {}, fm = {};
     if (!factorize(n_intercept, &fy) || !factorize(n_slope, &fx)) return FT_ERR_UNSUPPORTED_SIZE;
+    if (interp == FT_INTERP_FOURIER) {
+        int M = W + n_slope;
+        while (M <= FT_MAX_LENGTH && !factorize(M, &fm)) ++M;
+        if (M > FT_MAX_LENGTH || !factorize(W, &fw)) return FT_ERR_UNSUPPORTED_SIZE;
+    }
 
     ft_plan p = new (std::nothrow) ft_plan_s();
     if (!p) return FT_ERR_OOM;
@@ -246,11 +295,14 @@ ft_status ft_plan_create_space(ft_plan* out, int img_H, int img_W, int n_slope, 
     const bool generic = force && force[0] == '1';
     const bool fast_y = fs_has(fy.N), fast_x = fs_has(fx.N);
     const size_t sy = fast_y ? fs_twsize(fy.N) : 0, sx = fast_x ? fs_twsize(fx.N) : 0;
-    std::vector<float2> tw((size_t)fy.N + fx.N + sy + sx);
+    std::vector<float2> tw((size_t)fy.N + fx.N + sy + sx + fw.N + fm.N);
     twiddles(fy.N, tw.data());
     twiddles(fx.N, tw.data() + fy.N);
     if (fast_y) stage_twiddles(fy.N, tw.data(), tw.data() + fy.N + fx.N);
     if (fast_x) stage_twiddles(fx.N, tw.data() + fy.N, tw.data() + fy.N + fx.N + sy);
+    const size_t wo = (size_t)fy.N + fx.N + sy + sx;
+    if (fw.N) twiddles(fw.N, tw.data() + wo);
+    if (fm.N) twiddles(fm.N, tw.data() + wo + fw.N);
     e = cudaMalloc(&p->d_tw, tw.size() * sizeof(float2));
     if (e != cudaSuccess) {
         delete p;
@@ -267,6 +319,18 @@ ft_status ft_plan_create_space(ft_plan* out, int img_H, int img_W, int n_slope, 
     p->fx.tw = p->d_tw + fy.N;
     p->fy.stw = fast_y ? p->d_tw + fy.N + fx.N : nullptr;
     p->fx.stw = fast_x ? p->d_tw + fy.N + fx.N + sy : nullptr;
+    if (interp == FT_INTERP_FOURIER) {
+        p->fw = fw;
+        p->fm = fm;
+        p->fw.tw = p->d_tw + wo;
+        p->fm.tw = p->d_tw + wo + fw.N;
+        p->fw.stw = p->fm.stw = nullptr;
+        const ft_status cs = build_chirps(p);
+        if (cs != FT_OK) {
+            ft_plan_destroy(p);
+            return cs;
+        }
+    }
     // transforms per block: 2 ping-pong buffers of N x B complex within 96 KB
     const int cap = 96 * 1024 / (int)(2 * sizeof(float2));
     p->col_logB_y = log2_floor(cap / fy.N > 0 ? cap / fy.N : 1);
@@ -293,6 +357,7 @@ ft_status ft_plan_destroy(ft_plan p) {
     cudaDeviceSynchronize();
     free_ws(p);
     if (p->d_tw) cudaFree(p->d_tw);
+    if (p->d_chirp) cudaFree(p->d_chirp);
     if (p->d_img_host) cudaFree(p->d_img_host);
     if (p->d_map_host) cudaFree(p->d_map_host);
     if (p->d_peaks_host) cudaFree(p->d_peaks_host);
@@ -416,6 +481,8 @@ ft_status ft_forward(ft_plan p, const float* d_img, float* d_map, int batch, voi
 
 ft_status ft_backward(ft_plan p, const float* d_grad_map, float* d_grad_img, int batch, void* stream) {
     if (!p || batch < 0 || batch > 65535) return FT_ERR_INVALID_ARG;
+    if (p->interp == FT_INTERP_FOURIER)
+        return ft_record_error(FT_ERR_UNSUPPORTED_SIZE, "ft_backward: no adjoint for the band-limited interpolator");
     if (batch == 0) return FT_OK;
     if (!d_grad_map || !d_grad_img || ((uintptr_t)d_grad_map & 7) || ((uintptr_t)d_grad_img & 7))
         return FT_ERR_INVALID_ARG;

@@ -24,9 +24,10 @@ FT_ERR_CUDA = 4
 FT_ERR_TIMEOUT = 5
 FT_INTERP_LINEAR = 0
 FT_INTERP_CUBIC = 1
+FT_INTERP_FOURIER = 2
 FT_MAX_LENGTH = 8192
 FT_MAX_TOPK = 1024
-INTERP_NAMES = {"linear": FT_INTERP_LINEAR, "cubic": FT_INTERP_CUBIC}
+INTERP_NAMES = {"linear": FT_INTERP_LINEAR, "cubic": FT_INTERP_CUBIC, "fourier": FT_INTERP_FOURIER}
 
 EXPORTED = (
     "ft_plan_create", "ft_plan_destroy", "ft_forward", "ft_backward", "ft_peaks",

@@ -260,3 +260,27 @@ def test_detect_host_pipeline_matches_device_calls(torch):
             got = [[(int(p["t"]), int(p["s"]), float(p["value"])) for p in r]
                    for r in f.peaks_to_numpy(out, cnt, 16)]
             assert got == ref
+
+
+# ------------------------------------------ band-limited (chirp-z) interpolator
+@pytest.mark.parametrize("H,W,S,Hp", [(32, 32, 32, 32), (48, 48, 64, 72), (64, 64, 128, 96),
+                                      (128, 128, 128, 128), (96, 64, 64, 144)])
+def test_fourier_interp_matches_oracle(torch, H, W, S, Hp):
+    """Sec. IV's chirp-z NVMT: the oracle evaluates the trigonometric interpolant
+    of every row directly (dense Dirichlet kernel); the GPU uses a Bluestein
+    convolution of length M >= W + S with FP64-built chirps."""
+    imgs = inputs(H, W, 2, seed=W + S)
+    with make_plan(H, W, S, Hp, "fourier") as plan:
+        got = _gpu.forward(plan, imgs)
+    for i in range(2):
+        ref = oracle.funnel_ref(imgs[i], S, Hp, "fourier")
+        assert _gpu.rel_l2(got[i], ref) <= TOL_MAP, _gpu.rel_l2(got[i], ref)
+
+
+def test_fourier_interp_has_no_adjoint(torch):
+    from paper_1904_09409_gb300 import funnel as f
+    with make_plan(32, 32, 32, 32, "fourier") as plan:
+        g = torch.zeros((1, 32, 32), device="cuda")
+        with pytest.raises(f.FunnelError) as e:
+            f.ft_backward(plan, g, torch.empty_like(g))
+        assert e.value.status == f.FT_ERR_UNSUPPORTED_SIZE
