@@ -229,6 +229,27 @@ float ft_batch_group_tuned_ms(ft_batch batch, int g);
 ft_status ft_batch_run(ft_batch batch, const float* d_imgs, float* d_maps, int top_k, float threshold,
                        ft_peak* d_out, int32_t* d_count, void* stream, int flags);
 
+/* ------------------------------------------------------------------------
+ * Split-precision tensor-core transforms (the DFT-by-GEMM variant of the FFT
+ * stages).  FT_PRECISION_FP32 is the FFT path; the other two evaluate DFTs as
+ * GEMMs on the sm_103a tensor cores (tcgen05.mma, FP32 accumulation in tensor
+ * memory) with every FP32 operand split into a high and a low 16-bit part,
+ * D = Ahi Bhi + Ahi Blo + Alo Bhi. */
+typedef enum {
+    FT_PRECISION_FP32 = 0,
+    FT_PRECISION_BF16X3 = 1,
+    FT_PRECISION_FP16X3 = 2
+} ft_precision;
+
+/* Batched 64-point complex DFT y[v][k] = sum_n x[v][n] exp(sign 2 pi i k n / 64)
+ * (sign = +1 or -1) for v < nvec, x and y [nvec][64] complex FP32 (interleaved,
+ * 8-byte aligned, device).  precision: FT_PRECISION_BF16X3 or _FP16X3.  d_err:
+ * a device uint32 that gets bit 0 set if a tensor-core wait timed out (the
+ * outputs of that block are then NaN); the caller clears it.  This is the
+ * building block of the split-precision FFT stages and their self-check. */
+ft_status ft_tc_dft64(const void* d_x, void* d_y, int nvec, int sign, int precision, uint32_t* d_err,
+                      void* stream);
+
 /* Bytes of plan-owned device workspace that a call with this batch needs. */
 size_t ft_workspace_bytes(ft_plan plan, int batch);
 

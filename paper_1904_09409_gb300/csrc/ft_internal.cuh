@@ -288,6 +288,11 @@ cudaError_t launch_nvmt_rows_fourier(float2* ws, int W, int S, int Hp, int L, co
                                      const FftLen& fm, const FftLen& fs, const float2* chirp_u,
                                      const float2* chirp_x, const float2* hc, int batch, cudaStream_t st);
 
+// batched 64-point DFT as a split-precision tensor-core GEMM (k_tc.cu);
+// fmt 1 = BF16 hi+lo, 0 = FP16 hi+lo; err gets bit 0 set if a wait timed out
+cudaError_t launch_tc_dft64(const float2* x, float2* y, int nvec, int sign, int fmt, unsigned* err,
+                            cudaStream_t st);
+
 // in[b][R][C] -> out[b][C][R] (k_transpose.cu)
 cudaError_t launch_transpose(const float* in, float* out, int R, int C, int batch, cudaStream_t st);
 

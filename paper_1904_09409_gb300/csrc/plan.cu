@@ -554,6 +554,17 @@ ft_status ft_abs_mse_grad(ft_plan p, const float* d_map, const float* d_target, 
     return FT_OK;
 }
 
+ft_status ft_tc_dft64(const void* d_x, void* d_y, int nvec, int sign, int precision, uint32_t* d_err,
+                      void* stream) {
+    if (!d_x || !d_y || !d_err || nvec < 0 || (sign != 1 && sign != -1)) return FT_ERR_INVALID_ARG;
+    if (precision != FT_PRECISION_BF16X3 && precision != FT_PRECISION_FP16X3) return FT_ERR_INVALID_ARG;
+    if (nvec == 0) return FT_OK;
+    FT_CUDA(launch_tc_dft64((const float2*)d_x, (float2*)d_y, nvec, sign, precision == FT_PRECISION_BF16X3 ? 1 : 0,
+                            d_err, (cudaStream_t)stream),
+            "ft_tc_dft64");
+    return FT_OK;
+}
+
 ft_status ft_profile_enable(ft_plan p, int enable) {
     if (!p) return FT_ERR_INVALID_ARG;
     p->prof_on = enable ? 1 : 0;

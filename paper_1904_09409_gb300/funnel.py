@@ -36,8 +36,12 @@ EXPORTED = (
     "ft_peaks_noalloc", "ft_abs_mse_grad", "ft_plan_create_space",
     "ft_plan_variant_count", "ft_plan_set_variant", "ft_plan_get_variant",
     "ft_batch_create", "ft_batch_destroy", "ft_batch_layout", "ft_batch_group_count",
-    "ft_batch_group_info", "ft_batch_group_tuned_ms", "ft_batch_run",
+    "ft_batch_group_info", "ft_batch_group_tuned_ms", "ft_batch_run", "ft_tc_dft64",
 )
+FT_PRECISION_FP32 = 0
+FT_PRECISION_BF16X3 = 1
+FT_PRECISION_FP16X3 = 2
+PRECISION_NAMES = {"fp32": FT_PRECISION_FP32, "bf16x3": FT_PRECISION_BF16X3, "fp16x3": FT_PRECISION_FP16X3}
 FT_BATCH_GRAPH = 1
 FT_BATCH_TUNE = 2
 FT_SPACE_REGULAR = 0
@@ -109,6 +113,8 @@ def lib() -> ctypes.CDLL:
     L.ft_batch_group_tuned_ms.argtypes = [vp, ci]
     L.ft_batch_group_tuned_ms.restype = cf
     L.ft_batch_run.argtypes = [vp, vp, vp, ci, cf, vp, vp, vp, ci]
+    L.ft_tc_dft64.argtypes = [vp, vp, ci, ci, ci, vp, vp]
+    L.ft_tc_dft64.restype = ci
     for name in ("ft_plan_variant_count", "ft_plan_set_variant", "ft_plan_get_variant", "ft_batch_create",
                  "ft_batch_destroy", "ft_batch_layout", "ft_batch_group_count", "ft_batch_group_info",
                  "ft_batch_run"):
@@ -338,6 +344,19 @@ def ft_status_string(status: int) -> str:
 
 def ft_last_error() -> str:
     return lib().ft_last_error().decode()
+
+
+def ft_tc_dft64(x, y, sign: int, precision, err, stream=None) -> None:
+    """Batched 64-point DFTs on the tensor cores; x, y: complex64 CUDA tensors
+    [nvec, 64]; err: int32 CUDA tensor of 1 element (bit 0 set on a wait timeout)."""
+    import torch
+    if x.dtype != torch.complex64 or y.dtype != torch.complex64 or not x.is_cuda or not y.is_cuda:
+        raise TypeError("x and y must be complex64 CUDA tensors")
+    if not (x.is_contiguous() and y.is_contiguous()) or x.shape[-1] != 64 or y.shape != x.shape:
+        raise ValueError("x, y: contiguous [nvec, 64]")
+    prec = PRECISION_NAMES[precision] if isinstance(precision, str) else int(precision)
+    _check(lib().ft_tc_dft64(x.data_ptr(), y.data_ptr(), x.shape[0], int(sign), prec,
+                             _dev_ptr(err, "int32", 1, "err"), _stream_ptr(stream)), "ft_tc_dft64")
 
 
 def ft_plan_set_variant(plan: Plan, variant: int) -> None:
