@@ -250,6 +250,26 @@ typedef enum {
 ft_status ft_tc_dft64(const void* d_x, void* d_y, int nvec, int sign, int precision, uint32_t* d_err,
                       void* stream);
 
+/* Arithmetic of step 3 (the transform along x' of eq. (13), Sec. 3.2) for
+ * this plan.  FT_PRECISION_FP32 (the default) is the FP32 FFT.  The split
+ * variants run steps 2-3 of ft_forward as the NVMT gather followed by a
+ * four-step DFT, 4096 = 64 x 64: two split-precision GEMMs (the 64-point DFT
+ * matrix against 64 rows of gathered or twiddled values) with FP32 twiddles in
+ * between, in one persistent kernel that keeps the DFT matrix in shared memory.
+ * Steps 1 and 4, the peaks and ft_backward stay FP32.  Returns
+ * FT_ERR_UNSUPPORTED_SIZE for a split precision unless n_slope = 4096 and the
+ * interpolator is linear or cubic (the plan keeps its previous precision);
+ * FT_ERR_INVALID_ARG for an unknown value.  Changes the result of later calls
+ * only. */
+ft_status ft_plan_set_precision(ft_plan plan, int precision);
+int ft_plan_get_precision(ft_plan plan);
+
+/* Error flags of the plan's tensor-core kernels: bit 0 is set when a wait for
+ * the tensor cores timed out (about 2 s; the kernel then stops and its rows are
+ * incomplete).  Waits for all work on the plan's device, copies the flags to
+ * *flags (host) and clears them.  0 when no split precision was ever set. */
+ft_status ft_plan_tc_errors(ft_plan plan, uint32_t* flags);
+
 /* Bytes of plan-owned device workspace that a call with this batch needs. */
 size_t ft_workspace_bytes(ft_plan plan, int batch);
 

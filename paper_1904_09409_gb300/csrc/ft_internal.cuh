@@ -213,6 +213,8 @@ struct ft_plan_s {
     int col_logB_max, row_logB_max;  // the largest that fit the shared-memory budget
     int use_fast_y, use_fast_x;      // fixed-length kernels in use for H' / S
     int variant;            // see ft_plan_set_variant
+    int precision;          // ft_precision of step 3 (ft_plan_set_precision)
+    unsigned* d_tc_err;     // error flags of the tensor-core kernels (allocated with the first split precision)
     // band-limited (chirp-z) interpolator: lengths W and M >= W + S, chirp tables
     FftLen fw, fm;
     float2* d_chirp;        // [L][W+1] pre-chirps, [L][S] post-chirps, [L][M] chirp spectra
@@ -292,6 +294,12 @@ cudaError_t launch_nvmt_rows_fourier(float2* ws, int W, int S, int Hp, int L, co
 // fmt 1 = BF16 hi+lo, 0 = FP16 hi+lo; err gets bit 0 set if a wait timed out
 cudaError_t launch_tc_dft64(const float2* x, float2* y, int nvec, int sign, int fmt, unsigned* err,
                             cudaStream_t st);
+// tables of the tensor-core kernels on the current device (host call, before any capture)
+cudaError_t tc_prepare();
+// Steps 2-3 for n_slope = 4096 with the split-precision four-step DFT (k_tc.cu);
+// tw = exp(-2 pi i t / 4096), t < 4096
+cudaError_t launch_nvmt_rows_tc4096(float2* ws, int W, int Hp, int L, int interp, int fmt, const float2* tw,
+                                    unsigned* err, int batch, cudaStream_t st);
 
 // in[b][R][C] -> out[b][C][R] (k_transpose.cu)
 cudaError_t launch_transpose(const float* in, float* out, int R, int C, int batch, cudaStream_t st);

@@ -13,8 +13,9 @@
 // two so that FP16 stays in range; the scale is undone on output.
 //
 // k_tc_dft64 is the building block and its own check (ft_tc_dft64); the row
-// transform of length 4096 = 64 x 64 in k_tc_rows4096 composes two of these GEMMs
+// transform of length 4096 = 64 x 64 in k_nvmt_rows_tc4096 composes two of these GEMMs
 // with a twiddle pass in between (four-step FFT).
+#include "fft_fast.cuh"
 #include "tc_common.cuh"
 
 #define TC_THREADS 128
@@ -154,16 +155,26 @@ static cudaError_t set_w64() {
     return cudaMemcpyToSymbol(g_w64, w, sizeof(w));
 }
 
-cudaError_t launch_tc_dft64(const float2* x, float2* y, int nvec, int sign, int fmt, unsigned* err,
-                            cudaStream_t st) {
+// g_w64 is set once per device (the first call on a device does it)
+static cudaError_t ensure_w64() {
     static int ready[64] = {0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 64 && !ready[dev]) {
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!ready[dev]) {
         if ((e = set_w64()) != cudaSuccess) return e;
         ready[dev] = 1;
     }
+    return cudaSuccess;
+}
+
+cudaError_t tc_prepare() { return ensure_w64(); }
+
+cudaError_t launch_tc_dft64(const float2* x, float2* y, int nvec, int sign, int fmt, unsigned* err,
+                            cudaStream_t st) {
+    cudaError_t e = ensure_w64();
+    if (e != cudaSuccess) return e;
     const size_t sm = dft64_smem();
     const dim3 grid((nvec + 63) / 64);
     if (fmt == 1) {
@@ -176,4 +187,254 @@ cudaError_t launch_tc_dft64(const float2* x, float2* y, int nvec, int sign, int 
         k_tc_dft64<0><<<grid, TC_THREADS, sm, st>>>(x, y, nvec, sign, err);
     }
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Steps 2-3 for n_slope = 4096 with the step-3 transform on the tensor cores.
+// Per frequency row: the NVMT gather (as in the FP32 row kernels) of
+// V[n] (-1)^n, then the four-step DFT with 4096 = 64 x 64 (n = n1 + 64 n2,
+// k = k2 + 64 k1), sign +1:
+//     A[k2][n1]  = sum_n2 exp(+2 pi i n2 k2 / 64) V[n1 + 64 n2]     GEMM 1 (B row n1)
+//     A'[k2][n1] = A[k2][n1] exp(+2 pi i n1 k2 / 4096)                 FP32 twiddles
+//     Y[k1][k2]  = sum_n1 exp(+2 pi i n1 k1 / 64) A'[k2][n1]           GEMM 2 (B row k2)
+//     G[k2 + 64 k1] = Y[k1][k2] (-1)^{k + S/2}
+// The gather writes GEMM 1's operand directly (each thread builds 16-byte runs
+// of 8 columns of one operand row), the twiddle pass writes GEMM 2's.  Each
+// operand gets a power-of-two scale, undone on output: for GEMM 1 from a bound
+// on |V| (the largest component of the spectrum row times the interpolator's
+// sum of |weights|), for GEMM 2 from the largest component of A (the twiddle
+// keeps |A'| = |A| <= sqrt(2) max component).  Persistent blocks loop over the
+// rows; the DFT matrix stays in shared memory and one 64-column TMEM
+// accumulator serves both GEMMs of every row.
+#define TCR_THREADS 256
+#define TCR_S 4096
+#define TCR_PITCH 65                                   // stage row pitch (floats): conflict-free rows and columns
+
+static constexpr size_t tcr_stage_bytes(int W) {
+    return (size_t)128 * TCR_PITCH * 4 > (size_t)(W + 2) * 8 ? (size_t)128 * TCR_PITCH * 4 : (size_t)(W + 2) * 8;
+}
+static size_t tcr_smem(int W) { return 2 * TC_A_BYTES + 2 * TC_B_BYTES + tcr_stage_bytes(W); }
+
+template <int FMT>
+__device__ __forceinline__ void split8(const float (&x)[8], uint4& hi, uint4& lo) {
+    uint16_t h[8], l[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) split16<FMT>(x[j], h[j], l[j]);
+    hi = make_uint4(h[0] | ((uint32_t)h[1] << 16), h[2] | ((uint32_t)h[3] << 16), h[4] | ((uint32_t)h[5] << 16),
+                    h[6] | ((uint32_t)h[7] << 16));
+    lo = make_uint4(l[0] | ((uint32_t)l[1] << 16), l[2] | ((uint32_t)l[3] << 16), l[4] | ((uint32_t)l[5] << 16),
+                    l[6] | ((uint32_t)l[7] << 16));
+}
+
+// Write 8 complex values (columns c0..c0+7 of operand row r) as hi/lo: real parts
+// to columns c0.., imaginary parts to c0 + 64.. of the K = 128 K-major tile.
+template <int FMT>
+__device__ __forceinline__ void put8(unsigned char* b_hi, unsigned char* b_lo, int r, int kg, const float (&re)[8],
+                                     const float (&im)[8]) {
+    const uint32_t off = (uint32_t)(((r >> 3) * 16 + kg) * 128 + (r & 7) * 16);
+    uint4 h, l;
+    split8<FMT>(re, h, l);
+    *reinterpret_cast<uint4*>(b_hi + off) = h;
+    *reinterpret_cast<uint4*>(b_lo + off) = l;
+    split8<FMT>(im, h, l);
+    *reinterpret_cast<uint4*>(b_hi + off + 1024) = h;
+    *reinterpret_cast<uint4*>(b_lo + off + 1024) = l;
+}
+
+template <int FMT, int INTERP>
+__global__ void __launch_bounds__(TCR_THREADS, 1)
+k_nvmt_rows_tc4096(float2* __restrict__ ws, int W, int Hp, int L, int total_rows,
+                   const float2* __restrict__ tw, unsigned* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    constexpr int S = TCR_S, T = TCR_THREADS, NW = T / 32, CW = 256 / NW;   // TMEM columns per warp
+    static_assert(CW % 16 == 0 && CW >= 16, "warps must split the 64 accumulator columns in x16 loads");
+    unsigned char* a_hi = sm;
+    unsigned char* a_lo = a_hi + TC_A_BYTES;
+    unsigned char* b_hi = a_lo + TC_A_BYTES;
+    unsigned char* b_lo = b_hi + TC_B_BYTES;
+    float* stage = reinterpret_cast<float*>(b_lo + TC_B_BYTES);         // [128][TCR_PITCH] accumulator copy
+    float2* srow = reinterpret_cast<float2*>(stage);                     // the spectrum row (aliases stage)
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    __shared__ float red[NW];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = warp & 3, c0 = (warp >> 2) * CW;     // TMEM lane quarter, first column
+
+    build_dft_matrix<FMT>(a_hi, a_lo, g_w64, +1);
+    if (threadIdx.x == 0) mbar_init(smem_u32(&mbar), 1);
+    if (warp == 0) {
+        tc_alloc(smem_u32(&tmem_base), 64);
+        tc_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    uint32_t parity = 0;
+
+    auto block_max = [&](float v) -> float {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) red[warp] = v;
+        __syncthreads();
+        float r = red[0];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) r = fmaxf(r, red[w]);
+        __syncthreads();
+        return r;
+    };
+    // issue the split GEMM on the current B and wait; block-uniform result
+    auto gemm = [&]() -> bool {
+        fence_async_smem();
+        __syncthreads();
+        tc_fence_after();
+        if (threadIdx.x == 0)
+            issue_split_gemm<FMT>(tmem, smem_u32(a_hi), smem_u32(a_lo), smem_u32(b_hi), smem_u32(b_lo),
+                                  smem_u32(&mbar));
+        bool ok = mbar_wait(smem_u32(&mbar), parity);
+        if (!ok) {
+            atomicOr(err, 1u);
+            mbar_wait(smem_u32(&mbar), parity);        // let our own MMAs drain
+        }
+        parity ^= 1u;
+        tc_fence_after();
+        return !__syncthreads_or(!ok);
+    };
+    // accumulator rows 32 q + lane, columns c0 .. c0 + CW - 1 -> stage; returns the max |value|
+    auto read_d = [&]() -> float {
+        float mx = 0.f;
+        const int r = 32 * q + lane;
+#pragma unroll
+        for (int c16 = 0; c16 < CW / 16; ++c16) {
+            float d[16];
+            tc_ld16(tmem + ((uint32_t)(32 * q) << 16) + c0 + 16 * c16, d);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                stage[r * TCR_PITCH + c0 + 16 * c16 + j] = d[j];
+                mx = fmaxf(mx, fabsf(d[j]));
+            }
+        }
+        tc_fence_before();
+        return mx;
+    };
+
+    for (int job = blockIdx.x; job < total_rows; job += gridDim.x) {
+        const int l = job % L;
+        float2* row = ws + (size_t)job * S;            // row l of image job / L
+        if (l == 0) {                                   // the DC row is zero
+            for (int k = threadIdx.x; k < S; k += T) row[k] = make_float2(0.f, 0.f);
+            continue;
+        }
+        for (int i = threadIdx.x; i < W / 2; i += T) cp_async16(srow + 2 * i, row + 2 * i);
+        cp_async_wait_all();
+        float mx = 0.f;
+        for (int i = threadIdx.x; i < W / 2; i += T) {  // this thread's own copies
+            const float4 v = *reinterpret_cast<const float4*>(srow + 2 * i);
+            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+        }
+        mx = block_max(mx) * (INTERP == FT_INTERP_LINEAR ? 1.f : 1.25f);   // sum of |Keys weights| <= 1.25
+        const int e1 = mx > 0.f ? ilogbf(mx) : 0;
+        const float s1 = ldexpf(1.f, 10 - e1);
+        // gather V[n1 + 64 n2] for n2 = 8 kg .. 8 kg + 7 straight into B row n1
+        {
+            const int den = 2 * l;
+            const float inv = 1.f / (float)den;
+            const int step = 64 * Hp;                   // n advances by 64 per n2
+            const int sA = step / den, sB = step - sA * den;
+            const int halfW = W >> 1;
+            const float2 zero = make_float2(0.f, 0.f);
+            for (int item = threadIdx.x; item < 512; item += T) {
+                const int r = (item & 7) | ((item >> 6) << 3), kg = (item >> 3) & 7;
+                const int n0 = r + 512 * kg;
+                const int num = (n0 - S / 2) * Hp;
+                int qf = floor_div(num, den), rem = num - qf * den;
+                float re[8], im[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float fr = (float)rem * inv;
+                    const int cc = qf + halfW;
+                    float2 acc;
+                    if (INTERP == FT_INTERP_LINEAR) {
+                        const float2 a0 = (unsigned)cc < (unsigned)W ? srow[cc] : zero;
+                        const float2 a1 = (unsigned)(cc + 1) < (unsigned)W ? srow[cc + 1] : zero;
+                        acc = make_float2(fmaf(fr, a1.x - a0.x, a0.x), fmaf(fr, a1.y - a0.y, a0.y));
+                    } else {
+                        acc = zero;
+#pragma unroll
+                        for (int d = -1; d <= 2; ++d) {
+                            const float2 a = (unsigned)(cc + d) < (unsigned)W ? srow[cc + d] : zero;
+                            const float w = keys_w(fr - (float)d);
+                            acc.x = fmaf(w, a.x, acc.x);
+                            acc.y = fmaf(w, a.y, acc.y);
+                        }
+                    }
+                    const float sg = (r & 1) ? -s1 : s1;          // (-1)^n, n = r + 64 (8 kg + j)
+                    re[j] = acc.x * sg;
+                    im[j] = acc.y * sg;
+                    rem += sB;
+                    qf += sA;
+                    if (rem >= den) { rem -= den; qf += 1; }
+                }
+                put8<FMT>(b_hi, b_lo, r, kg, re, im);
+            }
+        }
+        if (!gemm()) break;
+        mx = block_max(read_d());                       // also orders the stage writes before the reads below
+        const int e2 = mx > 0.f ? ilogbf(mx) : 0;
+        const float s2 = ldexpf(1.f, 10 - e2);
+        // twiddle A[k2][n1] (rows k2 / k2 + 64 of stage) and write B row k2
+        for (int item = threadIdx.x; item < 512; item += T) {
+            const int k2 = (item & 7) | ((item >> 6) << 3), kg = (item >> 3) & 7;
+            float re[8], im[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int n1 = 8 * kg + j;
+                const float2 w = __ldg(tw + n1 * k2);   // exp(-2 pi i n1 k2 / S), n1 k2 < S
+                const float a = stage[k2 * TCR_PITCH + n1], b = stage[(k2 + 64) * TCR_PITCH + n1];
+                re[j] = (a * w.x + b * w.y) * s2;       // (a + i b) conj(w)
+                im[j] = (b * w.x - a * w.y) * s2;
+            }
+            put8<FMT>(b_hi, b_lo, k2, kg, re, im);
+        }
+        if (!gemm()) break;
+        read_d();
+        __syncthreads();
+        const float un = ldexpf(1.f, e1 + e2 - 20);
+        for (int k = threadIdx.x; k < S; k += T) {
+            const int k1 = k >> 6, k2 = k & 63;
+            const float sg = ((k + S / 2) & 1) ? -un : un;
+            row[k] = make_float2(stage[k1 * TCR_PITCH + k2] * sg, stage[(k1 + 64) * TCR_PITCH + k2] * sg);
+        }
+        __syncthreads();                                // stage is the next row's srow
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc_dealloc(tmem, 64);
+}
+
+template <int FMT, int INTERP>
+static cudaError_t go_tc_rows(float2* ws, int W, int Hp, int L, int batch, const float2* tw, unsigned* err,
+                              cudaStream_t st) {
+    const size_t sm = tcr_smem(W);
+    cudaError_t e = cudaFuncSetAttribute(k_nvmt_rows_tc4096<FMT, INTERP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int total = batch * L;
+    k_nvmt_rows_tc4096<FMT, INTERP><<<total < sms ? total : sms, TCR_THREADS, sm, st>>>(ws, W, Hp, L, total, tw, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nvmt_rows_tc4096(float2* ws, int W, int Hp, int L, int interp, int fmt, const float2* tw,
+                                    unsigned* err, int batch, cudaStream_t st) {
+    if (W <= 0 || W > TCR_S || (W & 1)) return cudaErrorInvalidValue;
+    cudaError_t e = ensure_w64();
+    if (e != cudaSuccess) return e;
+    if (interp == FT_INTERP_LINEAR)
+        return fmt == 1 ? go_tc_rows<1, FT_INTERP_LINEAR>(ws, W, Hp, L, batch, tw, err, st)
+                        : go_tc_rows<0, FT_INTERP_LINEAR>(ws, W, Hp, L, batch, tw, err, st);
+    return fmt == 1 ? go_tc_rows<1, FT_INTERP_CUBIC>(ws, W, Hp, L, batch, tw, err, st)
+                    : go_tc_rows<0, FT_INTERP_CUBIC>(ws, W, Hp, L, batch, tw, err, st);
 }

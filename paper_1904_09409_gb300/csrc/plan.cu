@@ -224,6 +224,9 @@ static cudaError_t nvmt_rows(ft_plan p, float2* ws, int batch, cudaStream_t st) 
         return launch_nvmt_rows_fourier(ws, p->W, p->S, p->Hp, p->L, p->fw, p->fm, p->fx, p->d_chirp,
                                         p->d_chirp + nu, p->d_chirp + nu + nx, batch, st);
     }
+    if (p->precision != FT_PRECISION_FP32)
+        return launch_nvmt_rows_tc4096(ws, p->W, p->Hp, p->L, p->interp, p->precision == FT_PRECISION_BF16X3 ? 1 : 0,
+                                       p->fx.tw, p->d_tc_err, batch, st);
     if (p->use_fast_x) return launch_nvmt_rows_fast(ws, p->W, p->Hp, p->L, p->interp, p->fx, batch, st);
     return launch_nvmt_rows(ws, p->W, p->S, p->Hp, p->L, p->interp, p->fx, p->row_logB_x, batch, st);
 }
@@ -358,6 +361,7 @@ ft_status ft_plan_destroy(ft_plan p) {
     free_ws(p);
     if (p->d_tw) cudaFree(p->d_tw);
     if (p->d_chirp) cudaFree(p->d_chirp);
+    if (p->d_tc_err) cudaFree(p->d_tc_err);
     if (p->d_img_host) cudaFree(p->d_img_host);
     if (p->d_map_host) cudaFree(p->d_map_host);
     if (p->d_peaks_host) cudaFree(p->d_peaks_host);
@@ -397,6 +401,47 @@ ft_status ft_plan_set_variant(ft_plan p, int variant) {
 }
 
 int ft_plan_get_variant(ft_plan p) { return p ? p->variant : -1; }
+
+ft_status ft_plan_set_precision(ft_plan p, int precision) {
+    if (!p || precision < FT_PRECISION_FP32 || precision > FT_PRECISION_FP16X3) return FT_ERR_INVALID_ARG;
+    if (precision != FT_PRECISION_FP32) {
+        if (p->S != 4096 || p->interp == FT_INTERP_FOURIER)
+            return ft_record_error(FT_ERR_UNSUPPORTED_SIZE, "split precision: n_slope 4096, linear or cubic only");
+        if (!p->d_tc_err) {
+            int cur = 0;
+            FT_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
+            FT_CUDA(cudaSetDevice(p->device), "cudaSetDevice");
+            cudaError_t e = cudaMalloc(&p->d_tc_err, sizeof(unsigned));
+            if (e == cudaSuccess) e = cudaMemset(p->d_tc_err, 0, sizeof(unsigned));
+            if (e == cudaSuccess) e = tc_prepare();
+            cudaSetDevice(cur);
+            if (e != cudaSuccess) {
+                if (p->d_tc_err) cudaFree(p->d_tc_err);
+                p->d_tc_err = nullptr;
+                return ft_record_cuda(e, "tensor-core error flags");
+            }
+        }
+    }
+    p->precision = precision;
+    return FT_OK;
+}
+
+int ft_plan_get_precision(ft_plan p) { return p ? p->precision : -1; }
+
+ft_status ft_plan_tc_errors(ft_plan p, uint32_t* flags) {
+    if (!p || !flags) return FT_ERR_INVALID_ARG;
+    *flags = 0;
+    if (!p->d_tc_err) return FT_OK;
+    int cur = 0;
+    FT_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
+    FT_CUDA(cudaSetDevice(p->device), "cudaSetDevice");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(flags, p->d_tc_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(p->d_tc_err, 0, sizeof(unsigned));
+    cudaSetDevice(cur);
+    FT_CUDA(e, "ft_plan_tc_errors");
+    return FT_OK;
+}
 
 size_t ft_workspace_bytes(ft_plan p, int batch) {
     if (!p || batch <= 0) return 0;

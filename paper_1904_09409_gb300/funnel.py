@@ -37,6 +37,7 @@ EXPORTED = (
     "ft_plan_variant_count", "ft_plan_set_variant", "ft_plan_get_variant",
     "ft_batch_create", "ft_batch_destroy", "ft_batch_layout", "ft_batch_group_count",
     "ft_batch_group_info", "ft_batch_group_tuned_ms", "ft_batch_run", "ft_tc_dft64",
+    "ft_plan_set_precision", "ft_plan_get_precision", "ft_plan_tc_errors",
 )
 FT_PRECISION_FP32 = 0
 FT_PRECISION_BF16X3 = 1
@@ -115,6 +116,12 @@ def lib() -> ctypes.CDLL:
     L.ft_batch_run.argtypes = [vp, vp, vp, ci, cf, vp, vp, vp, ci]
     L.ft_tc_dft64.argtypes = [vp, vp, ci, ci, ci, vp, vp]
     L.ft_tc_dft64.restype = ci
+    L.ft_plan_set_precision.argtypes = [vp, ci]
+    L.ft_plan_set_precision.restype = ci
+    L.ft_plan_get_precision.argtypes = [vp]
+    L.ft_plan_get_precision.restype = ci
+    L.ft_plan_tc_errors.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
+    L.ft_plan_tc_errors.restype = ci
     for name in ("ft_plan_variant_count", "ft_plan_set_variant", "ft_plan_get_variant", "ft_batch_create",
                  "ft_batch_destroy", "ft_batch_layout", "ft_batch_group_count", "ft_batch_group_info",
                  "ft_batch_run"):
@@ -365,6 +372,23 @@ def ft_plan_set_variant(plan: Plan, variant: int) -> None:
 
 def ft_plan_get_variant(plan: Plan) -> int:
     return int(lib().ft_plan_get_variant(plan.handle))
+
+
+def ft_plan_set_precision(plan: Plan, precision) -> None:
+    """Arithmetic of step 3: "fp32", "bf16x3" or "fp16x3" (or the FT_PRECISION_* value)."""
+    prec = PRECISION_NAMES[precision] if isinstance(precision, str) else int(precision)
+    _check(lib().ft_plan_set_precision(plan.handle, prec), "ft_plan_set_precision")
+
+
+def ft_plan_get_precision(plan: Plan) -> int:
+    return int(lib().ft_plan_get_precision(plan.handle))
+
+
+def ft_plan_tc_errors(plan: Plan) -> int:
+    """Waits for the device, returns and clears the tensor-core error flags."""
+    v = ctypes.c_uint32(0)
+    _check(lib().ft_plan_tc_errors(plan.handle, ctypes.byref(v)), "ft_plan_tc_errors")
+    return int(v.value)
 
 
 class Batch:

@@ -33,3 +33,88 @@ def test_dft64_on_tensor_cores(torch, precision, sign, nvec, scale):
     got = yd.cpu().numpy().astype(np.complex128)
     e = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     assert e <= TOL[precision], (precision, e)
+
+
+# ------------------------------------------------ steps 2-3 as a four-step DFT
+# The split-precision row transform (n_slope = 4096) against the FP64 oracle
+# map.  The relative L2 bar of the parameter map is 1e-5 for every variant.
+TOL_MAP = {"fp32": 1e-5, "bf16x3": 1e-5, "fp16x3": 1e-5}
+
+
+def _plan(H, W, Hp, interp, precision):
+    from paper_1904_09409_gb300 import funnel as f
+    plan = f.Plan(H, W, 4096, Hp, interp)
+    f.ft_plan_set_precision(plan, precision)
+    assert f.ft_plan_get_precision(plan) == f.PRECISION_NAMES[precision]
+    return plan
+
+
+def _images(n, H, W, seed):
+    from paper_1904_09409_gb300 import synth
+    return np.stack([synth.mixed_image(synth.WL_LARGE_4096, seed + i, H, W).img for i in range(n)])
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "fp16x3"])
+@pytest.mark.parametrize("n,H,W,Hp,interp", [
+    (3, 256, 1024, 256, "linear"),      # 387 rows over the persistent blocks
+    (1, 200, 4096, 512, "cubic"),       # full-width rows, padded intercepts
+    (5, 96, 2048, 96, "linear"),        # n_intercept 2^5 * 3, a lane split
+    (1, 64, 4096, 8192, "cubic"),       # 4097 rows, steep funnel
+])
+def test_split_precision_rows_match_oracle(torch, precision, n, H, W, Hp, interp):
+    import oracle
+    from paper_1904_09409_gb300 import funnel as f
+    imgs = _images(n, H, W, 11 * H + W)
+    with _plan(H, W, Hp, interp, precision) as plan:
+        got = _gpu.forward(plan, imgs)
+        assert f.ft_plan_tc_errors(plan) == 0
+    for i in range(n):
+        ref = oracle.funnel_ref(imgs[i].astype(np.float64), 4096, Hp, interp)
+        e = _gpu.rel_l2(got[i], ref)
+        print(f"{precision} {interp} {H}x{W}->{Hp}x4096 image {i}: rel-L2 {e:.3e}")
+        assert e <= TOL_MAP[precision], (precision, i, e)
+
+
+def test_split_precision_settings(torch):
+    from paper_1904_09409_gb300 import funnel as f
+    with f.Plan(64, 64, 1024, 64, "linear") as plan:
+        with pytest.raises(f.FunnelError) as ex:
+            f.ft_plan_set_precision(plan, "bf16x3")
+        assert ex.value.status == f.FT_ERR_UNSUPPORTED_SIZE
+        assert f.ft_plan_get_precision(plan) == f.FT_PRECISION_FP32
+        assert f.ft_plan_tc_errors(plan) == 0
+    with f.Plan(64, 64, 4096, 64, "fourier") as plan:
+        with pytest.raises(f.FunnelError):
+            f.ft_plan_set_precision(plan, "fp16x3")
+    with f.Plan(64, 64, 4096, 64, "linear") as plan:
+        with pytest.raises(f.FunnelError) as ex:
+            f.ft_plan_set_precision(plan, 7)
+        assert ex.value.status == f.FT_ERR_INVALID_ARG
+        f.ft_plan_set_precision(plan, "fp16x3")
+        f.ft_plan_set_precision(plan, "fp32")          # back to the FFT path
+        assert f.ft_plan_get_precision(plan) == f.FT_PRECISION_FP32
+
+
+def test_split_precision_4096_image_and_top100(torch):
+    """The precision workload's image size (4096^2, 100 lines, noise 0.2): every
+    variant against the FP64 map, and the top-100 peaks of each variant against
+    the FP64 list wherever that list is unambiguous at the variant's error."""
+    import oracle
+    from paper_1904_09409_gb300 import funnel as f, synth
+    img = synth.large_4096(1)[0].img
+    ref = oracle.funnel_ref(img.astype(np.float64), 4096, 4096, "linear")
+    ref_pk = oracle.peaks_ref(np.abs(ref), 100)
+    ref_set = {(t, s) for t, s, _ in ref_pk}
+    for precision in ("fp32", "bf16x3", "fp16x3"):
+        with _plan(4096, 4096, 4096, "linear", precision) as plan:
+            got = _gpu.forward(plan, img[None])[0]
+            pk, _ = _gpu.peaks(plan, got[None], 100)
+            assert f.ft_plan_tc_errors(plan) == 0
+        e = _gpu.rel_l2(got, ref)
+        agree = len(ref_set & {(t, s) for t, s, _ in pk[0]})
+        print(f"{precision} 4096^2: rel-L2 {e:.3e}, top-100 agreement {agree}/100")
+        assert e <= TOL_MAP[precision], (precision, e)
+        # the peaks of the variant's own map are what ft_peaks promises
+        assert pk[0] == oracle.peaks_ref(np.abs(got).astype(np.float64), 100)
+        tol = 4 * e * np.abs(ref).max()
+        assert not _gpu.robust_rank_mismatches(ref, ref_pk, pk[0], tol), precision
