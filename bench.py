@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-varlen", action="store_true", help="skip the mixed-size batch measurement")
+    ap.add_argument("--no-precision", action="store_true", help="skip the 8 x 4096^2 split-precision leg")
     ap.add_argument("--no-extras", action="store_true",
                     help="time only the main step (no e2e, forward+backward or mixed-size legs), for ncu captures")
     ap.add_argument("--images", type=int, default=64,
@@ -250,6 +251,73 @@ def _varlen_img(args):
     return synth.varlen_image(idx, h, w).img
 
 
+def _large_img(i):
+    from paper_1904_09409_gb300 import synth
+    return synth.large_4096(1, start=i)[0].img
+
+
+def large_images(pool, count=8):
+    return pool.map(_large_img, list(range(count)), chunksize=1)
+
+
+def time_precision(f, imgs, steps, stream, dev):
+    """8 x 4096^2 (100 lines each): forward + top-100 peaks per step-3 precision.
+    The split variants are compared with the FP32 path's maps and peaks on the
+    device (their error against the FP64 oracle is what the GPU tests check)."""
+    import torch
+    x = torch.from_numpy(np.stack(imgs)).to(dev)
+    B = x.shape[0]
+    K = 100
+    maps, peaks, out = {}, {}, {}
+    for prec in ("fp32", "bf16x3", "fp16x3"):
+        plan = f.Plan(4096, 4096, 4096, 4096, "linear")
+        f.ft_plan_set_precision(plan, prec)
+        m = torch.empty((B, 4096, 4096), dtype=torch.float32, device=dev)
+        pk = torch.empty(B * K * f.PEAK_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        cn = torch.empty(B, dtype=torch.int32, device=dev)
+
+        def step():
+            f.ft_forward(plan, x, m, stream=stream)
+            f.ft_peaks(plan, m, K, out=pk, count=cn, stream=stream)
+
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize(dev)
+        f.ft_profile_enable(plan, True)
+        f.ft_profile_read(plan)
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for _ in range(steps):
+            step()
+        q1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = q0.elapsed_time(q1) / steps
+        prof = f.ft_profile_read(plan)
+        errs = f.ft_plan_tc_errors(plan)
+        res = f.peaks_to_numpy(pk, cn, K)
+        peaks[prec] = [{(int(p["t"]), int(p["s"])) for p in r} for r in res]
+        out[prec] = {"value": B * 4096 * 4096 / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms,
+                     "steps": steps, "tc_error_flags": errs,
+                     "kernels_us_per_launch": {k: v[0] / v[1] * 1e3 for k, v in prof.items()}}
+        if prec == "fp32":
+            maps[prec] = m
+        else:
+            ref = maps["fp32"]
+            num = sum(float(torch.linalg.vector_norm((m[i].double() - ref[i].double()))) ** 2 for i in range(B))
+            den = sum(float(torch.linalg.vector_norm(ref[i].double())) ** 2 for i in range(B))
+            out[prec]["rel_l2_vs_fp32_path"] = (num / den) ** 0.5
+            out[prec]["top100_agreement_vs_fp32_path"] = sum(
+                len(a & b) for a, b in zip(peaks[prec], peaks["fp32"])) / (B * K)
+            del m
+        plan.close()
+    del maps, x
+    torch.cuda.empty_cache()
+    return {"workload": "8 x 4096^2 images, 100 lines each (mixed edge types, noise 0.2), n_slope = "
+                        "n_intercept = 4096, linear NVMT: ft_forward + top-100 peaks; step 3 in FP32 "
+                        "(FFT) or as the split-precision four-step DFT on the tensor cores",
+            "variants": out}
+
+
 def varlen_images(pool, shapes):
     return pool.map(_varlen_img, [(i, h, w) for i, (h, w) in enumerate(shapes)], chunksize=4)
 
@@ -369,9 +437,13 @@ def run_ours(args):
     cpu = None
     vl_shapes = synth.varlen_shapes(512)
     vl_imgs = None
-    if not (args.no_varlen or args.no_extras):
+    big_imgs = None
+    if not args.no_extras:
         with oracle_pool(min(host_cores(), 32)) as pool:
-            vl_imgs = varlen_images(pool, vl_shapes)
+            if not args.no_varlen:
+                vl_imgs = varlen_images(pool, vl_shapes)
+            if not args.no_precision:
+                big_imgs = large_images(pool, 8)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(imgs)
 
@@ -414,7 +486,7 @@ def run_ours(args):
     ms = replicas.max_over_ranks(ms, dev)
 
     extra = {} if args.no_extras else run_extras(f, args, plan, imgs, lines, x, stream, dev, rank, ws,
-                                                  vl_imgs, vl_shapes)
+                                                  vl_imgs, vl_shapes, big_imgs)
 
     px_step = ws * BATCH * SIDE * SIDE
     value = args.steps * px_step / (ms / 1e3) / 1e6
@@ -461,7 +533,7 @@ def run_ours(args):
     return 0
 
 
-def run_extras(f, args, plan, imgs, lines, x, stream, dev, rank, ws, vl_imgs, vl_shapes):
+def run_extras(f, args, plan, imgs, lines, x, stream, dev, rank, ws, vl_imgs, vl_shapes, big_imgs):
     """e2e through ft_detect_host, forward+backward legs, the mixed-size batch and
     the host-to-device copy rate; returns the extra JSON keys."""
     import torch
@@ -520,6 +592,10 @@ def run_extras(f, args, plan, imgs, lines, x, stream, dev, rank, ws, vl_imgs, vl
     fplan.close()
     del mf
 
+    precision = None
+    if big_imgs is not None:
+        precision = time_precision(f, big_imgs, max(3, min(args.steps, 20)), stream, dev)
+
     # host -> device copy rate of the pinned image buffer (context for e2e)
     hd = torch.empty_like(x)
     c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -536,6 +612,7 @@ def run_extras(f, args, plan, imgs, lines, x, stream, dev, rank, ws, vl_imgs, vl
                 "d2h_bytes_per_step": ws * (BATCH * TOP_K * f.PEAK_DTYPE.itemsize + BATCH * 4),
                 "call": "ft_detect_host", "steps": e2e_steps, "h2d_copy_gbs": h2d_gbs},
         "varlen": varlen,
+        "precision_4096": precision,
         "fourier_interp": {"value": px_step / (fo_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": fo_ms,
                            "steps": fo_steps,
                            "workload": "the same 64 x 1024^2 step (forward + top-32 peaks) with the band-limited "

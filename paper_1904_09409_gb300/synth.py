@@ -81,6 +81,13 @@ def render_step(img: np.ndarray, k: float, b_c: float, h: float) -> None:
     img += h * (rows > thr)
 
 
+def step_first_rows(H: int, W: int, k: float, b_c: float) -> np.ndarray:
+    """Per column, the first row strictly below the edge row = k*col + b_c
+    (H where there is none): the rows that render_step raises start there."""
+    thr = k * np.arange(W) + b_c
+    return np.clip(np.floor(thr).astype(np.int64) + 1, 0, H)
+
+
 def line_col_extent(H: int, W: int, k: float, b_c: float) -> Tuple[float, float]:
     """Column interval over which row = k*col + b_c stays inside [0, H-1]."""
     lo, hi = 0.0, float(W - 1)
@@ -127,11 +134,15 @@ def draw_lines(rng: np.random.Generator, n_lines: int, H: int, ridge_frac: float
 def compose(rng: np.random.Generator, H: int, W: int, lines: Sequence[Line],
             occlusion_max: float, noise_sigma: float, background: float) -> SynthImage:
     img = np.full((H, W), background, dtype=np.float64)
+    steps = np.zeros((H + 1, W), dtype=np.float64)      # step heights at their first rows
+    cols = np.arange(W)
     for ln in lines:
         if ln.kind == "ridge":
             render_ridge(img, ln.k, ln.b_c, ln.sigma, ln.amp)
         else:
-            render_step(img, ln.k, ln.b_c, ln.amp)
+            steps[step_first_rows(H, W, ln.k, ln.b_c), cols] += ln.amp
+    if any(ln.kind == "step" for ln in lines):
+        img += np.cumsum(steps, axis=0)[:H]              # the same half-planes as render_step
     if occlusion_max > 0.0:
         for ln in lines:
             occlude(img, ln, rng.uniform(0.0, occlusion_max), rng, background)

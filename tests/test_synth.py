@@ -42,3 +42,15 @@ def test_ridge_profile_peak_on_the_line():
     img = np.zeros((64, 64))
     synth.render_ridge(img, 0.0, 20.0, 1.5, 1.0)
     assert np.allclose(img[20], 1.0) and np.allclose(img[21], np.exp(-1 / (2 * 1.5 ** 2)))
+
+
+def test_step_edges_match_the_half_plane_definition():
+    """compose() paints step edges through first-row increments; the result is
+    the half-plane sum of render_step."""
+    rng = synth.rng_for(99, 0)
+    lines = synth.draw_lines(rng, 12, 64, 0.0, (1.0, 1.0), 1.0, (0.3, 1.0))
+    got = synth.compose(synth.rng_for(99, 1), 64, 80, lines, 0.0, 0.0, 0.25).img
+    ref = np.full((64, 80), 0.25)
+    for ln in lines:
+        synth.render_step(ref, ln.k, ln.b_c, ln.amp)
+    assert np.max(np.abs(got - ref)) <= 1e-6
