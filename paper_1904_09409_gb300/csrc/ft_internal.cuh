@@ -273,15 +273,18 @@ cudaError_t launch_nvmt_rows_adjoint(float2* ws, int W, int S, int Hp, int L, in
 
 // Peak detection of Sec. 4.4: per-tile strict local maxima -> per-tile best
 // keys (launch_peak_tiles), then per-image selection of the top_k keys in order
-// (launch_peak_select).  keys must hold peaks_key_bytes() bytes.
+// (launch_peak_select).  keys must hold peaks_key_bytes() bytes.  bounds holds
+// two words per image (the running bound of the top_k-th value and the length
+// of the image's appended key list); the sub-batch of images b0.. uses
+// keys + b0 * peaks_tile_keys() and bounds + 2 * b0.
 cudaError_t launch_peak_tiles(const float* map, int Hp, int S, int batch, int top_k, float threshold,
                               unsigned long long* keys, unsigned* bounds, cudaStream_t st);
-// keys per image, and the running bounds (one per image) inside a key buffer
-// of peaks_key_bytes(Hp, S, batch, top_k) bytes
+// keys per image, and the per-image words inside a key buffer of
+// peaks_key_bytes(Hp, S, batch, top_k) bytes
 size_t peaks_tile_keys(int Hp, int S, int top_k);
 unsigned* peaks_bounds(unsigned long long* keys, int Hp, int S, int batch, int top_k);
-cudaError_t launch_peak_select(const unsigned long long* keys, int Hp, int S, int batch, int top_k,
-                               ft_peak* out, int32_t* count, cudaStream_t st);
+cudaError_t launch_peak_select(const unsigned long long* keys, const unsigned* bounds, int Hp, int S, int batch,
+                               int top_k, ft_peak* out, int32_t* count, cudaStream_t st);
 size_t peaks_key_bytes(int Hp, int S, int batch, int top_k);
 
 // the band-limited NVMT fused with step 3 (k_fourier.cu)

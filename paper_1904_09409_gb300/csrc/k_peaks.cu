@@ -15,14 +15,18 @@
 //                 512 per tile; neighbour indices are computed only to break exact
 //                 ties), and keep the best min(top_k, 512) by radix selection.
 //  k_peak_tiles_fast  the same for maps with S % 128 == 0 and H' % 32 == 0, one
-//                 block per 32 x 128 tile without a shared-memory copy: each lane
-//                 holds 4 columns of 6 rows (float4 loads), column neighbours come
-//                 from the adjacent lanes by shuffles, candidates are appended per
-//                 warp with one scan (at most 1024 per tile); a cell is tested
-//                 against the max of its 8 neighbours (a vertical max per column
-//                 first), exact ties alone take the index comparison.
+//                 block per 32 x 128 tile (image index fastest in the grid): the
+//                 tile and its halo are copied with cp.async, each lane tests 4
+//                 columns of 4 rows against the max of their 8 neighbours (exact
+//                 ties alone take the index comparison), candidates are appended
+//                 per warp with one scan (at most 1024 per tile).  The tile's best
+//                 min(top_k, 512) keys go to the tile's own slots or, for large
+//                 maps, are appended to the image's key list (one atomic per
+//                 tile); a per-image running bound of the top_k-th value lets
+//                 later tiles drop dimmer candidates early.
 //  k_peak_select  one block per image: radix selection of the top_k keys among
-//                 the tiles' keys, then a bitonic sort of those top_k and the
+//                 the tiles' keys (the appended list, or every tile's slots for
+//                 the generic tiles), then a bitonic sort of those top_k and the
 //                 ft_peak records.
 //
 // Radix selection (cta_select): MSB-first passes over 8-bit digits of the
@@ -228,11 +232,12 @@ k_peak_tiles(const float* __restrict__ map, int Hp, int S, int KT, float thr, u6
 }
 
 __global__ void __launch_bounds__(PK_SEL_THREADS)
-k_peak_select(const u64* __restrict__ keys, int n, int K, int Hp, int S, ft_peak* __restrict__ out,
-              int32_t* __restrict__ count) {
+k_peak_select(const u64* __restrict__ keys, const unsigned* __restrict__ bounds, int n, int K, int Hp, int S,
+              ft_peak* __restrict__ out, int32_t* __restrict__ count) {
     __shared__ u64 sel[FT_MAX_TOPK];
     __shared__ SelState st;
     const u64* kk = keys + (size_t)blockIdx.x * n;
+    if (bounds) n = min(n, (int)bounds[2 * blockIdx.x + 1]);   // appended key lists hold fewer keys
     cta_select(kk, n, K, st);
     if (threadIdx.x == 0) st.count = 0;
     __syncthreads();
@@ -280,12 +285,14 @@ struct TileShared {
     u64 cand[PF_CAND];
     int ncand;
     unsigned kth_bits;
+    unsigned base;          // first slot of this tile's keys in the image's key list
     SelState st;
 };
 
 __device__ __forceinline__ void peak_tile_fast(const float* __restrict__ m, int Hp, int S, int KT, float thr,
-                                               int img, int ty, int tx, u64* __restrict__ out,
-                                               unsigned* __restrict__ tau, TileShared& sh) {
+                                               int img, int ty, int tx, int tile, u64* __restrict__ out,
+                                               unsigned* __restrict__ tau, unsigned* __restrict__ fill,
+                                               TileShared& sh) {
     u64* cand = sh.cand;
     SelState& st = sh.st;
     const int warp = threadIdx.x >> 5;
@@ -298,7 +305,7 @@ __device__ __forceinline__ void peak_tile_fast(const float* __restrict__ m, int 
     }
     // running lower bound of the image's top_k-th peak value (see launch_peak_tiles)
     float lower = thr;
-    if (tau) lower = fmaxf(lower, __uint_as_float(__ldcg(tau + img)));
+    if (tau) lower = fmaxf(lower, __uint_as_float(__ldcg(tau)));
 
     // the tile with its one-cell halo, |.| applied when read: PF_TT + 2 rows of
     // PF_TS + 2 columns (interior at 16-byte aligned offset 4, halo at 3 and
@@ -390,9 +397,19 @@ __device__ __forceinline__ void peak_tile_fast(const float* __restrict__ m, int 
     }
     __syncthreads();
     const int n = min(sh.ncand, PF_CAND);
+    if (fill) {
+        // the tile's min(n, KT) keys are appended to the image's key list
+        if (n == 0) return;
+        if (threadIdx.x == 0) sh.base = atomicAdd(fill, (unsigned)min(n, KT));
+        __syncthreads();
+        out += sh.base;
+    } else {
+        // the tile's KT slots, unused ones zero
+        out += (size_t)tile * KT;
+        for (int i = n + threadIdx.x; i < KT; i += blockDim.x) out[i] = 0ull;
+    }
     if (n < KT) {
-        for (int i = threadIdx.x; i < KT; i += blockDim.x) out[i] = i < n ? cand[i] : 0ull;
-        __syncthreads();                                   // cand / ncand reused by the next tile
+        for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = cand[i];
         return;
     }
     if (n == KT) {
@@ -415,8 +432,7 @@ __device__ __forceinline__ void peak_tile_fast(const float* __restrict__ m, int 
     // this tile alone has top_k candidates >= kth: the image's top_k-th peak is
     // at least that bright, so later tiles may drop anything dimmer
     __syncthreads();
-    if (tau && threadIdx.x == 0) atomicMax(tau + img, sh.kth_bits);
-    __syncthreads();                                       // cand / ncand reused by the next tile
+    if (tau && threadIdx.x == 0) atomicMax(tau, sh.kth_bits);
 }
 
 // One block per tile; the image index runs fastest in the grid, so the blocks of
@@ -424,17 +440,25 @@ __device__ __forceinline__ void peak_tile_fast(const float* __restrict__ m, int 
 // each image's running bound already raised.
 __global__ void __launch_bounds__(PK_TILE_THREADS)
 k_peak_tiles_fast(const float* __restrict__ map, int Hp, int S, int KT, float thr, u64* __restrict__ keys,
-                  unsigned* __restrict__ tau) {
+                  unsigned* __restrict__ bounds, int use_tau, int compact) {
     __shared__ TileShared sh;
     const int img = blockIdx.x;
     const int tile = blockIdx.y;
     const int ntx = S / PF_TS, ntiles = ntx * (Hp / PF_TT);
     const int ty = tile / ntx, tx = tile - ty * ntx;
-    peak_tile_fast(map + (size_t)img * Hp * S, Hp, S, KT, thr, img, ty, tx,
-                   keys + ((size_t)img * ntiles + tile) * KT, tau, sh);
+    peak_tile_fast(map + (size_t)img * Hp * S, Hp, S, KT, thr, img, ty, tx, tile, keys + (size_t)img * ntiles * KT,
+                   use_tau ? bounds + 2 * img : nullptr, compact ? bounds + 2 * img + 1 : nullptr, sh);
 }
 
 static int kt_of(int top_k) { return top_k < PK_CAND ? top_k : PK_CAND; }
+
+// Key layout of the register tiles: every tile's KT slots (zero when unused)
+// while the selection can afford to scan them all, else one appended list per
+// image (one global atomic per tile, the selection reads only real keys).
+#define PK_COMPACT_MIN 32768
+static bool compact_keys(int Hp, int S, int top_k) {
+    return (long long)(S / PF_TS) * (Hp / PF_TT) * kt_of(top_k) > PK_COMPACT_MIN;
+}
 
 static bool fast_tiles(int Hp, int S) { return S % PF_TS == 0 && Hp % PF_TT == 0; }
 
@@ -452,9 +476,9 @@ static size_t key_bytes(int Hp, int S, int batch, int top_k) {
     return ((size_t)batch * peaks_tile_keys(Hp, S, top_k) * sizeof(u64) + 255) & ~(size_t)255;
 }
 
-// scratch: the tiles' keys, then one running bound per image
+// scratch: the tiles' keys, then per image {running bound, key count}
 size_t peaks_key_bytes(int Hp, int S, int batch, int top_k) {
-    return key_bytes(Hp, S, batch, top_k) + (size_t)batch * sizeof(unsigned);
+    return key_bytes(Hp, S, batch, top_k) + (size_t)2 * batch * sizeof(unsigned);
 }
 
 unsigned* peaks_bounds(unsigned long long* keys, int Hp, int S, int batch, int top_k) {
@@ -469,14 +493,12 @@ unsigned* peaks_bounds(unsigned long long* keys, int Hp, int S, int batch, int t
 cudaError_t launch_peak_tiles(const float* map, int Hp, int S, int batch, int top_k, float threshold,
                               unsigned long long* keys, unsigned* bounds, cudaStream_t st) {
     if (fast_tiles(Hp, S)) {
-        unsigned* tau = nullptr;
-        if (top_k <= PK_CAND) {
-            tau = bounds;
-            cudaError_t e = cudaMemsetAsync(tau, 0, (size_t)batch * sizeof(unsigned), st);
-            if (e != cudaSuccess) return e;
-        }
+        cudaError_t e = cudaMemsetAsync(bounds, 0, (size_t)2 * batch * sizeof(unsigned), st);
+        if (e != cudaSuccess) return e;
         const dim3 grid(batch, (S / PF_TS) * (Hp / PF_TT));
-        k_peak_tiles_fast<<<grid, PK_TILE_THREADS, 0, st>>>(map, Hp, S, kt_of(top_k), threshold, keys, tau);
+        k_peak_tiles_fast<<<grid, PK_TILE_THREADS, 0, st>>>(map, Hp, S, kt_of(top_k), threshold, keys, bounds,
+                                                            top_k <= PK_CAND ? 1 : 0,
+                                                            compact_keys(Hp, S, top_k) ? 1 : 0);
     }
     else {
         k_peak_tiles<<<tile_grid(Hp, S, batch), PK_TILE_THREADS, 0, st>>>(map, Hp, S, kt_of(top_k), threshold,
@@ -485,10 +507,11 @@ cudaError_t launch_peak_tiles(const float* map, int Hp, int S, int batch, int to
     return cudaGetLastError();
 }
 
-cudaError_t launch_peak_select(const unsigned long long* keys, int Hp, int S, int batch, int top_k,
-                               ft_peak* out, int32_t* count, cudaStream_t st) {
+cudaError_t launch_peak_select(const unsigned long long* keys, const unsigned* bounds, int Hp, int S, int batch,
+                               int top_k, ft_peak* out, int32_t* count, cudaStream_t st) {
     const dim3 g = tile_grid(Hp, S, 1);
     const int n = (int)(g.x * g.y) * kt_of(top_k);
-    k_peak_select<<<batch, PK_SEL_THREADS, 0, st>>>(keys, n, top_k, Hp, S, out, count);
+    const bool appended = fast_tiles(Hp, S) && compact_keys(Hp, S, top_k);
+    k_peak_select<<<batch, PK_SEL_THREADS, 0, st>>>(keys, appended ? bounds : nullptr, n, top_k, Hp, S, out, count);
     return cudaGetLastError();
 }

@@ -203,17 +203,37 @@ cudaError_t launch_tc_dft64(const float2* x, float2* y, int nvec, int sign, int 
 // operand gets a power-of-two scale, undone on output: for GEMM 1 from a bound
 // on |V| (the largest component of the spectrum row times the interpolator's
 // sum of |weights|), for GEMM 2 from the largest component of A (the twiddle
-// keeps |A'| = |A| <= sqrt(2) max component).  Persistent blocks loop over the
-// rows; the DFT matrix stays in shared memory and one 64-column TMEM
-// accumulator serves both GEMMs of every row.
-#define TCR_THREADS 256
+// keeps |A'| = |A| <= sqrt(2) max component).
+//
+// Persistent blocks of two independent row groups (4 warps each) that share the
+// DFT matrix in shared memory: each group has its own operand buffers, staging
+// area, 64 TMEM columns, mbarrier and named barrier, so one group's SIMT work
+// (gather, twiddles, stores) overlaps the other's tensor-core GEMMs.
+#define TCR_GROUPS 2
+#define TCR_GT 128                                     // threads per group
+#define TCR_THREADS (TCR_GROUPS * TCR_GT)
 #define TCR_S 4096
 #define TCR_PITCH 65                                   // stage row pitch (floats): conflict-free rows and columns
 
 static constexpr size_t tcr_stage_bytes(int W) {
     return (size_t)128 * TCR_PITCH * 4 > (size_t)(W + 2) * 8 ? (size_t)128 * TCR_PITCH * 4 : (size_t)(W + 2) * 8;
 }
-static size_t tcr_smem(int W) { return 2 * TC_A_BYTES + 2 * TC_B_BYTES + tcr_stage_bytes(W); }
+static size_t tcr_group_bytes(int W) { return ((2 * TC_B_BYTES + tcr_stage_bytes(W)) + 1023) & ~(size_t)1023; }
+static size_t tcr_smem(int W) { return 2 * TC_A_BYTES + TCR_GROUPS * tcr_group_bytes(W); }
+
+__device__ __forceinline__ void group_sync(int id) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(TCR_GT) : "memory");
+}
+// named-barrier sync of the group that also ORs v over its threads
+__device__ __forceinline__ bool group_sync_or(int id, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, %2, %3, p;\nselp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(TCR_GT)
+        : "memory");
+    return r != 0;
+}
 
 template <int FMT>
 __device__ __forceinline__ void split8(const float (&x)[8], uint4& hi, uint4& lo) {
@@ -243,74 +263,73 @@ __device__ __forceinline__ void put8(unsigned char* b_hi, unsigned char* b_lo, i
 
 template <int FMT, int INTERP>
 __global__ void __launch_bounds__(TCR_THREADS, 1)
-k_nvmt_rows_tc4096(float2* __restrict__ ws, int W, int Hp, int L, int total_rows,
+k_nvmt_rows_tc4096(float2* __restrict__ ws, int W, int Hp, int L, int total_rows, size_t group_bytes,
                    const float2* __restrict__ tw, unsigned* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    constexpr int S = TCR_S, T = TCR_THREADS, NW = T / 32, CW = 256 / NW;   // TMEM columns per warp
-    static_assert(CW % 16 == 0 && CW >= 16, "warps must split the 64 accumulator columns in x16 loads");
+    constexpr int S = TCR_S, T = TCR_GT;
+    const int g = threadIdx.x / TCR_GT, gt = threadIdx.x % TCR_GT;   // group, thread in group
+    const int warp = gt >> 5, lane = gt & 31;          // warp in group = TMEM lane quarter
     unsigned char* a_hi = sm;
     unsigned char* a_lo = a_hi + TC_A_BYTES;
-    unsigned char* b_hi = a_lo + TC_A_BYTES;
+    unsigned char* b_hi = a_lo + TC_A_BYTES + g * group_bytes;
     unsigned char* b_lo = b_hi + TC_B_BYTES;
     float* stage = reinterpret_cast<float*>(b_lo + TC_B_BYTES);         // [128][TCR_PITCH] accumulator copy
     float2* srow = reinterpret_cast<float2*>(stage);                     // the spectrum row (aliases stage)
-    __shared__ uint64_t mbar;
+    __shared__ uint64_t mbar[TCR_GROUPS];
     __shared__ uint32_t tmem_base;
-    __shared__ float red[NW];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int q = warp & 3, c0 = (warp >> 2) * CW;     // TMEM lane quarter, first column
+    __shared__ float red[TCR_GROUPS][4];
+    const int bar = 1 + g;                              // named barrier of the group
 
     build_dft_matrix<FMT>(a_hi, a_lo, g_w64, +1);
-    if (threadIdx.x == 0) mbar_init(smem_u32(&mbar), 1);
-    if (warp == 0) {
-        tc_alloc(smem_u32(&tmem_base), 64);
+    if (threadIdx.x == 0)
+        for (int j = 0; j < TCR_GROUPS; ++j) mbar_init(smem_u32(&mbar[j]), 1);
+    if (threadIdx.x < 32) {
+        tc_alloc(smem_u32(&tmem_base), 64 * TCR_GROUPS);
         tc_relinquish();
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = tmem_base;
+    const uint32_t tmem = tmem_base + 64 * g;          // this group's 64 accumulator columns
+    const uint32_t mb = smem_u32(&mbar[g]);
     uint32_t parity = 0;
 
-    auto block_max = [&](float v) -> float {
+    auto group_max = [&](float v) -> float {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-        if (lane == 0) red[warp] = v;
-        __syncthreads();
-        float r = red[0];
-#pragma unroll
-        for (int w = 1; w < NW; ++w) r = fmaxf(r, red[w]);
-        __syncthreads();
+        if (lane == 0) red[g][warp] = v;
+        group_sync(bar);
+        const float r = fmaxf(fmaxf(red[g][0], red[g][1]), fmaxf(red[g][2], red[g][3]));
+        group_sync(bar);
         return r;
     };
-    // issue the split GEMM on the current B and wait; block-uniform result
+    // issue the split GEMM on the group's B and wait; group-uniform result
     auto gemm = [&]() -> bool {
         fence_async_smem();
-        __syncthreads();
+        group_sync(bar);
         tc_fence_after();
-        if (threadIdx.x == 0)
-            issue_split_gemm<FMT>(tmem, smem_u32(a_hi), smem_u32(a_lo), smem_u32(b_hi), smem_u32(b_lo),
-                                  smem_u32(&mbar));
-        bool ok = mbar_wait(smem_u32(&mbar), parity);
+        if (gt == 0)
+            issue_split_gemm<FMT>(tmem, smem_u32(a_hi), smem_u32(a_lo), smem_u32(b_hi), smem_u32(b_lo), mb);
+        bool ok = mbar_wait(mb, parity);
         if (!ok) {
             atomicOr(err, 1u);
-            mbar_wait(smem_u32(&mbar), parity);        // let our own MMAs drain
+            mbar_wait(mb, parity);                      // let our own MMAs drain
         }
         parity ^= 1u;
         tc_fence_after();
-        return !__syncthreads_or(!ok);
+        return !group_sync_or(bar, !ok);
     };
-    // accumulator rows 32 q + lane, columns c0 .. c0 + CW - 1 -> stage; returns the max |value|
+    // accumulator rows 32 warp + lane, all 64 columns -> stage; returns the max |value|
     auto read_d = [&]() -> float {
         float mx = 0.f;
-        const int r = 32 * q + lane;
+        const int r = 32 * warp + lane;
 #pragma unroll
-        for (int c16 = 0; c16 < CW / 16; ++c16) {
+        for (int c16 = 0; c16 < 4; ++c16) {
             float d[16];
-            tc_ld16(tmem + ((uint32_t)(32 * q) << 16) + c0 + 16 * c16, d);
+            tc_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 16 * c16, d);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                stage[r * TCR_PITCH + c0 + 16 * c16 + j] = d[j];
+                stage[r * TCR_PITCH + 16 * c16 + j] = d[j];
                 mx = fmaxf(mx, fabsf(d[j]));
             }
         }
@@ -318,21 +337,21 @@ k_nvmt_rows_tc4096(float2* __restrict__ ws, int W, int Hp, int L, int total_rows
         return mx;
     };
 
-    for (int job = blockIdx.x; job < total_rows; job += gridDim.x) {
+    for (int job = blockIdx.x * TCR_GROUPS + g; job < total_rows; job += gridDim.x * TCR_GROUPS) {
         const int l = job % L;
         float2* row = ws + (size_t)job * S;            // row l of image job / L
         if (l == 0) {                                   // the DC row is zero
-            for (int k = threadIdx.x; k < S; k += T) row[k] = make_float2(0.f, 0.f);
+            for (int k = gt; k < S; k += T) row[k] = make_float2(0.f, 0.f);
             continue;
         }
-        for (int i = threadIdx.x; i < W / 2; i += T) cp_async16(srow + 2 * i, row + 2 * i);
+        for (int i = gt; i < W / 2; i += T) cp_async16(srow + 2 * i, row + 2 * i);
         cp_async_wait_all();
         float mx = 0.f;
-        for (int i = threadIdx.x; i < W / 2; i += T) {  // this thread's own copies
+        for (int i = gt; i < W / 2; i += T) {           // this thread's own copies
             const float4 v = *reinterpret_cast<const float4*>(srow + 2 * i);
             mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
         }
-        mx = block_max(mx) * (INTERP == FT_INTERP_LINEAR ? 1.f : 1.25f);   // sum of |Keys weights| <= 1.25
+        mx = group_max(mx) * (INTERP == FT_INTERP_LINEAR ? 1.f : 1.25f);   // sum of |Keys weights| <= 1.25
         const int e1 = mx > 0.f ? ilogbf(mx) : 0;
         const float s1 = ldexpf(1.f, 10 - e1);
         // gather V[n1 + 64 n2] for n2 = 8 kg .. 8 kg + 7 straight into B row n1
@@ -343,7 +362,7 @@ k_nvmt_rows_tc4096(float2* __restrict__ ws, int W, int Hp, int L, int total_rows
             const int sA = step / den, sB = step - sA * den;
             const int halfW = W >> 1;
             const float2 zero = make_float2(0.f, 0.f);
-            for (int item = threadIdx.x; item < 512; item += T) {
+            for (int item = gt; item < 512; item += T) {
                 const int r = (item & 7) | ((item >> 6) << 3), kg = (item >> 3) & 7;
                 const int n0 = r + 512 * kg;
                 const int num = (n0 - S / 2) * Hp;
@@ -379,11 +398,11 @@ k_nvmt_rows_tc4096(float2* __restrict__ ws, int W, int Hp, int L, int total_rows
             }
         }
         if (!gemm()) break;
-        mx = block_max(read_d());                       // also orders the stage writes before the reads below
+        mx = group_max(read_d());                       // also orders the stage writes before the reads below
         const int e2 = mx > 0.f ? ilogbf(mx) : 0;
         const float s2 = ldexpf(1.f, 10 - e2);
         // twiddle A[k2][n1] (rows k2 / k2 + 64 of stage) and write B row k2
-        for (int item = threadIdx.x; item < 512; item += T) {
+        for (int item = gt; item < 512; item += T) {
             const int k2 = (item & 7) | ((item >> 6) << 3), kg = (item >> 3) & 7;
             float re[8], im[8];
 #pragma unroll
@@ -398,18 +417,18 @@ k_nvmt_rows_tc4096(float2* __restrict__ ws, int W, int Hp, int L, int total_rows
         }
         if (!gemm()) break;
         read_d();
-        __syncthreads();
+        group_sync(bar);
         const float un = ldexpf(1.f, e1 + e2 - 20);
-        for (int k = threadIdx.x; k < S; k += T) {
+        for (int k = gt; k < S; k += T) {
             const int k1 = k >> 6, k2 = k & 63;
             const float sg = ((k + S / 2) & 1) ? -un : un;
             row[k] = make_float2(stage[k1 * TCR_PITCH + k2] * sg, stage[(k1 + 64) * TCR_PITCH + k2] * sg);
         }
-        __syncthreads();                                // stage is the next row's srow
+        group_sync(bar);                                // stage is the next row's srow
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tc_dealloc(tmem, 64);
+    if (threadIdx.x < 32) tc_dealloc(tmem_base, 64 * TCR_GROUPS);
 }
 
 template <int FMT, int INTERP>
@@ -423,7 +442,9 @@ static cudaError_t go_tc_rows(float2* ws, int W, int Hp, int L, int batch, const
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     const int total = batch * L;
-    k_nvmt_rows_tc4096<FMT, INTERP><<<total < sms ? total : sms, TCR_THREADS, sm, st>>>(ws, W, Hp, L, total, tw, err);
+    const int blocks = (total + TCR_GROUPS - 1) / TCR_GROUPS;
+    k_nvmt_rows_tc4096<FMT, INTERP><<<blocks < sms ? blocks : sms, TCR_THREADS, sm, st>>>(
+        ws, W, Hp, L, total, tcr_group_bytes(W), tw, err);
     return cudaGetLastError();
 }
 

@@ -61,9 +61,10 @@ extern "C" ft_status ft_peaks_noalloc(const float* d_map, int n_intercept, int n
     if (e != cudaSuccess) return ft_record_cuda(e, "ft_peaks_noalloc: cudaGetSymbolAddress");
     unsigned long long* keys = (unsigned long long*)scratch;
     cudaStream_t st = (cudaStream_t)stream;
-    e = launch_peak_tiles(d_map, n_intercept, n_slope, batch, top_k, threshold, keys,
-                          peaks_bounds(keys, n_intercept, n_slope, batch, top_k), st);
-    if (e == cudaSuccess) e = launch_peak_select(keys, n_intercept, n_slope, batch, top_k, d_out, d_count, st);
+    unsigned* bounds = peaks_bounds(keys, n_intercept, n_slope, batch, top_k);
+    e = launch_peak_tiles(d_map, n_intercept, n_slope, batch, top_k, threshold, keys, bounds, st);
+    if (e == cudaSuccess)
+        e = launch_peak_select(keys, bounds, n_intercept, n_slope, batch, top_k, d_out, d_count, st);
     if (e != cudaSuccess) return ft_record_cuda(e, "ft_peaks_noalloc: launch");
     return FT_OK;
 }

@@ -572,11 +572,12 @@ ft_status ft_peaks(ft_plan p, const float* d_map, int batch, int top_k, float th
         cudaStream_t ls = lanes > 1 ? p->lane_streams[j] : st;
         const float* m = d_map + (size_t)b0 * p->Hp * p->S;
         FT_LAUNCH(p, FT_KERNEL_PEAK_TILES, ls,
-                  launch_peak_tiles(m, p->Hp, p->S, b1 - b0, top_k, threshold, kbuf + b0 * kpi, bounds + b0, ls),
+                  launch_peak_tiles(m, p->Hp, p->S, b1 - b0, top_k, threshold, kbuf + b0 * kpi, bounds + 2 * b0,
+                                    ls),
                   "peak detection (tiles)");
         FT_LAUNCH(p, FT_KERNEL_PEAK_SELECT, ls,
-                  launch_peak_select(kbuf + b0 * kpi, p->Hp, p->S, b1 - b0, top_k, d_out + (size_t)b0 * top_k,
-                                     d_count + b0, ls),
+                  launch_peak_select(kbuf + b0 * kpi, bounds + 2 * b0, p->Hp, p->S, b1 - b0, top_k,
+                                     d_out + (size_t)b0 * top_k, d_count + b0, ls),
                   "peak detection (select)");
     }
     if (lanes > 1) return lanes_join(p, st);

@@ -156,6 +156,21 @@ def test_peaks_exact_large_k(torch, K, Hp, S):
         assert got[i] == ref
 
 
+@pytest.mark.parametrize("K,thr", [(200, float("-inf")), (1024, float("-inf")), (300, 2.5)])
+def test_peaks_exact_appended_key_lists(torch, K, thr):
+    """Maps large enough that the register tiles append their keys to one list
+    per image (256 tiles x K keys above the fixed-slot limit), with ties and a
+    threshold, against the list procedure; a batch of 5 crosses the lane split."""
+    rng = np.random.default_rng(K + 7)
+    maps = rng.standard_normal((5, 1024, 1024)).astype(np.float32)
+    maps[1] = np.round(maps[1] * 2.0)                             # many equal |values|
+    with make_plan(1024, 1024, 1024, 1024) as plan:
+        got, recs = _gpu.peaks(plan, maps, K, thr)
+    for i in range(5):
+        ref = oracle.peaks_ref(np.abs(maps[i]).astype(np.float64), K, thr)
+        assert got[i] == ref, i
+
+
 def test_peaks_fewer_than_k(torch):
     maps = np.zeros((1, 16, 16), np.float32)
     maps[0, 3, 4] = 5.0
