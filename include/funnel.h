@@ -274,9 +274,10 @@ ft_status ft_plan_tc_errors(ft_plan plan, uint32_t* flags);
 size_t ft_workspace_bytes(ft_plan plan, int batch);
 
 /* Number of kernel launches ft_forward / ft_peaks issue for a call with this
- * batch (a batch of 4 or more images is split over 2 plan-owned streams forked
- * from and joined back into the caller's stream: same kernels, same results;
- * FT_LANES=1 in the environment at plan creation turns the split off). */
+ * batch.  With FT_LANES=2 in the environment at plan creation, a batch of 4 or
+ * more images is split over 2 plan-owned streams forked from and joined back
+ * into the caller's stream (same kernels, same results, kernels of the two
+ * halves overlapping); by default everything runs on the caller's stream. */
 int ft_forward_launches(ft_plan plan, int batch);
 int ft_peaks_launches(ft_plan plan, int batch);
 

@@ -34,19 +34,13 @@
 // chosen so far, a warp scan finds the digit where the top_k boundary falls, and
 // the search stops as soon as that digit's bin is taken whole.  Keys are
 // distinct, so the selected set has exactly min(top_k, #keys) elements.
-#include "ft_internal.cuh"
+#include "peaks_common.cuh"
 
 #define PK_TT 32
 #define PK_TS 64
 #define PK_CAND 512
 #define PK_TILE_THREADS 256
 #define PK_SEL_THREADS 1024
-
-typedef unsigned long long u64;
-
-__device__ __forceinline__ u64 peak_key(float v, unsigned lin) {
-    return ((u64)__float_as_uint(v) << 32) | (u64)(0xFFFFFFFFu - lin);
-}
 
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
@@ -58,108 +52,6 @@ __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) 
 }
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
-__device__ __forceinline__ int wrap_into(int a, int n) {
-    if (a < 0) a += n;
-    if (a >= n) a %= n;
-    return a;
-}
-
-// Bitonic sort, descending, of n (power of two) keys in shared memory.
-__device__ void bitonic_desc(u64* v, int n) {
-    for (int k = 2; k <= n; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const bool desc = (i & k) == 0;
-                    const u64 x = v[i], y = v[ixj];
-                    if (desc ? (x < y) : (x > y)) {
-                        v[i] = y;
-                        v[ixj] = x;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-}
-
-struct SelState {
-    unsigned hist[256];
-    u64 prefix, mask;
-    int remaining;
-    int done;
-    int count;
-};
-
-// Marks the top K non-zero keys of keys[0..n) (any address space): on return
-// every key k != 0 with (k & st.mask) >= st.prefix is selected and there are
-// exactly min(K, #non-zero keys) of them.  Called by the whole block.
-__device__ void cta_select(const u64* keys, int n, int K, SelState& st) {
-    if (threadIdx.x == 0) {
-        st.prefix = 0ull;
-        st.mask = 0ull;
-        st.remaining = K;
-        st.done = 0;
-    }
-    __syncthreads();
-    for (int pass = 0; pass < 8; ++pass) {
-        const int shift = 56 - 8 * pass;
-        for (int i = threadIdx.x; i < 256; i += blockDim.x) st.hist[i] = 0u;
-        __syncthreads();
-        const u64 pf = st.prefix, mk = st.mask;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const u64 key = keys[i];
-            if (key != 0ull && (key & mk) == pf) atomicAdd(&st.hist[(key >> shift) & 255u], 1u);
-        }
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            // lane j owns digits 255-8j .. 248-8j (descending)
-            const int lane = threadIdx.x;
-            unsigned own = 0;
-#pragma unroll
-            for (int b = 0; b < 8; ++b) own += st.hist[255 - 8 * lane - b];
-            unsigned incl = own;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            const unsigned rem = (unsigned)st.remaining;
-            const unsigned ballot = __ballot_sync(0xffffffffu, incl >= rem);
-            if (ballot == 0u) {
-                // fewer non-zero keys than K share the prefix: take them all (pass 0 only)
-                if (lane == 0) {
-                    st.done = 1;
-                    st.prefix = 1ull;
-                    st.mask = ~0ull;
-                }
-            } else if (lane == __ffs(ballot) - 1) {
-                unsigned cum = incl - own;
-                int d = 255 - 8 * lane;
-                for (int b = 0; b < 8; ++b, --d) {
-                    const unsigned h = st.hist[d];
-                    if (cum + h >= rem) break;
-                    cum += h;
-                }
-                const unsigned left = rem - cum;
-                const u64 np = st.prefix | ((u64)d << shift);
-                const u64 nm = st.mask | (0xFFull << shift);
-                st.prefix = np;
-                st.mask = nm;
-                st.remaining = (int)left;
-                if (st.hist[d] == left) st.done = 1;       // the whole bin is in
-            }
-        }
-        __syncthreads();
-        if (st.done) break;
-    }
-}
-
-__device__ __forceinline__ bool selected(u64 key, const SelState& st) {
-    return key != 0ull && (key & st.mask) >= st.prefix;
 }
 
 __global__ void __launch_bounds__(PK_TILE_THREADS)
@@ -450,17 +342,22 @@ k_peak_tiles_fast(const float* __restrict__ map, int Hp, int S, int KT, float th
                    use_tau ? bounds + 2 * img : nullptr, compact ? bounds + 2 * img + 1 : nullptr, sh);
 }
 
-static int kt_of(int top_k) { return top_k < PK_CAND ? top_k : PK_CAND; }
+static bool fast_tiles(int Hp, int S) { return S % PF_TS == 0 && Hp % PF_TT == 0; }
+
+// keys kept per tile: every candidate a tile can hold when top_k exceeds it
+// (a 32 x 64 tile has at most 512 strict local maxima, a 32 x 128 tile 1024)
+static int kt_of(int Hp, int S, int top_k) {
+    const int cap = fast_tiles(Hp, S) ? PF_CAND : PK_CAND;
+    return top_k < cap ? top_k : cap;
+}
 
 // Key layout of the register tiles: every tile's KT slots (zero when unused)
 // while the selection can afford to scan them all, else one appended list per
 // image (one global atomic per tile, the selection reads only real keys).
 #define PK_COMPACT_MIN 32768
 static bool compact_keys(int Hp, int S, int top_k) {
-    return (long long)(S / PF_TS) * (Hp / PF_TT) * kt_of(top_k) > PK_COMPACT_MIN;
+    return (long long)(S / PF_TS) * (Hp / PF_TT) * kt_of(Hp, S, top_k) > PK_COMPACT_MIN;
 }
-
-static bool fast_tiles(int Hp, int S) { return S % PF_TS == 0 && Hp % PF_TT == 0; }
 
 static dim3 tile_grid(int Hp, int S, int batch) {
     if (fast_tiles(Hp, S)) return dim3(S / PF_TS, Hp / PF_TT, batch);
@@ -469,7 +366,7 @@ static dim3 tile_grid(int Hp, int S, int batch) {
 
 size_t peaks_tile_keys(int Hp, int S, int top_k) {
     const dim3 g = tile_grid(Hp, S, 1);
-    return (size_t)g.x * g.y * kt_of(top_k);
+    return (size_t)g.x * g.y * kt_of(Hp, S, top_k);
 }
 
 static size_t key_bytes(int Hp, int S, int batch, int top_k) {
@@ -488,30 +385,29 @@ unsigned* peaks_bounds(unsigned long long* keys, int Hp, int S, int batch, int t
 // The register-only tile kernel keeps, per image, a running lower bound of the
 // top_k-th peak value (as float bits): a tile that finds top_k candidates raises
 // it to its own top_k-th value, and later tiles drop dimmer candidates before
-// selecting.  It only applies when every tile keeps top_k keys (top_k <= 512).
-// The bounds are cleared on the stream before the tiles run.
+// selecting.  Every such tile keeps top_k keys (top_k <= 1024 = its capacity),
+// so the bound always applies.  The bounds are cleared on the stream before the
+// tiles run.
 cudaError_t launch_peak_tiles(const float* map, int Hp, int S, int batch, int top_k, float threshold,
                               unsigned long long* keys, unsigned* bounds, cudaStream_t st) {
+    const int KT = kt_of(Hp, S, top_k);
     if (fast_tiles(Hp, S)) {
         cudaError_t e = cudaMemsetAsync(bounds, 0, (size_t)2 * batch * sizeof(unsigned), st);
         if (e != cudaSuccess) return e;
         const dim3 grid(batch, (S / PF_TS) * (Hp / PF_TT));
-        k_peak_tiles_fast<<<grid, PK_TILE_THREADS, 0, st>>>(map, Hp, S, kt_of(top_k), threshold, keys, bounds,
-                                                            top_k <= PK_CAND ? 1 : 0,
-                                                            compact_keys(Hp, S, top_k) ? 1 : 0);
+        k_peak_tiles_fast<<<grid, PK_TILE_THREADS, 0, st>>>(map, Hp, S, KT, threshold, keys, bounds,
+                                                            KT == top_k ? 1 : 0, compact_keys(Hp, S, top_k) ? 1 : 0);
     }
     else {
-        k_peak_tiles<<<tile_grid(Hp, S, batch), PK_TILE_THREADS, 0, st>>>(map, Hp, S, kt_of(top_k), threshold,
-                                                                          keys);
+        k_peak_tiles<<<tile_grid(Hp, S, batch), PK_TILE_THREADS, 0, st>>>(map, Hp, S, KT, threshold, keys);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_peak_select(const unsigned long long* keys, const unsigned* bounds, int Hp, int S, int batch,
                                int top_k, ft_peak* out, int32_t* count, cudaStream_t st) {
-    const dim3 g = tile_grid(Hp, S, 1);
-    const int n = (int)(g.x * g.y) * kt_of(top_k);
     const bool appended = fast_tiles(Hp, S) && compact_keys(Hp, S, top_k);
-    k_peak_select<<<batch, PK_SEL_THREADS, 0, st>>>(keys, appended ? bounds : nullptr, n, top_k, Hp, S, out, count);
+    k_peak_select<<<batch, PK_SEL_THREADS, 0, st>>>(keys, appended ? bounds : nullptr,
+                                                    (int)peaks_tile_keys(Hp, S, top_k), top_k, Hp, S, out, count);
     return cudaGetLastError();
 }

@@ -347,7 +347,7 @@ ft_status ft_plan_create_space(ft_plan* out, int img_H, int img_W, int n_slope, 
     p->use_fast_x = fast_x && !generic;
     p->variant = generic ? 1 : 0;
     const char* lanes = getenv("FT_LANES");
-    p->lanes = lanes ? (atoi(lanes) > 1 ? FT_LANES : 1) : FT_LANES;
+    p->lanes = lanes && atoi(lanes) > 1 ? FT_LANES : 1;
     *out = p;
     return FT_OK;
 }
@@ -453,8 +453,10 @@ size_t ft_workspace_bytes(ft_plan p, int batch) {
 // parts run on plan-owned streams forked from and joined back into the caller's
 // stream, so that one part's compute-bound kernels share the SMs with another
 // part's memory-bound ones.  The parts use disjoint slices of the workspace and
-// the same kernels, so results do not depend on the split.  FT_LANES=1 in the
-// environment at plan creation keeps everything on the caller's stream.
+// the same kernels, so results do not depend on the split.  Off by default
+// (every kernel then runs alone on the caller's stream, one launch per step
+// over the whole batch); FT_LANES=2 in the environment at plan creation turns
+// it on.
 
 static ft_status lanes_fork(ft_plan p, cudaStream_t st) {
     if (!p->lane_fork) {

@@ -160,7 +160,7 @@ def test_peaks_exact_large_k(torch, K, Hp, S):
 def test_peaks_exact_appended_key_lists(torch, K, thr):
     """Maps large enough that the register tiles append their keys to one list
     per image (256 tiles x K keys above the fixed-slot limit), with ties and a
-    threshold, against the list procedure; a batch of 5 crosses the lane split."""
+    threshold, against the list procedure."""
     rng = np.random.default_rng(K + 7)
     maps = rng.standard_normal((5, 1024, 1024)).astype(np.float32)
     maps[1] = np.round(maps[1] * 2.0)                             # many equal |values|
@@ -169,6 +169,38 @@ def test_peaks_exact_appended_key_lists(torch, K, thr):
     for i in range(5):
         ref = oracle.peaks_ref(np.abs(maps[i]).astype(np.float64), K, thr)
         assert got[i] == ref, i
+
+
+@pytest.mark.parametrize("Hp,S", [(256, 256), (256, 192)])     # 32 x 128 and 32 x 64 tiles
+def test_peaks_dense_tile_with_k_1024(torch, Hp, S):
+    """Every (even, even) cell a strict local maximum (1024 in a 32 x 128 tile,
+    the most a tile can hold), one tile much brighter than the rest: the top
+    1024 peaks all come from that tile."""
+    rng = np.random.default_rng(5)
+    m = rng.uniform(0.0, 0.5, size=(Hp, S)).astype(np.float32)
+    m[0::2, 0::2] += 10.0
+    m[0:32, 0:128][0::2, 0::2] += 100.0
+    with make_plan(Hp, S, S, Hp) as plan:
+        got, _ = _gpu.peaks(plan, m[None], 1024)
+    ref = oracle.peaks_ref(np.abs(m).astype(np.float64), 1024)
+    assert got[0] == ref
+
+
+def test_lane_split_gives_identical_results(torch, monkeypatch):
+    """FT_LANES=2 splits a batch over two plan-owned streams: maps and peaks are
+    bit-identical to the single-stream run."""
+    imgs = synth.batch_1024(6, side=256)
+    with make_plan(256, 256, 256, 256) as plan:
+        ref = _gpu.forward(plan, imgs)
+        ref_pk, _ = _gpu.peaks(plan, ref, 16)
+    monkeypatch.setenv("FT_LANES", "2")
+    from paper_1904_09409_gb300 import funnel as f
+    with make_plan(256, 256, 256, 256) as plan:
+        assert f.lib().ft_forward_launches(plan.handle, 6) == 6
+        got = _gpu.forward(plan, imgs)
+        got_pk, _ = _gpu.peaks(plan, got, 16)
+    assert np.array_equal(got, ref)
+    assert got_pk == ref_pk
 
 
 def test_peaks_fewer_than_k(torch):

@@ -58,7 +58,7 @@ def _images(n, H, W, seed):
 @pytest.mark.parametrize("n,H,W,Hp,interp", [
     (3, 256, 1024, 256, "linear"),      # 387 rows over the persistent blocks
     (1, 200, 4096, 512, "cubic"),       # full-width rows, padded intercepts
-    (5, 96, 2048, 96, "linear"),        # n_intercept 2^5 * 3, a lane split
+    (5, 96, 2048, 96, "linear"),        # n_intercept 2^5 * 3
     (1, 64, 4096, 8192, "cubic"),       # 4097 rows, steep funnel
 ])
 def test_split_precision_rows_match_oracle(torch, precision, n, H, W, Hp, interp):
