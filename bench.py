@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-varlen", action="store_true", help="skip the mixed-size batch measurement")
     ap.add_argument("--no-precision", action="store_true", help="skip the 8 x 4096^2 split-precision leg")
+    ap.add_argument("--precision-only", action="store_true",
+                    help="run only the 4096^2 precision leg on --images images (8 = its workload; fewer for ncu)")
     ap.add_argument("--no-extras", action="store_true",
                     help="time only the main step (no e2e, forward+backward or mixed-size legs), for ncu captures")
     ap.add_argument("--images", type=int, default=64,
@@ -269,7 +271,7 @@ def time_precision(f, imgs, steps, stream, dev):
     B = x.shape[0]
     K = 100
     maps, peaks, out = {}, {}, {}
-    for prec in ("fp32", "bf16x3", "fp16x3"):
+    for prec in ("fp32", "bf16x3", "fp16x3", "bf16x6"):
         plan = f.Plan(4096, 4096, 4096, 4096, "linear")
         f.ft_plan_set_precision(plan, prec)
         m = torch.empty((B, 4096, 4096), dtype=torch.float32, device=dev)
@@ -313,8 +315,9 @@ def time_precision(f, imgs, steps, stream, dev):
     del maps, x
     torch.cuda.empty_cache()
     return {"workload": "8 x 4096^2 images, 100 lines each (mixed edge types, noise 0.2), n_slope = "
-                        "n_intercept = 4096, linear NVMT: ft_forward + top-100 peaks; step 3 in FP32 "
-                        "(FFT) or as the split-precision four-step DFT on the tensor cores",
+                        "n_intercept = 4096, linear NVMT: ft_forward + top-100 peaks; the three length-4096 "
+                        "transforms (steps 1, 3, 4) in FP32 (FFT) or as split-precision four-step DFTs on "
+                        "the tensor cores",
             "variants": out}
 
 
@@ -628,10 +631,25 @@ def run_extras(f, args, plan, imgs, lines, x, stream, dev, rank, ws, vl_imgs, vl
     }
 
 
+def run_precision_only(args):
+    import torch
+    from paper_1904_09409_gb300 import funnel as f
+    n = args.images if args.images != 64 else 8
+    with oracle_pool(min(host_cores(), 32)) as pool:
+        imgs = large_images(pool, n)
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    res = time_precision(f, imgs, max(1, args.steps), torch.cuda.current_stream(dev), dev)
+    print(json.dumps({"precision_4096": res}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.precision_only:
+        return run_precision_only(args)
     return run_ours(args)
 
 

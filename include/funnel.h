@@ -237,8 +237,9 @@ ft_status ft_batch_run(ft_batch batch, const float* d_imgs, float* d_maps, int t
  * D = Ahi Bhi + Ahi Blo + Alo Bhi. */
 typedef enum {
     FT_PRECISION_FP32 = 0,
-    FT_PRECISION_BF16X3 = 1,
-    FT_PRECISION_FP16X3 = 2
+    FT_PRECISION_BF16X3 = 1,     /* BF16 hi + lo, 3 products */
+    FT_PRECISION_FP16X3 = 2,     /* FP16 hi + lo, 3 products */
+    FT_PRECISION_BF16X6 = 3      /* BF16 hi + mid + lo, 6 products (all of order <= 2) */
 } ft_precision;
 
 /* Batched 64-point complex DFT y[v][k] = sum_n x[v][n] exp(sign 2 pi i k n / 64)
@@ -250,17 +251,20 @@ typedef enum {
 ft_status ft_tc_dft64(const void* d_x, void* d_y, int nvec, int sign, int precision, uint32_t* d_err,
                       void* stream);
 
-/* Arithmetic of step 3 (the transform along x' of eq. (13), Sec. 3.2) for
- * this plan.  FT_PRECISION_FP32 (the default) is the FP32 FFT.  The split
- * variants run steps 2-3 of ft_forward as the NVMT gather followed by a
- * four-step DFT, 4096 = 64 x 64: two split-precision GEMMs (the 64-point DFT
- * matrix against 64 rows of gathered or twiddled values) with FP32 twiddles in
- * between, in one persistent kernel that keeps the DFT matrix in shared memory.
- * Steps 1 and 4, the peaks and ft_backward stay FP32.  Returns
- * FT_ERR_UNSUPPORTED_SIZE for a split precision unless n_slope = 4096 and the
- * interpolator is linear or cubic (the plan keeps its previous precision);
- * FT_ERR_INVALID_ARG for an unknown value.  Changes the result of later calls
- * only. */
+/* Arithmetic of the length-4096 Fourier transforms of ft_forward (Sec. 3.1:
+ * step 1 along y, eq. (16); step 3 along x', eq. (13); step 4 along omega_2,
+ * eq. (19)).  FT_PRECISION_FP32 (the default) is the FP32 FFT.  The split
+ * variants evaluate every transform of length 4096 as a four-step DFT,
+ * 4096 = 64 x 64: two split-precision GEMMs (the 64-point DFT matrix against
+ * 64 rows of gathered or twiddled values) with FP32 twiddles in between, in one
+ * persistent kernel per step that keeps the DFT matrix in shared memory: steps
+ * 2-3 when n_slope = 4096 (the NVMT gather writes the first GEMM's operand; not
+ * with the band-limited interpolator), steps 1 and 4 when n_intercept = 4096
+ * (two image or map columns per complex transform).  Transforms of other
+ * lengths, the peaks and ft_backward stay FP32.  Returns
+ * FT_ERR_UNSUPPORTED_SIZE for a split precision when the plan has no such
+ * transform (the plan keeps its previous precision); FT_ERR_INVALID_ARG for an
+ * unknown value.  Changes the result of later calls only. */
 ft_status ft_plan_set_precision(ft_plan plan, int precision);
 int ft_plan_get_precision(ft_plan plan);
 

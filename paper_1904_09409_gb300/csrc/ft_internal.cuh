@@ -299,10 +299,17 @@ cudaError_t launch_tc_dft64(const float2* x, float2* y, int nvec, int sign, int 
                             cudaStream_t st);
 // tables of the tensor-core kernels on the current device (host call, before any capture)
 cudaError_t tc_prepare();
-// Steps 2-3 for n_slope = 4096 with the split-precision four-step DFT (k_tc.cu);
-// tw = exp(-2 pi i t / 4096), t < 4096
-cudaError_t launch_nvmt_rows_tc4096(float2* ws, int W, int Hp, int L, int interp, int fmt, const float2* tw,
-                                    unsigned* err, int batch, cudaStream_t st);
+// The split-precision four-step DFT of length 4096 (k_tc.cu): steps 2-3 for
+// n_slope = 4096, and steps 1 and 4 of the forward path for n_intercept = 4096
+// (same layouts as launch_col_r2c with unit scales and launch_col_c2r with
+// mid scale 1 and out scale 1/H')
+// (prec: FT_PRECISION_BF16X3, _FP16X3 or _BF16X6)
+cudaError_t launch_nvmt_rows_tc4096(float2* ws, int W, int Hp, int L, int interp, int prec, unsigned* err, int batch,
+                                    cudaStream_t st);
+cudaError_t launch_col_r2c_tc4096(const float* img, int H, int W, int row0, float2* ws, int L, int S, int prec,
+                                  unsigned* err, int batch, cudaStream_t st);
+cudaError_t launch_col_c2r_tc4096(const float2* ws, int L, int S, float* map, int prec, unsigned* err, int batch,
+                                  cudaStream_t st);
 
 // in[b][R][C] -> out[b][C][R] (k_transpose.cu)
 cudaError_t launch_transpose(const float* in, float* out, int R, int C, int batch, cudaStream_t st);

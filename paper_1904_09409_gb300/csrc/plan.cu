@@ -224,9 +224,8 @@ static cudaError_t nvmt_rows(ft_plan p, float2* ws, int batch, cudaStream_t st) 
         return launch_nvmt_rows_fourier(ws, p->W, p->S, p->Hp, p->L, p->fw, p->fm, p->fx, p->d_chirp,
                                         p->d_chirp + nu, p->d_chirp + nu + nx, batch, st);
     }
-    if (p->precision != FT_PRECISION_FP32)
-        return launch_nvmt_rows_tc4096(ws, p->W, p->Hp, p->L, p->interp, p->precision == FT_PRECISION_BF16X3 ? 1 : 0,
-                                       p->fx.tw, p->d_tc_err, batch, st);
+    if (p->precision != FT_PRECISION_FP32 && p->S == 4096)
+        return launch_nvmt_rows_tc4096(ws, p->W, p->Hp, p->L, p->interp, p->precision, p->d_tc_err, batch, st);
     if (p->use_fast_x) return launch_nvmt_rows_fast(ws, p->W, p->Hp, p->L, p->interp, p->fx, batch, st);
     return launch_nvmt_rows(ws, p->W, p->S, p->Hp, p->L, p->interp, p->fx, p->row_logB_x, batch, st);
 }
@@ -403,10 +402,12 @@ ft_status ft_plan_set_variant(ft_plan p, int variant) {
 int ft_plan_get_variant(ft_plan p) { return p ? p->variant : -1; }
 
 ft_status ft_plan_set_precision(ft_plan p, int precision) {
-    if (!p || precision < FT_PRECISION_FP32 || precision > FT_PRECISION_FP16X3) return FT_ERR_INVALID_ARG;
+    if (!p || precision < FT_PRECISION_FP32 || precision > FT_PRECISION_BF16X6) return FT_ERR_INVALID_ARG;
     if (precision != FT_PRECISION_FP32) {
-        if (p->S != 4096 || p->interp == FT_INTERP_FOURIER)
-            return ft_record_error(FT_ERR_UNSUPPORTED_SIZE, "split precision: n_slope 4096, linear or cubic only");
+        if (!((p->S == 4096 && p->interp != FT_INTERP_FOURIER) || p->Hp == 4096))
+            return ft_record_error(FT_ERR_UNSUPPORTED_SIZE,
+                                   "split precision: a length-4096 transform (n_slope 4096 with the linear or "
+                                   "cubic interpolator, or n_intercept 4096) is needed");
         if (!p->d_tc_err) {
             int cur = 0;
             FT_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
@@ -491,12 +492,18 @@ int ft_peaks_launches(ft_plan p, int batch) {
 }
 
 static ft_status forward_part(ft_plan p, const float* src, float* d_map, float2* ws, int nb, cudaStream_t st) {
+    // split precision: the length-4096 column transforms on the tensor cores too
+    const bool tc_cols = p->precision != FT_PRECISION_FP32 && p->Hp == 4096;
     FT_LAUNCH(p, FT_KERNEL_COL_R2C, st,
-              col_r2c(p, src, p->H, p->W, p->W, (size_t)p->H * p->W, p->top, ws, 1.f, 1.f, nb, st),
+              tc_cols ? launch_col_r2c_tc4096(src, p->H, p->W, p->top, ws, p->L, p->S, p->precision, p->d_tc_err, nb,
+                                              st)
+                      : col_r2c(p, src, p->H, p->W, p->W, (size_t)p->H * p->W, p->top, ws, 1.f, 1.f, nb, st),
               "step 1 (column R2C)");
     FT_LAUNCH(p, FT_KERNEL_NVMT_ROWS, st, nvmt_rows(p, ws, nb, st), "steps 2-3 (NVMT + row FFT)");
     FT_LAUNCH(p, FT_KERNEL_COL_C2R, st,
-              col_c2r(p, ws, p->S, 1.f, d_map, 0, p->Hp, p->S, (size_t)p->Hp * p->S, 1.f / (float)p->Hp, nb, st),
+              tc_cols ? launch_col_c2r_tc4096(ws, p->L, p->S, d_map, p->precision, p->d_tc_err, nb, st)
+                      : col_c2r(p, ws, p->S, 1.f, d_map, 0, p->Hp, p->S, (size_t)p->Hp * p->S, 1.f / (float)p->Hp,
+                                nb, st),
               "step 4 (column C2R)");
     return FT_OK;
 }

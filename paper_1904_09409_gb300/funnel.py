@@ -42,7 +42,9 @@ EXPORTED = (
 FT_PRECISION_FP32 = 0
 FT_PRECISION_BF16X3 = 1
 FT_PRECISION_FP16X3 = 2
-PRECISION_NAMES = {"fp32": FT_PRECISION_FP32, "bf16x3": FT_PRECISION_BF16X3, "fp16x3": FT_PRECISION_FP16X3}
+FT_PRECISION_BF16X6 = 3
+PRECISION_NAMES = {"fp32": FT_PRECISION_FP32, "bf16x3": FT_PRECISION_BF16X3, "fp16x3": FT_PRECISION_FP16X3,
+                   "bf16x6": FT_PRECISION_BF16X6}
 FT_BATCH_GRAPH = 1
 FT_BATCH_TUNE = 2
 FT_SPACE_REGULAR = 0
@@ -375,7 +377,8 @@ def ft_plan_get_variant(plan: Plan) -> int:
 
 
 def ft_plan_set_precision(plan: Plan, precision) -> None:
-    """Arithmetic of step 3: "fp32", "bf16x3" or "fp16x3" (or the FT_PRECISION_* value)."""
+    """Arithmetic of the length-4096 transforms: "fp32", "bf16x3", "fp16x3" or
+    "bf16x6" (or the FT_PRECISION_* value)."""
     prec = PRECISION_NAMES[precision] if isinstance(precision, str) else int(precision)
     _check(lib().ft_plan_set_precision(plan.handle, prec), "ft_plan_set_precision")
 
