@@ -210,7 +210,9 @@ cudaError_t launch_tc_dft64(const float2* x, float2* y, int nvec, int sign, int 
 // combined when the accumulators are read back.  Every operand is split into
 // high and low 16-bit parts; D = A_hi B_hi + A_hi B_lo + A_lo B_hi in FP32.
 // The gather writes GEMM 1's operands directly (each thread builds 16-byte runs
-// of 8 columns of one operand row), the twiddle pass writes GEMM 2's.  Each
+// of 8 columns of one operand row; the 32 threads of a warp take 32 consecutive
+// rows of the same 8 columns, so their reads of consecutive samples and of the
+// swizzled stage are conflict-free), the twiddle pass writes GEMM 2's.  Each
 // operand gets a power-of-two scale, undone on output: for GEMM 1 from a bound
 // on |V| (the largest component of the spectrum row times the interpolator's
 // sum of |weights|), for GEMM 2 from the largest component of A (the twiddle
@@ -549,7 +551,7 @@ k_tc4096(TcArgs a) {
             const int halfW = a.W >> 1;
             const float2 zero = make_float2(0.f, 0.f);
             for (int item = gt; item < 512; item += T) {
-                const int rr = (item & 7) | ((item >> 6) << 3), kg = (item >> 3) & 7;
+                const int rr = item & 63, kg = item >> 6;       // a warp: 32 operand rows, one K run
                 const int n0 = rr + 512 * kg;
                 const int num = (n0 - N / 2) * a.Hp;
                 int qf = floor_div(num, den), rem = num - qf * den;
@@ -585,7 +587,7 @@ k_tc4096(TcArgs a) {
         } else {
             const float4* gst = reinterpret_cast<const float4*>(zin);
             for (int item = gt; item < 512; item += T) {
-                const int rr = (item & 7) | ((item >> 6) << 3), kg = (item >> 3) & 7;
+                const int rr = item & 63, kg = item >> 6;       // a warp: 32 operand rows, one K run
                 float re[8], im[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
@@ -616,7 +618,7 @@ k_tc4096(TcArgs a) {
         const float s2 = ldexpf(1.f, 10 - e2);
         // ---- twiddle A[k2][n1] (rows k2 / k2 + 64 of stage) and write GEMM 2's operand row k2
         for (int item = gt; item < 512; item += T) {
-            const int k2 = (item & 7) | ((item >> 6) << 3), kg = (item >> 3) & 7;
+            const int k2 = item & 63, kg = item >> 6;
             float re[8], im[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
