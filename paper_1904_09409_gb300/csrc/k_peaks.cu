@@ -166,30 +166,39 @@ k_peak_select(const u64* __restrict__ keys, const unsigned* __restrict__ bounds,
     if (threadIdx.x == 0) count[blockIdx.x] = cnt;
 }
 
-#define PF_TT 32
 #define PF_TS 128
-#define PF_CAND 1024
-
 #define PF_PITCH (PF_TS + 8)
 
-struct TileShared {
-    float tile[(PF_TT + 2) * PF_PITCH];
-    u64 cand[PF_CAND];
+// Shared memory of one register tile of TT rows: the tile with its one-cell
+// halo, then the candidate list (at most one strict local maximum per 2 x 2
+// block: TT * PF_TS / 4), then the scalars.
+template <int TT>
+struct TileLayout {
+    static constexpr int CAND = TT * PF_TS / 4;
+    static constexpr size_t TILE_BYTES = (size_t)(TT + 2) * PF_PITCH * sizeof(float);
+    static constexpr size_t BYTES = TILE_BYTES + (size_t)CAND * sizeof(u64);
+};
+struct TileScalars {
     int ncand;
     unsigned kth_bits;
     unsigned base;          // first slot of this tile's keys in the image's key list
     SelState st;
 };
 
+// One block of 8 warps per tile of 8 RW rows x 128 columns; warp w tests rows
+// RW w .. RW w + RW - 1, lane l columns 4 l .. 4 l + 3, walking down the rows
+// with a three-row window.
+template <int RW>
 __device__ __forceinline__ void peak_tile_fast(const float* __restrict__ m, int Hp, int S, int KT, float thr,
-                                               int img, int ty, int tx, int tile, u64* __restrict__ out,
+                                               int ty, int tx, int tile, u64* __restrict__ out,
                                                unsigned* __restrict__ tau, unsigned* __restrict__ fill,
-                                               TileShared& sh) {
-    u64* cand = sh.cand;
+                                               float* tl, u64* cand, TileScalars& sh) {
+    constexpr int TT = 8 * RW, CAND = TileLayout<TT>::CAND;
+    static_assert(4 * RW <= 32, "one mask bit per cell of a lane");
     SelState& st = sh.st;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int t0 = ty * PF_TT + 4 * warp;                  // first of this warp's 4 rows
+    const int t0 = ty * TT + RW * warp;                    // first of this warp's rows
     const int s0 = tx * PF_TS;
     if (threadIdx.x == 0) {
         sh.ncand = 0;
@@ -199,18 +208,17 @@ __device__ __forceinline__ void peak_tile_fast(const float* __restrict__ m, int 
     float lower = thr;
     if (tau) lower = fmaxf(lower, __uint_as_float(__ldcg(tau)));
 
-    // the tile with its one-cell halo, |.| applied when read: PF_TT + 2 rows of
-    // PF_TS + 2 columns (interior at 16-byte aligned offset 4, halo at 3 and
-    // 4 + PF_TS), copied with cp.async (16 bytes interior, 4 bytes halo)
-    float* tl = sh.tile;
-    const int tb = ty * PF_TT;
-    for (int idx = threadIdx.x; idx < (PF_TT + 2) * (PF_TS / 4); idx += blockDim.x) {
+    // the tile with its one-cell halo: TT + 2 rows of PF_TS + 2 columns (interior
+    // at 16-byte aligned offset 4, halo at 3 and 4 + PF_TS), copied with cp.async
+    // (16 bytes interior, 4 bytes halo); |.| is applied when read
+    const int tb = ty * TT;
+    for (int idx = threadIdx.x; idx < (TT + 2) * (PF_TS / 4); idx += blockDim.x) {
         const int r = idx / (PF_TS / 4);
         const int j = idx - r * (PF_TS / 4);
         const int t = wrap_into(tb - 1 + r, Hp);
         cp_async16(tl + r * PF_PITCH + 4 + 4 * j, m + (size_t)t * S + s0 + 4 * j);
     }
-    if (threadIdx.x < 2 * (PF_TT + 2)) {
+    if (threadIdx.x < 2 * (TT + 2)) {
         const int r = threadIdx.x >> 1;
         const int side = threadIdx.x & 1;
         const int t = wrap_into(tb - 1 + r, Hp);
@@ -219,24 +227,26 @@ __device__ __forceinline__ void peak_tile_fast(const float* __restrict__ m, int 
     }
     cp_async_wait_all();
     __syncthreads();
-    // rows t0-1 .. t0+4 of this warp; lane holds columns s0 + 4 lane .. + 3
-    float4 a[6];
-    float lo[6], hi[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        const float* rowp = tl + (4 * warp + k) * PF_PITCH + 4 + 4 * lane;
-        const float4 x = *reinterpret_cast<const float4*>(rowp);
-        a[k] = make_float4(fabsf(x.x), fabsf(x.y), fabsf(x.z), fabsf(x.w));
-        lo[k] = fabsf(rowp[-1]);
-        hi[k] = fabsf(rowp[4]);
-    }
 
+    // row k of this warp's window (k = 0 is row t0 - 1) as |.| of columns
+    // s0 + 4 lane - 1 .. s0 + 4 lane + 4
+    auto row6 = [&](int k, float (&x)[6]) {
+        const float* rowp = tl + (RW * warp + k) * PF_PITCH + 4 + 4 * lane;
+        const float4 v = *reinterpret_cast<const float4*>(rowp);
+        x[0] = fabsf(rowp[-1]);
+        x[1] = fabsf(v.x);
+        x[2] = fabsf(v.y);
+        x[3] = fabsf(v.z);
+        x[4] = fabsf(v.w);
+        x[5] = fabsf(rowp[4]);
+    };
     unsigned mask = 0u;                                    // bit 4 (k-1) + c: cell is a candidate
+    float rm[6], r0[6], rp[6];
+    row6(0, rm);
+    row6(1, r0);
 #pragma unroll
-    for (int k = 1; k <= 4; ++k) {
-        const float rm[6] = {lo[k - 1], a[k - 1].x, a[k - 1].y, a[k - 1].z, a[k - 1].w, hi[k - 1]};
-        const float r0[6] = {lo[k], a[k].x, a[k].y, a[k].z, a[k].w, hi[k]};
-        const float rp[6] = {lo[k + 1], a[k + 1].x, a[k + 1].y, a[k + 1].z, a[k + 1].w, hi[k + 1]};
+    for (int k = 1; k <= RW; ++k) {
+        row6(k + 1, rp);
         float cm[6];                                       // max of the rows above and below
 #pragma unroll
         for (int j = 0; j < 6; ++j) cm[j] = fmaxf(rm[j], rp[j]);
@@ -263,32 +273,35 @@ __device__ __forceinline__ void peak_tile_fast(const float* __restrict__ m, int 
             }
             if (is_max) mask |= 1u << (4 * (k - 1) + c);
         }
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            rm[j] = r0[j];
+            r0[j] = rp[j];
+        }
     }
-    __syncthreads();                                       // ncand initialised
-    // one append per warp: exclusive scan of the lanes' candidate counts
+    // one append per warp (only warps with candidates): exclusive scan of the lanes' counts
     const int cnt = __popc(mask);
-    int incl = cnt;
+    if (__any_sync(0xffffffffu, cnt != 0)) {
+        int incl = cnt;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    int basepos = 0;
-    if (lane == 31 && incl > 0) basepos = atomicAdd(&sh.ncand, incl);
-    basepos = __shfl_sync(0xffffffffu, basepos, 31) + incl - cnt;
-#pragma unroll
-    for (int k = 1; k <= 4; ++k) {
-        const float r0[4] = {a[k].x, a[k].y, a[k].z, a[k].w};
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            if (mask & (1u << (4 * (k - 1) + c))) {
-                const unsigned lin = (unsigned)(t0 + k - 1) * (unsigned)S + (unsigned)(s0 + 4 * lane + c);
-                cand[basepos++] = peak_key(r0[c], lin);
-            }
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        int basepos = 0;
+        if (lane == 31) basepos = atomicAdd(&sh.ncand, incl);
+        basepos = __shfl_sync(0xffffffffu, basepos, 31) + incl - cnt;
+        for (unsigned mk = mask; mk; mk &= mk - 1u) {      // the set bits only
+            const int b = __ffs(mk) - 1;
+            const int k = b >> 2, c = b & 3;
+            const float v = fabsf(tl[(RW * warp + k + 1) * PF_PITCH + 4 + 4 * lane + c]);
+            const unsigned lin = (unsigned)(t0 + k) * (unsigned)S + (unsigned)(s0 + 4 * lane + c);
+            if (basepos < CAND) cand[basepos] = peak_key(v, lin);
+            ++basepos;
         }
     }
     __syncthreads();
-    const int n = min(sh.ncand, PF_CAND);
+    const int n = min(sh.ncand, CAND);
     if (fill) {
         // the tile's min(n, KT) keys are appended to the image's key list
         if (n == 0) return;
@@ -330,24 +343,32 @@ __device__ __forceinline__ void peak_tile_fast(const float* __restrict__ m, int 
 // One block per tile; the image index runs fastest in the grid, so the blocks of
 // the first wave cover the first tiles of every image and the later waves find
 // each image's running bound already raised.
+template <int RW>
 __global__ void __launch_bounds__(PK_TILE_THREADS)
 k_peak_tiles_fast(const float* __restrict__ map, int Hp, int S, int KT, float thr, u64* __restrict__ keys,
                   unsigned* __restrict__ bounds, int use_tau, int compact) {
-    __shared__ TileShared sh;
+    constexpr int TT = 8 * RW;
+    extern __shared__ __align__(16) unsigned char psm[];
+    __shared__ TileScalars sh;
     const int img = blockIdx.x;
     const int tile = blockIdx.y;
-    const int ntx = S / PF_TS, ntiles = ntx * (Hp / PF_TT);
+    const int ntx = S / PF_TS, ntiles = ntx * (Hp / TT);
     const int ty = tile / ntx, tx = tile - ty * ntx;
-    peak_tile_fast(map + (size_t)img * Hp * S, Hp, S, KT, thr, img, ty, tx, tile, keys + (size_t)img * ntiles * KT,
-                   use_tau ? bounds + 2 * img : nullptr, compact ? bounds + 2 * img + 1 : nullptr, sh);
+    peak_tile_fast<RW>(map + (size_t)img * Hp * S, Hp, S, KT, thr, ty, tx, tile, keys + (size_t)img * ntiles * KT,
+                       use_tau ? bounds + 2 * img : nullptr, compact ? bounds + 2 * img + 1 : nullptr,
+                       reinterpret_cast<float*>(psm),
+                       reinterpret_cast<u64*>(psm + TileLayout<TT>::TILE_BYTES), sh);
 }
 
-static bool fast_tiles(int Hp, int S) { return S % PF_TS == 0 && Hp % PF_TT == 0; }
+// register tiles: 64 rows where n_intercept allows, else 32
+static bool fast_tiles(int Hp, int S) { return S % PF_TS == 0 && Hp % 32 == 0; }
+static int fast_rows(int Hp) { return Hp % 64 == 0 ? 64 : 32; }
 
 // keys kept per tile: every candidate a tile can hold when top_k exceeds it
-// (a 32 x 64 tile has at most 512 strict local maxima, a 32 x 128 tile 1024)
+// (a 32 x 64 tile has at most 512 strict local maxima, a register tile of 32 or
+// 64 x 128 cells 1024 or 2048, both at least FT_MAX_TOPK)
 static int kt_of(int Hp, int S, int top_k) {
-    const int cap = fast_tiles(Hp, S) ? PF_CAND : PK_CAND;
+    const int cap = fast_tiles(Hp, S) ? fast_rows(Hp) * PF_TS / 4 : PK_CAND;
     return top_k < cap ? top_k : cap;
 }
 
@@ -356,11 +377,11 @@ static int kt_of(int Hp, int S, int top_k) {
 // image (one global atomic per tile, the selection reads only real keys).
 #define PK_COMPACT_MIN 32768
 static bool compact_keys(int Hp, int S, int top_k) {
-    return (long long)(S / PF_TS) * (Hp / PF_TT) * kt_of(Hp, S, top_k) > PK_COMPACT_MIN;
+    return (long long)(S / PF_TS) * (Hp / fast_rows(Hp)) * kt_of(Hp, S, top_k) > PK_COMPACT_MIN;
 }
 
 static dim3 tile_grid(int Hp, int S, int batch) {
-    if (fast_tiles(Hp, S)) return dim3(S / PF_TS, Hp / PF_TT, batch);
+    if (fast_tiles(Hp, S)) return dim3(S / PF_TS, Hp / fast_rows(Hp), batch);
     return dim3((S + PK_TS - 1) / PK_TS, (Hp + PK_TT - 1) / PK_TT, batch);
 }
 
@@ -394,9 +415,19 @@ cudaError_t launch_peak_tiles(const float* map, int Hp, int S, int batch, int to
     if (fast_tiles(Hp, S)) {
         cudaError_t e = cudaMemsetAsync(bounds, 0, (size_t)2 * batch * sizeof(unsigned), st);
         if (e != cudaSuccess) return e;
-        const dim3 grid(batch, (S / PF_TS) * (Hp / PF_TT));
-        k_peak_tiles_fast<<<grid, PK_TILE_THREADS, 0, st>>>(map, Hp, S, KT, threshold, keys, bounds,
-                                                            KT == top_k ? 1 : 0, compact_keys(Hp, S, top_k) ? 1 : 0);
+        const int TT = fast_rows(Hp);
+        const dim3 grid(batch, (S / PF_TS) * (Hp / TT));
+        const int use_tau = KT == top_k ? 1 : 0, compact = compact_keys(Hp, S, top_k) ? 1 : 0;
+        if (TT == 64) {
+            const size_t sm = TileLayout<64>::BYTES;
+            e = cudaFuncSetAttribute(k_peak_tiles_fast<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+            k_peak_tiles_fast<8><<<grid, PK_TILE_THREADS, sm, st>>>(map, Hp, S, KT, threshold, keys, bounds, use_tau,
+                                                                    compact);
+        } else {
+            k_peak_tiles_fast<4><<<grid, PK_TILE_THREADS, TileLayout<32>::BYTES, st>>>(map, Hp, S, KT, threshold, keys,
+                                                                                    bounds, use_tau, compact);
+        }
     }
     else {
         k_peak_tiles<<<tile_grid(Hp, S, batch), PK_TILE_THREADS, 0, st>>>(map, Hp, S, KT, threshold, keys);
