@@ -13,7 +13,7 @@ transform     the transform step by step (Sec. 3.1 steps 1-4, Sec. 4.2 padding)
 funnel_direct brute-force evaluation of the same definition without any FFT
 peaks_ref     the list-based peak detection of Sec. 4.4 and eqs. (22)-(25)
 adjoint_ref   the exact transpose of the (linear) transform, for gradients
-verify_ref    the line verification of Sec. 4.5 (band profile along a candidate line)
+verification  the line verification of Sec. 4.5 (band profile along a candidate line)
 """
 from .transform import (centred, pad_rows, fourier_y, nvmt_positions, nvmt,
                          fourier_xprime, inverse_fourier_omega2, funnel_ref,
@@ -21,7 +21,7 @@ from .transform import (centred, pad_rows, fourier_y, nvmt_positions, nvmt,
 from .funnel_direct import funnel_direct
 from .peaks_ref import peaks_ref, peak_to_line, inverse_peak_to_line
 from .adjoint_ref import adjoint_ref, map_loss_grad_ref
-from .verify_ref import band_profile, verify_ref
+from .verification import band_profile, verify_ref
 
 __all__ = [
     "centred", "pad_rows", "fourier_y", "nvmt_positions", "nvmt", "fourier_xprime",

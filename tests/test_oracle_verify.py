@@ -6,7 +6,7 @@ import os
 
 import numpy as np
 
-from oracle import verify_ref as vr
+from oracle import verification as vr
 from tests._lines import ridge_image
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
