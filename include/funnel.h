@@ -274,6 +274,28 @@ int ft_plan_get_precision(ft_plan plan);
  * *flags (host) and clears them.  0 when no split precision was ever set. */
 ft_status ft_plan_tc_errors(ft_plan plan, uint32_t* flags);
 
+/* Line verification (Sec. 4.5, steps 1-4) of detected peaks.  For peak j of
+ * image b (d_peaks[b * top_k + j], j < d_count[b], as written by ft_peaks on
+ * this plan's maps) the candidate line is read from the peak's map cell by
+ * eqs. (22)-(23) (regular space) or (24)-(25) (inverse space); a band of
+ * 2 * half_width + 1 pixels (half_width 1..3: the paper's 3 to 7) centred on
+ * the line is cut from the original image d_img (device, [batch][H][W] FP32,
+ * the forward's input) and integrated along the line's length: every image
+ * column (regular space; image row in the inverse space) gives one sample per
+ * offset d = -h..h at the line's centre row + d, linearly interpolated between
+ * the two nearest rows, counted where both rows are inside the image.
+ * Outputs (device): d_profile[b][j][2h+1] = mean sample per offset,
+ * d_length[b][j] = samples on the centre line, d_verdict[b][j] = 1 when
+ * d_length >= min_length and max(|p[0] - (p[-h] + p[h]) / 2|, |p[h] - p[-h]| / 2)
+ * >= min_contrast (ridge or step edge present), 0 when not, -1 for j >=
+ * d_count[b] (profile zeros).  The decision rule and the band geometry are
+ * readings of the paper's steps 2-4.  Stream-ordered, no allocation.
+ * FT_ERR_INVALID_ARG for null pointers, top_k outside 1..FT_MAX_TOPK or
+ * half_width outside 1..3. */
+ft_status ft_verify(ft_plan plan, const float* d_img, const ft_peak* d_peaks, const int32_t* d_count, int batch,
+                    int top_k, int half_width, float min_contrast, int32_t min_length, float* d_profile,
+                    int32_t* d_length, int32_t* d_verdict, void* stream);
+
 /* Bytes of plan-owned device workspace that a call with this batch needs. */
 size_t ft_workspace_bytes(ft_plan plan, int batch);
 
@@ -294,7 +316,8 @@ typedef enum {
     FT_KERNEL_PEAK_SELECT = 4,     /* Sec. 4.4, top_k per image */
     FT_KERNEL_NVMT_ROWS_ADJ = 5,   /* transpose of steps 2-3 */
     FT_KERNEL_LOSS = 6,            /* ft_abs_mse_grad */
-    FT_KERNEL_COUNT = 7
+    FT_KERNEL_VERIFY = 7,          /* ft_verify, Sec. 4.5 */
+    FT_KERNEL_COUNT = 8
 } ft_kernel_id;
 
 /* Per-launch timing (a measurement aid, off by default).  While enabled, every

@@ -311,6 +311,13 @@ cudaError_t launch_col_r2c_tc4096(const float* img, int H, int W, int row0, floa
 cudaError_t launch_col_c2r_tc4096(const float2* ws, int L, int S, float* map, int prec, unsigned* err, int batch,
                                   cudaStream_t st);
 
+// line verification of Sec. 4.5 (k_verify.cu): image element (v, u) of the
+// transform's frame at img[v * stride_v + u * stride_u] (image b at b * img_stride)
+cudaError_t launch_verify(const float* img, int H, int W, int stride_v, int stride_u, size_t img_stride, int S,
+                          int Hp, const ft_peak* peaks, const int32_t* count, int batch, int top_k, int h,
+                          float min_contrast, int min_length, float* profile, int32_t* length, int32_t* verdict,
+                          cudaStream_t st);
+
 // in[b][R][C] -> out[b][C][R] (k_transpose.cu)
 cudaError_t launch_transpose(const float* in, float* out, int R, int C, int batch, cudaStream_t st);
 

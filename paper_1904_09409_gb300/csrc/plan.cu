@@ -609,6 +609,25 @@ ft_status ft_abs_mse_grad(ft_plan p, const float* d_map, const float* d_target, 
     return FT_OK;
 }
 
+ft_status ft_verify(ft_plan p, const float* d_img, const ft_peak* d_peaks, const int32_t* d_count, int batch,
+                    int top_k, int half_width, float min_contrast, int32_t min_length, float* d_profile,
+                    int32_t* d_length, int32_t* d_verdict, void* stream) {
+    if (!p || batch < 0 || batch > 65535 || top_k < 1 || top_k > FT_MAX_TOPK) return FT_ERR_INVALID_ARG;
+    if (half_width < 1 || half_width > 3) return FT_ERR_INVALID_ARG;
+    if (batch == 0) return FT_OK;
+    if (!d_img || !d_peaks || !d_count || !d_profile || !d_length || !d_verdict) return FT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the transform's frame: the image itself, or its transpose in the inverse space
+    const bool inv = p->space == FT_SPACE_INVERSE;
+    const int stride_v = inv ? 1 : p->W, stride_u = inv ? p->img_W : 1;
+    FT_LAUNCH(p, FT_KERNEL_VERIFY, st,
+              launch_verify(d_img, p->H, p->W, stride_v, stride_u, (size_t)p->img_H * p->img_W, p->S, p->Hp, d_peaks,
+                            d_count, batch, top_k, half_width, min_contrast, min_length, d_profile, d_length,
+                            d_verdict, st),
+              "line verification");
+    return FT_OK;
+}
+
 ft_status ft_tc_dft64(const void* d_x, void* d_y, int nvec, int sign, int precision, uint32_t* d_err,
                       void* stream) {
     if (!d_x || !d_y || !d_err || nvec < 0 || (sign != 1 && sign != -1)) return FT_ERR_INVALID_ARG;
@@ -662,6 +681,7 @@ const char* ft_kernel_name(int id) {
         case FT_KERNEL_PEAK_SELECT: return "k_peak_select";
         case FT_KERNEL_NVMT_ROWS_ADJ: return "k_nvmt_rows_adjoint";
         case FT_KERNEL_LOSS: return "k_abs_mse_grad";
+        case FT_KERNEL_VERIFY: return "k_verify";
     }
     return "unknown";
 }

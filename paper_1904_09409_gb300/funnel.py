@@ -37,7 +37,7 @@ EXPORTED = (
     "ft_plan_variant_count", "ft_plan_set_variant", "ft_plan_get_variant",
     "ft_batch_create", "ft_batch_destroy", "ft_batch_layout", "ft_batch_group_count",
     "ft_batch_group_info", "ft_batch_group_tuned_ms", "ft_batch_run", "ft_tc_dft64",
-    "ft_plan_set_precision", "ft_plan_get_precision", "ft_plan_tc_errors",
+    "ft_plan_set_precision", "ft_plan_get_precision", "ft_plan_tc_errors", "ft_verify",
 )
 FT_PRECISION_FP32 = 0
 FT_PRECISION_BF16X3 = 1
@@ -51,7 +51,7 @@ FT_SPACE_REGULAR = 0
 FT_SPACE_INVERSE = 1
 SPACE_NAMES = {"regular": FT_SPACE_REGULAR, "inverse": FT_SPACE_INVERSE}
 FT_NOALLOC_SCRATCH_BYTES = 16 << 20
-FT_KERNEL_COUNT = 7
+FT_KERNEL_COUNT = 8
 
 
 class FtPeak(ctypes.Structure):
@@ -124,6 +124,8 @@ def lib() -> ctypes.CDLL:
     L.ft_plan_get_precision.restype = ci
     L.ft_plan_tc_errors.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
     L.ft_plan_tc_errors.restype = ci
+    L.ft_verify.argtypes = [vp, vp, vp, vp, ci, ci, ci, cf, ci, vp, vp, vp, vp]
+    L.ft_verify.restype = ci
     for name in ("ft_plan_variant_count", "ft_plan_set_variant", "ft_plan_get_variant", "ft_batch_create",
                  "ft_batch_destroy", "ft_batch_layout", "ft_batch_group_count", "ft_batch_group_info",
                  "ft_batch_run"):
@@ -250,6 +252,27 @@ def ft_peaks(plan: Plan, fmap, top_k: int, threshold: float = float("-inf"), out
     _check(lib().ft_peaks(plan.handle, mp, b, int(top_k), float(threshold), op, cp,
                           _stream_ptr(stream)), "ft_peaks")
     return out, count
+
+
+def ft_verify(plan: Plan, img, peaks, count, top_k: int, half_width: int = 2, min_contrast: float = 0.1,
+              min_length: int = 16, batch: Optional[int] = None, stream=None):
+    """Line verification (Sec. 4.5) of the peaks ft_peaks wrote for this plan.
+    img: the forward's input (batch, H, W) CUDA float32; peaks/count: ft_peaks'
+    outputs.  Returns (profile [batch, top_k, 2h+1] float32, length
+    [batch, top_k] int32, verdict [batch, top_k] int32: 1 line, 0 none, -1 no peak)."""
+    import torch
+    b = img.shape[0] if batch is None else int(batch)
+    ip = _dev_ptr(img, "float32", b * plan.H * plan.W, "img")
+    pp = _dev_ptr(peaks, "uint8", b * top_k * PEAK_DTYPE.itemsize, "peaks")
+    cp = _dev_ptr(count, "int32", b, "count")
+    nb = 2 * int(half_width) + 1
+    prof = torch.empty((b, top_k, nb), dtype=torch.float32, device=img.device)
+    length = torch.empty((b, top_k), dtype=torch.int32, device=img.device)
+    verdict = torch.empty((b, top_k), dtype=torch.int32, device=img.device)
+    _check(lib().ft_verify(plan.handle, ip, pp, cp, b, int(top_k), int(half_width), float(min_contrast),
+                           int(min_length), prof.data_ptr(), length.data_ptr(), verdict.data_ptr(),
+                           _stream_ptr(stream)), "ft_verify")
+    return prof, length, verdict
 
 
 def ft_peaks_noalloc(fmap, top_k: int, threshold: float = float("-inf"), out=None, count=None,

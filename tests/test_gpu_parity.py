@@ -331,3 +331,71 @@ def test_fourier_interp_has_no_adjoint(torch):
         with pytest.raises(f.FunnelError) as e:
             f.ft_backward(plan, g, torch.empty_like(g))
         assert e.value.status == f.FT_ERR_UNSUPPORTED_SIZE
+
+
+# ------------------------------------------------------- line verification
+def _verify_both(plan, imgs, maps, K, h, min_contrast, min_length, inverse=False):
+    from paper_1904_09409_gb300 import funnel as f
+    from oracle import verification as vr
+    import torch
+    x = torch.from_numpy(np.ascontiguousarray(imgs, dtype=np.float32)).cuda()
+    m = torch.from_numpy(np.ascontiguousarray(maps, dtype=np.float32)).cuda()
+    pk, cnt = f.ft_peaks(plan, m, K)
+    prof, length, verdict = f.ft_verify(plan, x, pk, cnt, K, h, min_contrast, min_length)
+    torch.cuda.synchronize()
+    recs = f.peaks_to_numpy(pk, cnt, K)
+    prof, length, verdict = prof.cpu().numpy(), length.cpu().numpy(), verdict.cpu().numpy()
+    out = []
+    for i in range(imgs.shape[0]):
+        cells = [(int(r["t"]), int(r["s"])) for r in recs[i]]
+        ref = vr.verify_ref(imgs[i].astype(np.float64), cells, plan.S, plan.Hp, h, min_contrast, min_length,
+                            inverse=inverse)
+        for j, (p_ref, len_ref, ok_ref) in enumerate(ref):
+            assert length[i, j] == len_ref, (i, j)
+            assert np.max(np.abs(prof[i, j] - p_ref)) <= 1e-5 * max(1.0, np.max(np.abs(p_ref))), (i, j)
+            c = vr.contrast(p_ref)
+            if length[i, j] >= min_length and abs(c - min_contrast) > 1e-4:
+                assert verdict[i, j] == int(ok_ref), (i, j, c)
+        for j in range(len(ref), K):
+            assert verdict[i, j] == -1 and length[i, j] == 0
+        out.append((cells, verdict[i, :len(ref)]))
+    return out
+
+
+@pytest.mark.parametrize("h", [1, 2, 3])
+def test_verify_matches_oracle_on_benchmark_images(torch, h):
+    """Sec. 4.5 on the benchmark's content (1024^2, 1-20 ridge/step lines,
+    occluders, noise): band profiles, lengths and verdicts of the top-32 peaks
+    against the oracle; the true lines' cells are verified."""
+    imgs = synth.batch_1024(3)
+    with make_plan(1024, 1024, 1024, 1024) as plan:
+        maps = _gpu.forward(plan, imgs)
+        res = _verify_both(plan, imgs, maps, 32, h, 0.05, 64)
+    n_true = sum(int(v.sum()) for _, v in res)
+    assert n_true >= 3
+
+
+def test_verify_fewer_peaks_than_slots(torch):
+    maps = np.zeros((1, 64, 64), np.float32)
+    maps[0, 30, 40] = 5.0
+    imgs = np.random.default_rng(3).uniform(0, 1, (1, 64, 64)).astype(np.float32)
+    with make_plan(64, 64, 64, 64) as plan:
+        _verify_both(plan, imgs, maps, 8, 2, 0.1, 8)
+
+
+def test_verify_fig9_regular_rejects_inverse_accepts(torch):
+    """Fig. 9: the brightest regular-space peak of the 3.27-slope line is a
+    wrapping peak whose line does not exist; the inverse-space peak's line does."""
+    import json
+    import os
+    from paper_1904_09409_gb300 import funnel as f
+    from tests._lines import ridge_image
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "fig9_wrapped_peak.json")))
+    W, H, k = g["width_M"], g["height_N"], g["slope_k"]
+    img = ridge_image(H, W, W + H, [(k, float(g["regular_peak_mn"][1]))])[None].astype(np.float32)
+    with f.Plan(H, W, 432, 648, space="inverse") as plan:
+        (cells, ver), = _verify_both(plan, img, _gpu.forward(plan, img), 1, 2, 0.2, 20, inverse=True)
+        assert ver[0] == 1
+    with f.Plan(H, W, 192, 648) as plan:             # n_slope 192 >= 170, 648 >= 598: 2^a 3^b
+        (cells, ver), = _verify_both(plan, img, _gpu.forward(plan, img), 1, 2, 0.2, 20)
+        assert ver[0] == 0
