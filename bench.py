@@ -595,6 +595,29 @@ def run_extras(f, args, plan, imgs, lines, x, stream, dev, rank, ws, vl_imgs, vl
     fplan.close()
     del mf
 
+    # Sec. 4.5 line verification of the step's top-32 peaks (band of 5 pixels)
+    pk_b = torch.empty(BATCH * TOP_K * f.PEAK_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    cn_b = torch.empty(BATCH, dtype=torch.int32, device=dev)
+    mv = torch.empty((BATCH, SIDE, SIDE), dtype=torch.float32, device=dev)
+    f.ft_forward(plan, x, mv, stream=stream)
+    f.ft_peaks(plan, mv, TOP_K, out=pk_b, count=cn_b, stream=stream)
+    for _ in range(3):
+        f.ft_verify(plan, x, pk_b, cn_b, TOP_K, 2, 0.05, 64, stream=stream)
+    v_steps = max(3, min(args.steps, 50))
+    v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    v0.record(stream)
+    for _ in range(v_steps):
+        _, _, verdict = f.ft_verify(plan, x, pk_b, cn_b, TOP_K, 2, 0.05, 64, stream=stream)
+    v1.record(stream)
+    torch.cuda.synchronize(dev)
+    v_ms = v0.elapsed_time(v1) / v_steps
+    verified = int((verdict == 1).sum().item())
+    del mv
+    verify = {"ms_per_call": v_ms, "peaks_per_s": BATCH * TOP_K / (v_ms / 1e3), "steps": v_steps,
+              "verified": verified, "peaks": int(cn_b.sum().item()),
+              "workload": f"ft_verify of the top-{TOP_K} peaks of the same {BATCH} x 1024^2 maps: band of 5 pixels, "
+                          "contrast >= 0.05, centre line >= 64 samples"}
+
     precision = None
     if big_imgs is not None:
         precision = time_precision(f, big_imgs, max(3, min(args.steps, 20)), stream, dev)
@@ -615,6 +638,7 @@ def run_extras(f, args, plan, imgs, lines, x, stream, dev, rank, ws, vl_imgs, vl
                 "d2h_bytes_per_step": ws * (BATCH * TOP_K * f.PEAK_DTYPE.itemsize + BATCH * 4),
                 "call": "ft_detect_host", "steps": e2e_steps, "h2d_copy_gbs": h2d_gbs},
         "varlen": varlen,
+        "verify": verify,
         "precision_4096": precision,
         "fourier_interp": {"value": px_step / (fo_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": fo_ms,
                            "steps": fo_steps,
