@@ -67,8 +67,8 @@ typedef enum {
  * a = -0.5.  FOURIER: the trigonometric interpolant of the row (Nyquist term as
  * a cosine) evaluated at the samples by a chirp-z (Bluestein) convolution of
  * length M = the smallest 2^a 3^b >= W + S, zero outside p in [-W/2, W/2-1];
- * W must then be 2^a 3^b and M <= FT_MAX_LENGTH; ft_backward is not available
- * for it (FT_ERR_UNSUPPORTED_SIZE). */
+ * W must then be 2^a 3^b and M <= FT_MAX_LENGTH; ft_backward runs its exact
+ * transpose (the chirp-z stages conjugated in reverse order). */
 typedef enum {
     FT_INTERP_LINEAR = 0,
     FT_INTERP_CUBIC = 1,

@@ -289,6 +289,9 @@ size_t peaks_key_bytes(int Hp, int S, int batch, int top_k);
 
 // the band-limited NVMT fused with step 3 (k_fourier.cu)
 cudaError_t launch_chirp_fft(float2* hc, int L, const FftLen& fm, cudaStream_t st);
+cudaError_t launch_nvmt_rows_fourier_adj(float2* ws, int W, int S, int Hp, int L, const FftLen& fw,
+                                         const FftLen& fm, const FftLen& fs, const float2* chirp_u,
+                                         const float2* chirp_x, const float2* hc, int batch, cudaStream_t st);
 cudaError_t launch_nvmt_rows_fourier(float2* ws, int W, int S, int Hp, int L, const FftLen& fw,
                                      const FftLen& fm, const FftLen& fs, const float2* chirp_u,
                                      const float2* chirp_x, const float2* hc, int batch, cudaStream_t st);

@@ -231,6 +231,11 @@ static cudaError_t nvmt_rows(ft_plan p, float2* ws, int batch, cudaStream_t st) 
 }
 
 static cudaError_t nvmt_rows_adj(ft_plan p, float2* ws, int batch, cudaStream_t st) {
+    if (p->interp == FT_INTERP_FOURIER) {
+        const size_t nu = (size_t)p->L * (p->W + 1), nx = (size_t)p->L * p->S;
+        return launch_nvmt_rows_fourier_adj(ws, p->W, p->S, p->Hp, p->L, p->fw, p->fm, p->fx, p->d_chirp,
+                                            p->d_chirp + nu, p->d_chirp + nu + nx, batch, st);
+    }
     if (p->use_fast_x) return launch_nvmt_rows_adjoint_fast(ws, p->W, p->Hp, p->L, p->interp, p->fx, batch, st);
     return launch_nvmt_rows_adjoint(ws, p->W, p->S, p->Hp, p->L, p->interp, p->fx, p->row_logB_x, batch, st);
 }
@@ -535,8 +540,6 @@ ft_status ft_forward(ft_plan p, const float* d_img, float* d_map, int batch, voi
 
 ft_status ft_backward(ft_plan p, const float* d_grad_map, float* d_grad_img, int batch, void* stream) {
     if (!p || batch < 0 || batch > 65535) return FT_ERR_INVALID_ARG;
-    if (p->interp == FT_INTERP_FOURIER)
-        return ft_record_error(FT_ERR_UNSUPPORTED_SIZE, "ft_backward: no adjoint for the band-limited interpolator");
     if (batch == 0) return FT_OK;
     if (!d_grad_map || !d_grad_img || ((uintptr_t)d_grad_map & 7) || ((uintptr_t)d_grad_img & 7))
         return FT_ERR_INVALID_ARG;

@@ -324,13 +324,22 @@ def test_fourier_interp_matches_oracle(torch, H, W, S, Hp):
         assert _gpu.rel_l2(got[i], ref) <= TOL_MAP, _gpu.rel_l2(got[i], ref)
 
 
-def test_fourier_interp_has_no_adjoint(torch):
-    from paper_1904_09409_gb300 import funnel as f
-    with make_plan(32, 32, 32, 32, "fourier") as plan:
-        g = torch.zeros((1, 32, 32), device="cuda")
-        with pytest.raises(f.FunnelError) as e:
-            f.ft_backward(plan, g, torch.empty_like(g))
-        assert e.value.status == f.FT_ERR_UNSUPPORTED_SIZE
+@pytest.mark.parametrize("H,W,S,Hp", [(32, 32, 32, 32), (48, 48, 64, 72), (64, 64, 128, 96), (256, 256, 256, 256)])
+def test_fourier_interp_adjoint_matches_oracle(torch, H, W, S, Hp):
+    """ft_backward with the band-limited interpolator: the oracle's transpose
+    (dense Dirichlet kernel scattered back) and the dot-product identity."""
+    rng = np.random.default_rng(H * W + S)
+    g = rng.standard_normal((2, Hp, S)).astype(np.float32)
+    x = rng.standard_normal((2, H, W)).astype(np.float32)
+    with make_plan(H, W, S, Hp, "fourier") as plan:
+        gi = _gpu.backward(plan, g)
+        px = _gpu.forward(plan, x)
+    for i in range(2):
+        ref = oracle.adjoint_ref(g[i].astype(np.float64), H, W, "fourier")
+        assert _gpu.rel_l2(gi[i], ref) <= TOL_MAP
+        lhs = float(np.sum(px[i].astype(np.float64) * g[i]))
+        rhs = float(np.sum(x[i].astype(np.float64) * gi[i]))
+        assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(px[i]) * np.linalg.norm(g[i])
 
 
 # ------------------------------------------------------- line verification
