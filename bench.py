@@ -383,7 +383,9 @@ def cpu_baseline(imgs):
         time_oracle_sample(pool, imgs[:cores])                      # warm-up (imports)
         wall, per = time_oracle_sample(pool, imgs)
     px = n_images * SIDE * SIDE
+    single = statistics.median(per)                                 # one image on one core
     return {"value": px / wall / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_core_s_per_image": single, "single_core_value": SIDE * SIDE / single / 1e6,
             "sample": f"{n_images} of the 64 images (FP64 NumPy map + Sec. 4.4 peak list), "
                       f"one image per task, {cores} processes; {sum(per):.1f} CPU-s"}
 
@@ -513,6 +515,18 @@ def run_ours(args):
                 "unit": "GB/s", "frac": k["achieved_gbs"] / hbm, "peak_source": src,
                 "traffic": ncu_traffic(dom, k["images_per_launch"]),
                 "algorithmic_bytes_per_launch": k["algorithmic_bytes_per_launch"]}
+    # the whole step against the same peak: compulsory bytes (image in, map out: 8 B/px),
+    # algorithmic bytes (every kernel's inputs and outputs) and the ncu DRAM bytes
+    step_s = ms / args.steps / 1e3
+    alg = sum(kernel_bytes(n, SIDE, SIDE, SIDE, SIDE, TOP_K) for n in prof) * BATCH
+    traf = [ncu_traffic(n, BATCH) for n in prof]
+    step_roof = {"compulsory_gbs": 8.0 * BATCH * SIDE * SIDE / step_s / 1e9,
+                 "algorithmic_gbs": alg / step_s / 1e9,
+                 "dram_gbs": (sum(traf) / step_s / 1e9) if all(t is not None for t in traf) else None,
+                 "peak": hbm, "unit": "GB/s"}
+    step_roof["compulsory_frac"] = step_roof["compulsory_gbs"] / hbm
+    step_roof["algorithmic_frac"] = step_roof["algorithmic_gbs"] / hbm
+    step_roof["dram_frac"] = step_roof["dram_gbs"] / hbm if step_roof["dram_gbs"] else None
     launches = sum(n for _, n in prof.values())          # our kernels launched in the timed region
     if rank == 0:
         line = {
@@ -524,6 +538,7 @@ def run_ours(args):
                        "top_k": TOP_K, "l2": "inputs larger than L2 (268 MB images + 268 MB maps per GPU)",
                        "parallelism": f"replicas x{ws}, no collective on the data path"},
             "roofline": roof,
+            "step_roofline": step_roof,
             "kernels": kernels,
             "cpu_baseline": cpu,
             **extra,
