@@ -176,7 +176,9 @@ k_nvmt_rows_fast(float2* __restrict__ ws, int W, int Hp, int L, const float2* __
     constexpr int STEPX = N / R0;                      // x' distance between a thread's elements
     using F = FastFft<N, +1, B>;
     extern __shared__ float2 sm[];
-    float2* srow = sm + ((F::SLOTS + 1) & ~1);         // [B][W + 2] input rows (16-byte aligned)
+    // [B][W + 2] input rows (16-byte aligned) in the FFT's own exchange buffer:
+    // they are read only by the gather, which ends before the first exchange
+    float2* srow = sm;
     const int WP = srow_pitch(W);
     const int f = threadIdx.x % B;
     const int t = threadIdx.x / B;
@@ -244,6 +246,7 @@ k_nvmt_rows_fast(float2* __restrict__ ws, int W, int Hp, int L, const float2* __
             }
         }
     }
+    __syncthreads();                                   // the staged rows are dead from here
     F::template run<0>(v, sm, t, f, stw);
     if (l >= L) return;
     float2* row = base + (size_t)l * N;
@@ -370,7 +373,8 @@ static cudaError_t go_c2r(const float2* in, int ncols, int in_pitch, size_t in_i
 template <int N, int INTERP>
 static cudaError_t go_rows_i(float2* ws, int W, int Hp, int L, const float2* stw, int batch, cudaStream_t st) {
     constexpr int B = fs_Brow(N);
-    const size_t sm = ((size_t)((FastFft<N, +1, B>::SLOTS + 1) & ~1) + (size_t)srow_pitch(W) * B) * sizeof(float2);
+    const size_t slots = FastFft<N, +1, B>::SLOTS, rows = (size_t)srow_pitch(W) * B;
+    const size_t sm = (slots > rows ? slots : rows) * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_nvmt_rows_fast<N, INTERP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     dim3 grid((L + B - 1) / B, batch);
