@@ -98,14 +98,12 @@ def time_fwd_bwd(f, plan, x, target, steps, stream, dev):
     time per step (ms) and per-kernel timing of the timed region."""
     import torch
     P = torch.empty((x.shape[0], plan.Hp, plan.S), dtype=torch.float32, device=dev)
-    dP = torch.empty_like(P)
     loss = torch.empty(x.shape[0], dtype=torch.float32, device=dev)
     gx = torch.empty_like(x)
 
     def step():
         f.ft_forward(plan, x, P, stream=stream)
-        f.ft_abs_mse_grad(plan, P, target, 2.0 / plan.W, loss=loss, grad=dP, stream=stream)
-        f.ft_backward(plan, dP, gx, stream=stream)
+        f.ft_abs_mse_backward(plan, P, target, 2.0 / plan.W, loss=loss, grad_img=gx, stream=stream)
 
     for _ in range(3):
         step()
@@ -661,9 +659,10 @@ def run_extras(f, args, plan, imgs, lines, x, stream, dev, rank, ws, vl_imgs, vl
                                        "(chirp-z, Sec. IV) interpolator instead of the linear one"},
         "fwd_bwd": {"value": px_step / (fb_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": fb_ms,
                     "steps": fb_steps, "kernels_us": fb_kernels,
-                    "workload": "the same 64 x 1024^2 batch: ft_forward + ft_abs_mse_grad (loss "
+                    "workload": "the same 64 x 1024^2 batch: ft_forward + ft_abs_mse_backward (loss "
                                 "mean((|P|/(W/2) - T)^2), T Gaussian blobs of 2 cells at the drawn "
-                                "lines) + ft_backward"},
+                                "lines, and its gradient with respect to the images through the exact "
+                                "adjoint; the map gradient is formed inside the first adjoint kernel)"},
         "fwd_bwd_512": {"value": ws * 32 * 512 * 512 / (fb512_ms / 1e3) / 1e6, "unit": UNIT,
                         "ms_per_step": fb512_ms, "steps": fb_steps,
                         "workload": "32 x 512^2 gradient workload, same step"},

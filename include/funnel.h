@@ -145,6 +145,17 @@ ft_status ft_peaks(ft_plan plan, const float* d_map, int batch, int top_k, float
 ft_status ft_abs_mse_grad(ft_plan plan, const float* d_map, const float* d_target, int batch, float scale,
                           float* d_loss, float* d_grad_map, void* stream);
 
+/* The same loss and, instead of its map gradient, the gradient with respect to
+ * the images: ft_abs_mse_grad followed by ft_backward in one call, with the
+ * map gradient computed inside the first adjoint kernel as the map and target
+ * columns are loaded, so it is never written to or read back from memory.
+ * d_grad_img: [batch][H][W] FP32 (device, caller-owned).  The per-image sums
+ * are deterministic but summed in another order than ft_abs_mse_grad's (the
+ * losses agree to FP32 rounding).  Lengths n_intercept without a fixed-length
+ * kernel go through a plan-owned map gradient instead (same results). */
+ft_status ft_abs_mse_backward(ft_plan plan, const float* d_map, const float* d_target, int batch, float scale,
+                              float* d_loss, float* d_grad_img, void* stream);
+
 /* End-to-end detection from host memory: copies h_img ([batch][H][W]) to a
  * plan-owned device buffer, runs ft_forward and ft_peaks, copies the peaks and
  * counts back to h_out ([batch][top_k]) and h_count ([batch]) and synchronises

@@ -201,6 +201,13 @@ __host__ __device__ constexpr bool col_stage_ok(int ncols, int in_pitch) { retur
 cudaError_t launch_col_r2c_fast(const float* in, int rows_in, int ncols, int in_pitch, size_t in_img,
                                 int row0, const FftLen& f, float2* out, int out_pitch, size_t out_img,
                                 float end_scale, float mid_scale, int batch, cudaStream_t st);
+// the adjoint of step 4 with the input gradient computed from the map and the
+// target of the gradient workload (k_col_r2c_loss_fast); partial gets
+// col_r2c_loss_blocks() floats per image
+int col_r2c_loss_blocks(const FftLen& f, int ncols);
+cudaError_t launch_col_r2c_loss_fast(const float* map, const float* target, int ncols, const FftLen& f,
+                                     float2* out, int out_pitch, size_t out_img, float end_scale, float mid_scale,
+                                     float scale, float gscale, float* partial, int batch, cudaStream_t st);
 cudaError_t launch_col_c2r_fast(const float2* in, int ncols, int in_pitch, size_t in_img,
                                 const FftLen& f, float mid_scale, float* out, int row0, int rows_out,
                                 int out_pitch, size_t out_img, float out_scale, int batch,

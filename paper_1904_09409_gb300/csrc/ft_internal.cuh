@@ -329,3 +329,5 @@ cudaError_t launch_transpose(const float* in, float* out, int R, int C, int batc
 cudaError_t launch_abs_mse_grad(const float* map, const float* target, int batch, size_t cells, float scale,
                                 float* loss, float* grad, float* partial, cudaStream_t st);
 size_t loss_partial_bytes(int batch);
+// per-image loss from nblk partials each (fixed order, compensated), divided by cells
+cudaError_t launch_loss_finish(const float* partial, int nblk, size_t cells, float* loss, int batch, cudaStream_t st);

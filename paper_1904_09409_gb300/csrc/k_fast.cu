@@ -163,6 +163,87 @@ k_col_c2r_fast(const float2* __restrict__ in, int ncols, int in_pitch, size_t in
         }
 }
 
+// The adjoint of step 4 fed straight from the loss of the gradient workload:
+// the input column pair is not a stored gradient map but
+//     g = 2 r scale sign(P) gscale,   r = |P| scale - T
+// computed from the map P and the target T as the columns are loaded (the loss
+// gradient of k_loss.cu), while every thread adds r^2 of its samples (FP32,
+// compensated) and the block writes one partial of the image's loss.  Each map
+// cell is loaded by exactly one thread, so the partials of an image's blocks
+// add up to its sum of r^2.  Everything after the load is k_col_r2c_fast.
+template <int N>
+__global__ void __launch_bounds__(fs_T(N) * fs_Bcol(N))
+k_col_r2c_loss_fast(const float* __restrict__ map, const float* __restrict__ target, int ncols, size_t img_cells,
+                    const float2* __restrict__ stw, float2* __restrict__ out, int out_pitch, size_t out_img,
+                    float end_scale, float mid_scale, float scale, float gscale, float* __restrict__ partial) {
+    constexpr int B = fs_Bcol(N), E = fs_E(N), T = N / E;
+    constexpr int R0 = fs_radix(N, 0), G0 = E / R0;
+    constexpr int RL = fs_radix(N, fs_nst(N) - 1), GL = E / RL;
+    using F = FastFft<N, -1, B>;
+    extern __shared__ float2 sm[];
+    __shared__ float red[fs_T(N) * fs_Bcol(N)];
+    const int f = threadIdx.x % B;
+    const int t = threadIdx.x / B;
+    const int c = blockIdx.x * 2 * B + 2 * f;
+    const bool colok = c < ncols;
+    const float* P = map + (size_t)blockIdx.y * img_cells + c;
+    const float* Tg = target + (size_t)blockIdx.y * img_cells + c;
+
+    float2 v[E];
+    float acc = 0.f, comp = 0.f;
+    auto add = [&](float y) {                          // compensated sum of r^2
+        const float z = y - comp;
+        const float s2 = acc + z;
+        comp = (s2 - acc) - z;
+        acc = s2;
+    };
+#pragma unroll
+    for (int m = 0; m < G0; ++m)
+#pragma unroll
+        for (int q = 0; q < R0; ++q) {
+            const int row = F::template in_pos<0>(t, m, q);
+            float2 g = make_float2(0.f, 0.f);
+            if (colok) {
+                const float2 p = __ldg(reinterpret_cast<const float2*>(P + (size_t)row * ncols));
+                const float2 tt = __ldg(reinterpret_cast<const float2*>(Tg + (size_t)row * ncols));
+                const float r0 = fabsf(p.x) * scale - tt.x, r1 = fabsf(p.y) * scale - tt.y;
+                add(r0 * r0);
+                add(r1 * r1);
+                const float s0 = p.x > 0.f ? 1.f : (p.x < 0.f ? -1.f : 0.f);
+                const float s1 = p.y > 0.f ? 1.f : (p.y < 0.f ? -1.f : 0.f);
+                g = make_float2(2.f * r0 * scale * s0 * gscale, 2.f * r1 * scale * s1 * gscale);
+            }
+            v[m * R0 + q] = g;
+        }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = (fs_T(N) * fs_Bcol(N)) / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+    F::template run<0>(v, sm, t, f, stw);
+#pragma unroll
+    for (int m = 0; m < GL; ++m)
+#pragma unroll
+        for (int q = 0; q < RL; ++q) sm[spos(F::out_pos(t, m, q)) * B + f] = v[m * RL + q];
+    __syncthreads();
+
+    float2* dst = out + (size_t)blockIdx.y * out_img + c;
+    if (!colok) return;
+    for (int l = t; l <= N / 2; l += T) {
+        const float2 zl = sm[spos(l) * B + f];
+        const float2 zm = sm[spos(l == 0 ? 0 : N - l) * B + f];
+        const float s = (l == 0 || l == N / 2) ? end_scale : mid_scale;
+        float4 o;
+        o.x = 0.5f * s * (zl.x + zm.x);
+        o.y = 0.5f * s * (zl.y - zm.y);
+        o.z = 0.5f * s * (zl.y + zm.y);
+        o.w = -0.5f * s * (zl.x - zm.x);
+        *reinterpret_cast<float4*>(dst + (size_t)l * out_pitch) = o;
+    }
+}
+
 // row pitch (complex) of the staged spectrum rows: W + 2 keeps 16-byte
 // alignment for cp.async and shifts successive rows by 4 banks
 __host__ __device__ constexpr int srow_pitch(int W) { return W + 2; }
@@ -357,6 +438,20 @@ static cudaError_t go_r2c(const float* in, int rows_in, int ncols, int in_pitch,
 }
 
 template <int N>
+static cudaError_t go_r2c_loss(const float* map, const float* target, int ncols, const float2* stw, float2* out,
+                               int out_pitch, size_t out_img, float es, float ms, float scale, float gscale,
+                               float* partial, int batch, cudaStream_t st) {
+    constexpr int B = fs_Bcol(N);
+    const size_t sm = (size_t)FastFft<N, -1, B>::SLOTS * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_col_r2c_loss_fast<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid((ncols + 2 * B - 1) / (2 * B), batch);
+    k_col_r2c_loss_fast<N><<<grid, fs_T(N) * B, sm, st>>>(map, target, ncols, (size_t)N * ncols, stw, out, out_pitch,
+                                                          out_img, es, ms, scale, gscale, partial);
+    return cudaGetLastError();
+}
+
+template <int N>
 static cudaError_t go_c2r(const float2* in, int ncols, int in_pitch, size_t in_img, const float2* stw,
                           float mid, float* out, int row0, int rows_out, int out_pitch, size_t out_img,
                           float os, int batch, cudaStream_t st) {
@@ -413,6 +508,28 @@ cudaError_t launch_col_r2c_fast(const float* in, int rows_in, int ncols, int in_
     switch (f.N) {
 #define X(n) case n: return go_r2c<n>(in, rows_in, ncols, in_pitch, in_img, row0, f.stw, out, out_pitch, \
                                       out_img, end_scale, mid_scale, batch, st);
+        FT_FAST_LENGTHS(X)
+#undef X
+    }
+    return cudaErrorNotSupported;
+}
+
+int col_r2c_loss_blocks(const FftLen& f, int ncols) {
+    switch (f.N) {
+#define X(n) case n: return (ncols + 2 * fs_Bcol(n) - 1) / (2 * fs_Bcol(n));
+        FT_FAST_LENGTHS(X)
+#undef X
+    }
+    return 0;
+}
+
+cudaError_t launch_col_r2c_loss_fast(const float* map, const float* target, int ncols, const FftLen& f,
+                                     float2* out, int out_pitch, size_t out_img, float end_scale, float mid_scale,
+                                     float scale, float gscale, float* partial, int batch, cudaStream_t st) {
+    if (ncols & 1) return cudaErrorInvalidValue;
+    switch (f.N) {
+#define X(n) case n: return go_r2c_loss<n>(map, target, ncols, f.stw, out, out_pitch, out_img, end_scale, mid_scale, \
+                                           scale, gscale, partial, batch, st);
         FT_FAST_LENGTHS(X)
 #undef X
     }

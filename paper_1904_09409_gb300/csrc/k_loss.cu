@@ -56,6 +56,11 @@ __global__ void k_loss_finish(const float* __restrict__ partial, int nblk, size_
 
 size_t loss_partial_bytes(int batch) { return (size_t)batch * LOSS_BLOCKS * sizeof(float); }
 
+cudaError_t launch_loss_finish(const float* partial, int nblk, size_t cells, float* loss, int batch, cudaStream_t st) {
+    k_loss_finish<<<batch, 1, 0, st>>>(partial, nblk, cells, loss);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_abs_mse_grad(const float* map, const float* target, int batch, size_t cells, float scale,
                                 float* loss, float* grad, float* partial, cudaStream_t st) {
     dim3 g1(LOSS_BLOCKS, batch);

@@ -538,6 +538,19 @@ ft_status ft_forward(ft_plan p, const float* d_img, float* d_map, int batch, voi
     return lanes_join(p, st);
 }
 
+// the adjoint after its first step (the spectrum of the map gradient is in ws)
+static ft_status backward_tail(ft_plan p, float2* ws, float* d_grad_img, int batch, cudaStream_t st) {
+    float* gdst = d_grad_img;
+    if (p->space == FT_SPACE_INVERSE) gdst = (float*)((char*)p->d_ws + tposed_off(p, batch));
+    FT_LAUNCH(p, FT_KERNEL_NVMT_ROWS_ADJ, st, nvmt_rows_adj(p, ws, batch, st), "adjoint of steps 2-3");
+    FT_LAUNCH(p, FT_KERNEL_COL_C2R, st,
+              col_c2r(p, ws, p->W, 0.5f, gdst, p->top, p->H, p->W, (size_t)p->H * p->W, 1.f, batch, st),
+              "adjoint of step 1");
+    if (p->space == FT_SPACE_INVERSE)
+        FT_CUDA(launch_transpose(gdst, d_grad_img, p->H, p->W, batch, st), "transpose back (inverse space)");
+    return FT_OK;
+}
+
 ft_status ft_backward(ft_plan p, const float* d_grad_map, float* d_grad_img, int batch, void* stream) {
     if (!p || batch < 0 || batch > 65535) return FT_ERR_INVALID_ARG;
     if (batch == 0) return FT_OK;
@@ -548,18 +561,48 @@ ft_status ft_backward(ft_plan p, const float* d_grad_map, float* d_grad_img, int
     cudaStream_t st = (cudaStream_t)stream;
     float2* ws = (float2*)p->d_ws;
     const float inv = 1.f / (float)p->Hp;
-    float* gdst = d_grad_img;
-    if (p->space == FT_SPACE_INVERSE) gdst = (float*)((char*)p->d_ws + tposed_off(p, batch));
     FT_LAUNCH(p, FT_KERNEL_COL_R2C, st,
               col_r2c(p, d_grad_map, p->Hp, p->S, p->S, (size_t)p->Hp * p->S, 0, ws, inv, 2.f * inv, batch, st),
               "adjoint of step 4");
-    FT_LAUNCH(p, FT_KERNEL_NVMT_ROWS_ADJ, st, nvmt_rows_adj(p, ws, batch, st), "adjoint of steps 2-3");
-    FT_LAUNCH(p, FT_KERNEL_COL_C2R, st,
-              col_c2r(p, ws, p->W, 0.5f, gdst, p->top, p->H, p->W, (size_t)p->H * p->W, 1.f, batch, st),
-              "adjoint of step 1");
-    if (p->space == FT_SPACE_INVERSE)
-        FT_CUDA(launch_transpose(gdst, d_grad_img, p->H, p->W, batch, st), "transpose back (inverse space)");
-    return FT_OK;
+    return backward_tail(p, ws, d_grad_img, batch, st);
+}
+
+ft_status ft_abs_mse_backward(ft_plan p, const float* d_map, const float* d_target, int batch, float scale,
+                              float* d_loss, float* d_grad_img, void* stream) {
+    if (!p || batch < 0 || batch > 65535) return FT_ERR_INVALID_ARG;
+    if (batch == 0) return FT_OK;
+    if (!d_map || !d_target || !d_loss || !d_grad_img || ((uintptr_t)d_map & 7) || ((uintptr_t)d_target & 7) ||
+        ((uintptr_t)d_grad_img & 7))
+        return FT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t cells = (size_t)p->Hp * p->S;
+    const size_t off = aux_off(p, batch);
+    if (!p->use_fast_y) {
+        // no fused kernel for this length: the loss gradient through the workspace
+        const size_t gbytes = (batch * cells * sizeof(float) + 255) & ~(size_t)255;
+        ft_status s = ensure(&p->d_ws, &p->ws_bytes, off + gbytes + loss_partial_bytes(batch),
+                             "cudaMalloc(workspace)");
+        if (s != FT_OK) return s;
+        float* gmap = (float*)((char*)p->d_ws + off);
+        FT_LAUNCH(p, FT_KERNEL_LOSS, st,
+                  launch_abs_mse_grad(d_map, d_target, batch, cells, scale, d_loss, gmap,
+                                      (float*)((char*)p->d_ws + off + gbytes), st),
+                  "loss");
+        return ft_backward(p, gmap, d_grad_img, batch, stream);
+    }
+    const int nblk = col_r2c_loss_blocks(p->fy, p->S);
+    ft_status s = ensure(&p->d_ws, &p->ws_bytes, off + (size_t)batch * nblk * sizeof(float), "cudaMalloc(workspace)");
+    if (s != FT_OK) return s;
+    float2* ws = (float2*)p->d_ws;
+    float* partial = (float*)((char*)p->d_ws + off);
+    const float inv = 1.f / (float)p->Hp;
+    const float gscale = (float)(1.0 / ((double)batch * (double)cells));
+    FT_LAUNCH(p, FT_KERNEL_COL_R2C, st,
+              launch_col_r2c_loss_fast(d_map, d_target, p->S, p->fy, ws, p->S, (size_t)p->L * p->S, inv, 2.f * inv,
+                                       scale, gscale, partial, batch, st),
+              "loss and adjoint of step 4");
+    FT_LAUNCH(p, FT_KERNEL_LOSS, st, launch_loss_finish(partial, nblk, cells, d_loss, batch, st), "loss");
+    return backward_tail(p, ws, d_grad_img, batch, st);
 }
 
 ft_status ft_peaks(ft_plan p, const float* d_map, int batch, int top_k, float threshold,

@@ -38,6 +38,7 @@ EXPORTED = (
     "ft_batch_create", "ft_batch_destroy", "ft_batch_layout", "ft_batch_group_count",
     "ft_batch_group_info", "ft_batch_group_tuned_ms", "ft_batch_run", "ft_tc_dft64",
     "ft_plan_set_precision", "ft_plan_get_precision", "ft_plan_tc_errors", "ft_verify",
+    "ft_abs_mse_backward",
 )
 FT_PRECISION_FP32 = 0
 FT_PRECISION_BF16X3 = 1
@@ -126,6 +127,8 @@ def lib() -> ctypes.CDLL:
     L.ft_plan_tc_errors.restype = ci
     L.ft_verify.argtypes = [vp, vp, vp, vp, ci, ci, ci, cf, ci, vp, vp, vp, vp]
     L.ft_verify.restype = ci
+    L.ft_abs_mse_backward.argtypes = [vp, vp, vp, ci, cf, vp, vp, vp]
+    L.ft_abs_mse_backward.restype = ci
     for name in ("ft_plan_variant_count", "ft_plan_set_variant", "ft_plan_get_variant", "ft_batch_create",
                  "ft_batch_destroy", "ft_batch_layout", "ft_batch_group_count", "ft_batch_group_info",
                  "ft_batch_run"):
@@ -339,6 +342,24 @@ def ft_abs_mse_grad(plan: Plan, fmap, target, scale: float, loss=None, grad=None
     _check(lib().ft_abs_mse_grad(plan.handle, mp, tp, b, float(scale), _dev_ptr(loss, "float32", b, "loss"),
                                  gp, _stream_ptr(stream)), "ft_abs_mse_grad")
     return loss, (grad if grad is not False else None)
+
+
+def ft_abs_mse_backward(plan: Plan, fmap, target, scale: float, loss=None, grad_img=None, stream=None):
+    """The loss of ft_abs_mse_grad and its gradient with respect to the images
+    in one call (the map gradient is never stored).  Returns (loss, grad_img)."""
+    import torch
+    b = fmap.shape[0]
+    n = b * plan.Hp * plan.S
+    mp = _dev_ptr(fmap, "float32", n, "map")
+    tp = _dev_ptr(target, "float32", n, "target")
+    if loss is None:
+        loss = torch.empty(b, dtype=torch.float32, device=fmap.device)
+    if grad_img is None:
+        grad_img = torch.empty((b, plan.H, plan.W), dtype=torch.float32, device=fmap.device)
+    gp = _dev_ptr(grad_img, "float32", b * plan.H * plan.W, "grad_img")
+    _check(lib().ft_abs_mse_backward(plan.handle, mp, tp, b, float(scale), _dev_ptr(loss, "float32", b, "loss"),
+                                     gp, _stream_ptr(stream)), "ft_abs_mse_backward")
+    return loss, grad_img
 
 
 def ft_workspace_bytes(plan: Plan, batch: int) -> int:

@@ -90,3 +90,37 @@ def test_autograd_wrapper(torch):
         f.ft_backward(plan, dP, gx)
         torch.cuda.synchronize()
     assert _gpu.rel_l2(x.grad.cpu().numpy(), gx.cpu().numpy().astype(np.float64)) <= 1e-6
+
+
+@pytest.mark.parametrize("side,n,space,Hp", [(64, 3, "regular", 64), (512, 2, "regular", 512),
+                                             (128, 2, "inverse", 128), (96, 2, "regular", 216)])
+def test_fused_loss_backward_equals_the_two_calls(torch, side, n, space, Hp):
+    """ft_abs_mse_backward = ft_abs_mse_grad + ft_backward without storing the
+    map gradient: the losses agree to FP32 rounding, the image gradients to the
+    tolerance, and both are deterministic.  n_intercept 216 (no fixed-length
+    kernel) takes the fallback through the workspace."""
+    from paper_1904_09409_gb300 import funnel as f
+    imgs, _ = workload(side, n)
+    rng = np.random.default_rng(side + n)
+    with f.Plan(side, side, side, Hp, space=space) as plan:
+        x = torch.from_numpy(imgs).cuda()
+        P = torch.empty((n, plan.Hp, plan.S), dtype=torch.float32, device="cuda")
+        f.ft_forward(plan, x, P)
+        t = torch.from_numpy(rng.random((n, plan.Hp, plan.S)).astype(np.float32)).cuda()
+        loss_a, dP = f.ft_abs_mse_grad(plan, P, t, 2.0 / side)
+        gx_a = torch.empty_like(x)
+        f.ft_backward(plan, dP, gx_a)
+        loss_b, gx_b = f.ft_abs_mse_backward(plan, P, t, 2.0 / side)
+        loss_c, gx_c = f.ft_abs_mse_backward(plan, P, t, 2.0 / side)
+        torch.cuda.synchronize()
+    assert torch.equal(loss_b, loss_c) and torch.equal(gx_b, gx_c)
+    la, lb = loss_a.cpu().numpy().astype(np.float64), loss_b.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(la - lb) <= 2e-6 * la)
+    for i in range(n):
+        assert _gpu.rel_l2(gx_b[i].cpu().numpy(), gx_a[i].cpu().numpy().astype(np.float64)) <= 1e-6
+        # and against the FP64 adjoint of the oracle's own loss gradient of this map
+        _, dP_ref = oracle.map_loss_grad_ref(P[i].cpu().numpy().astype(np.float64),
+                                             t[i].cpu().numpy().astype(np.float64), side)
+        g_ref = oracle.adjoint_ref(dP_ref / n, side, side, "linear") if space == "regular" else None
+        if g_ref is not None:
+            assert _gpu.rel_l2(gx_b[i].cpu().numpy(), g_ref) <= TOL
