@@ -195,8 +195,6 @@ struct FastFft {
 
 // launchers of the fixed-length kernels (k_fast.cu); they return
 // cudaErrorNotSupported when N has no schedule
-// staging of the column kernels' inputs with cp.async needs 16-byte rows
-__host__ __device__ constexpr bool col_stage_ok(int ncols, int in_pitch) { return ncols % 4 == 0 && in_pitch % 4 == 0; }
 
 cudaError_t launch_col_r2c_fast(const float* in, int rows_in, int ncols, int in_pitch, size_t in_img,
                                 int row0, const FftLen& f, float2* out, int out_pitch, size_t out_img,

@@ -13,74 +13,23 @@
 //    rounding of the exact fraction).
 #include "fft_fast.cuh"
 
-// Staging the column kernel's image tile through shared memory measured slower
-// on GB300 than direct 8-byte loads into registers (60 vs 67 us for 32 images of
-// 1024^2), so it is compiled out; the C2R kernel keeps its staging.
-#define STAGE_R2C 0
-
+// The last pass of the column R2C and the split of each complex transform (two
+// real columns a + i b) into the two half spectra:
+//     A[l] = (Z[l] + conj Z[N-l]) / 2,  B[l] = (Z[l] - conj Z[N-l]) / (2 i),
+// scaled by end_scale (l = 0, N/2) or mid_scale, written as one float4 per row.
 template <int N>
-__global__ void __launch_bounds__(fs_T(N) * fs_Bcol(N))
-k_col_r2c_fast(const float* __restrict__ in, int rows_in, int ncols, int in_pitch, size_t in_img,
-               int row0, const float2* __restrict__ stw, float2* __restrict__ out, int out_pitch,
-               size_t out_img, float end_scale, float mid_scale) {
+__device__ __forceinline__ void r2c_finish(float2 (&v)[fs_E(N)], float2* sm, int t, int f, const float2* stw,
+                                           bool colok, float2* dst, int out_pitch, float end_scale,
+                                           float mid_scale) {
     constexpr int B = fs_Bcol(N), E = fs_E(N), T = N / E;
-    constexpr int R0 = fs_radix(N, 0), G0 = E / R0;
     constexpr int RL = fs_radix(N, fs_nst(N) - 1), GL = E / RL;
     using F = FastFft<N, -1, B>;
-    extern __shared__ float2 sm[];
-    const int f = threadIdx.x % B;
-    const int t = threadIdx.x / B;
-    const int c = blockIdx.x * 2 * B + 2 * f;
-    const bool colok = c < ncols;
-    const float* src = in + (size_t)blockIdx.y * in_img + c;
-
-    float2 v[E];
-    if (STAGE_R2C && B >= 2 && col_stage_ok(ncols, in_pitch)) {
-        // stage the N x 2B tile (zero rows outside the image) with 16-byte async
-        // copies, all in flight at once, then read the first pass from shared memory
-        constexpr int CPR = B >= 2 ? B / 2 : 1;         // 16-byte chunks per tile row
-        float* stg = reinterpret_cast<float*>(sm);      // [N][2B]
-        const int cb = blockIdx.x * 2 * B;
-        const float* img0 = in + (size_t)blockIdx.y * in_img;
-        for (int idx = threadIdx.x; idx < N * CPR; idx += blockDim.x) {
-            const int n = idx / CPR;
-            const int j = idx - n * CPR;
-            const int row = n - row0;
-            const int col = cb + 4 * j;
-            float* dst = stg + n * 2 * B + 4 * j;
-            if (row >= 0 && row < rows_in && col < ncols)
-                cp_async16(dst, img0 + (size_t)row * in_pitch + col);
-            else
-                *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        cp_async_wait_all();
-        __syncthreads();
-#pragma unroll
-        for (int m = 0; m < G0; ++m)
-#pragma unroll
-            for (int q = 0; q < R0; ++q)
-                v[m * R0 + q] = *reinterpret_cast<const float2*>(stg + F::template in_pos<0>(t, m, q) * 2 * B + 2 * f);
-        __syncthreads();
-    } else {
-#pragma unroll
-        for (int m = 0; m < G0; ++m)
-#pragma unroll
-            for (int q = 0; q < R0; ++q) {
-                const int row = F::template in_pos<0>(t, m, q) - row0;
-                float2 x = make_float2(0.f, 0.f);
-                if (colok && row >= 0 && row < rows_in)
-                    x = __ldg(reinterpret_cast<const float2*>(src + (size_t)row * in_pitch));
-                v[m * R0 + q] = x;
-            }
-    }
     F::template run<0>(v, sm, t, f, stw);
 #pragma unroll
     for (int m = 0; m < GL; ++m)
 #pragma unroll
         for (int q = 0; q < RL; ++q) sm[spos(F::out_pos(t, m, q)) * B + f] = v[m * RL + q];
     __syncthreads();
-
-    float2* dst = out + (size_t)blockIdx.y * out_img + c;
     if (!colok) return;
     for (int l = t; l <= N / 2; l += T) {
         const float2 zl = sm[spos(l) * B + f];
@@ -93,6 +42,37 @@ k_col_r2c_fast(const float* __restrict__ in, int rows_in, int ncols, int in_pitc
         o.w = -0.5f * s * (zl.x - zm.x);
         *reinterpret_cast<float4*>(dst + (size_t)l * out_pitch) = o;
     }
+}
+
+// The column kernel reads its first pass straight from global memory (8-byte
+// loads of its column pair): staging the image tile through shared memory first
+// measured slower on GB300 (67 vs 60 us for 32 images of 1024^2).
+template <int N>
+__global__ void __launch_bounds__(fs_T(N) * fs_Bcol(N))
+k_col_r2c_fast(const float* __restrict__ in, int rows_in, int ncols, int in_pitch, size_t in_img,
+               int row0, const float2* __restrict__ stw, float2* __restrict__ out, int out_pitch,
+               size_t out_img, float end_scale, float mid_scale) {
+    constexpr int B = fs_Bcol(N), E = fs_E(N);
+    constexpr int R0 = fs_radix(N, 0), G0 = E / R0;
+    using F = FastFft<N, -1, B>;
+    extern __shared__ float2 sm[];
+    const int f = threadIdx.x % B;
+    const int t = threadIdx.x / B;
+    const int c = blockIdx.x * 2 * B + 2 * f;
+    const bool colok = c < ncols;
+    const float* src = in + (size_t)blockIdx.y * in_img + c;
+
+    float2 v[E];
+#pragma unroll
+    for (int m = 0; m < G0; ++m)
+#pragma unroll
+        for (int q = 0; q < R0; ++q) {
+            const int row = F::template in_pos<0>(t, m, q) - row0;
+            float2 x = make_float2(0.f, 0.f);
+            if (colok && row >= 0 && row < rows_in) x = __ldg(reinterpret_cast<const float2*>(src + (size_t)row * in_pitch));
+            v[m * R0 + q] = x;
+        }
+    r2c_finish<N>(v, sm, t, f, stw, colok, out + (size_t)blockIdx.y * out_img + c, out_pitch, end_scale, mid_scale);
 }
 
 template <int N>
@@ -109,7 +89,6 @@ k_col_c2r_fast(const float2* __restrict__ in, int ncols, int in_pitch, size_t in
     const int t = threadIdx.x / B;
     const int c = blockIdx.x * 2 * B + 2 * f;
     const bool colok = c < ncols;
-    const float2* src = in + (size_t)blockIdx.y * in_img + c;
 
     // stage the Hermitian half (rows 0 .. N/2, 2B complex each) with 16-byte async
     // copies; every row is read once and serves both n and N - n
@@ -170,15 +149,14 @@ k_col_c2r_fast(const float2* __restrict__ in, int ncols, int in_pitch, size_t in
 // gradient of k_loss.cu), while every thread adds r^2 of its samples (FP32,
 // compensated) and the block writes one partial of the image's loss.  Each map
 // cell is loaded by exactly one thread, so the partials of an image's blocks
-// add up to its sum of r^2.  Everything after the load is k_col_r2c_fast.
+// add up to its sum of r^2.  Everything after the load is r2c_finish.
 template <int N>
 __global__ void __launch_bounds__(fs_T(N) * fs_Bcol(N))
 k_col_r2c_loss_fast(const float* __restrict__ map, const float* __restrict__ target, int ncols, size_t img_cells,
                     const float2* __restrict__ stw, float2* __restrict__ out, int out_pitch, size_t out_img,
                     float end_scale, float mid_scale, float scale, float gscale, float* __restrict__ partial) {
-    constexpr int B = fs_Bcol(N), E = fs_E(N), T = N / E;
+    constexpr int B = fs_Bcol(N), E = fs_E(N);
     constexpr int R0 = fs_radix(N, 0), G0 = E / R0;
-    constexpr int RL = fs_radix(N, fs_nst(N) - 1), GL = E / RL;
     using F = FastFft<N, -1, B>;
     extern __shared__ float2 sm[];
     __shared__ float red[fs_T(N) * fs_Bcol(N)];
@@ -222,26 +200,7 @@ k_col_r2c_loss_fast(const float* __restrict__ map, const float* __restrict__ tar
         __syncthreads();
     }
     if (threadIdx.x == 0) partial[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
-    F::template run<0>(v, sm, t, f, stw);
-#pragma unroll
-    for (int m = 0; m < GL; ++m)
-#pragma unroll
-        for (int q = 0; q < RL; ++q) sm[spos(F::out_pos(t, m, q)) * B + f] = v[m * RL + q];
-    __syncthreads();
-
-    float2* dst = out + (size_t)blockIdx.y * out_img + c;
-    if (!colok) return;
-    for (int l = t; l <= N / 2; l += T) {
-        const float2 zl = sm[spos(l) * B + f];
-        const float2 zm = sm[spos(l == 0 ? 0 : N - l) * B + f];
-        const float s = (l == 0 || l == N / 2) ? end_scale : mid_scale;
-        float4 o;
-        o.x = 0.5f * s * (zl.x + zm.x);
-        o.y = 0.5f * s * (zl.y - zm.y);
-        o.z = 0.5f * s * (zl.y + zm.y);
-        o.w = -0.5f * s * (zl.x - zm.x);
-        *reinterpret_cast<float4*>(dst + (size_t)l * out_pitch) = o;
-    }
+    r2c_finish<N>(v, sm, t, f, stw, colok, out + (size_t)blockIdx.y * out_img + c, out_pitch, end_scale, mid_scale);
 }
 
 // row pitch (complex) of the staged spectrum rows: W + 2 keeps 16-byte
