@@ -304,14 +304,15 @@ cudaError_t launch_tc_dft64(const float2* x, float2* y, int nvec, int sign, int 
 cudaError_t tc_prepare();
 // The split-precision four-step DFT of length 4096 (k_tc.cu): steps 2-3 for
 // n_slope = 4096, and steps 1 and 4 of the forward path for n_intercept = 4096
-// (same layouts as launch_col_r2c with unit scales and launch_col_c2r with
-// mid scale 1 and out scale 1/H')
+// (launch_col_r2c with unit scales, but the image column-major [batch][W][H];
+// launch_col_c2r with mid scale 1 and out scale 1/H', but the map written
+// column-major [batch][S][H'])
 // (prec: FT_PRECISION_BF16X3, _FP16X3 or _BF16X6)
 cudaError_t launch_nvmt_rows_tc4096(float2* ws, int W, int Hp, int L, int interp, int prec, unsigned* err, int batch,
                                     cudaStream_t st);
-cudaError_t launch_col_r2c_tc4096(const float* img, int H, int W, int row0, float2* ws, int L, int S, int prec,
+cudaError_t launch_col_r2c_tc4096(const float* img_cm, int H, int W, int row0, float2* ws, int L, int S, int prec,
                                   unsigned* err, int batch, cudaStream_t st);
-cudaError_t launch_col_c2r_tc4096(const float2* ws, int L, int S, float* map, int prec, unsigned* err, int batch,
+cudaError_t launch_col_c2r_tc4096(const float2* ws, int L, int S, float* map_cm, int prec, unsigned* err, int batch,
                                   cudaStream_t st);
 
 // line verification of Sec. 4.5 (k_verify.cu): image element (v, u) of the

@@ -343,23 +343,26 @@ __device__ __forceinline__ void issue_split_gemm_k64(uint32_t tmem_d, uint32_t a
 //   TCM_ROWS_*  steps 2-3: NVMT gather (linear / Keys cubic) of a spectrum row,
 //               sign +1, centred in x' and m, in place on the row;
 //   TCM_R2C     step 1: two real image columns x, x+1 (zero-expanded rows) as one
-//               complex sequence, sign -1, split into their two half spectra;
+//               complex sequence, sign -1, split into their two half spectra; the
+//               image comes column-major ([batch][W][H], a transposed copy), so a
+//               column pair is two contiguous rows;
 //   TCM_C2R     step 4: the Hermitian halves of map columns s, s+1 as one complex
 //               spectrum, sign +1, scaled by 1/H', real and imaginary parts to
-//               the two map columns.
+//               the two map columns, written column-major ([batch][S][H'], to be
+//               transposed into the map).
 enum { TCM_ROWS_LINEAR = 0, TCM_ROWS_CUBIC = 1, TCM_R2C = 2, TCM_C2R = 3 };
 
 struct TcArgs {
     float2* ws;             // spectrum / G rows [batch][L][S]
-    const float* img;       // TCM_R2C input [batch][H][W]
-    float* map;             // TCM_C2R output [batch][H'][S]
+    const float* img;       // TCM_R2C input, column-major [batch][W][H]
+    float* map;             // TCM_C2R output, column-major [batch][S][H']
     int W, H, Hp, L, S, row0, total;
     unsigned* err;
 };
 
-__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
     const unsigned a = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(a), "l"(gmem_src) : "memory");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(a), "l"(gmem_src) : "memory");
 }
 
 template <int PREC, int MODE>
@@ -500,25 +503,46 @@ k_tc4096(TcArgs a) {
         } else if constexpr (MODE == TCM_R2C) {
             img = job / (a.W / 2);
             col = 2 * (job - img * (a.W / 2));
-            const float* src = a.img + (size_t)img * a.H * a.W + col;
-            for (int y = gt; y < N; y += T) {
-                const int rr = y - a.row0;
-                if (rr >= 0 && rr < a.H) cp_async8(zin + y, src + (size_t)rr * a.W);
-                else zin[y] = make_float2(0.f, 0.f);
+            float* za = reinterpret_cast<float*>(zin);  // column col, zero-expanded to N rows
+            float* zb = za + N;                         // column col + 1
+            const float* ra = a.img + ((size_t)img * a.W + col) * a.H;
+            const float* rb = ra + a.H;
+            if (((a.row0 | a.H) & 3) == 0) {            // 16-byte copies
+                for (int i = gt; i < N / 4; i += T) {
+                    const int y = 4 * i, rr = y - a.row0;
+                    if (rr >= 0 && rr < a.H) {
+                        cp_async16(za + y, ra + rr);
+                        cp_async16(zb + y, rb + rr);
+                    } else {
+                        *reinterpret_cast<float4*>(za + y) = make_float4(0.f, 0.f, 0.f, 0.f);
+                        *reinterpret_cast<float4*>(zb + y) = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+            } else {
+                for (int y = gt; y < N; y += T) {
+                    const int rr = y - a.row0;
+                    if (rr >= 0 && rr < a.H) {
+                        cp_async4(za + y, ra + rr);
+                        cp_async4(zb + y, rb + rr);
+                    } else {
+                        za[y] = 0.f;
+                        zb[y] = 0.f;
+                    }
+                }
             }
             cp_async_wait_all();
+            group_sync(bar);
             // the column means (a constant shift changes only Z[0]; it is added back
             // below), so that the split operands carry the columns' variation
             // rather than their mean level
             float sa = 0.f, sb = 0.f;
             for (int y = gt; y < N; y += T) {
-                sa += zin[y].x;
-                sb += zin[y].y;
+                sa += za[y];
+                sb += zb[y];
             }
             const float2 tot = group_sum2(make_float2(sa, sb));
             mean = make_float2(tot.x * (1.f / N), tot.y * (1.f / N));
-            for (int y = gt; y < N; y += T)
-                mx = fmaxf(mx, fmaxf(fabsf(zin[y].x - mean.x), fabsf(zin[y].y - mean.y)));
+            for (int y = gt; y < N; y += T) mx = fmaxf(mx, fmaxf(fabsf(za[y] - mean.x), fabsf(zb[y] - mean.y)));
         } else {
             img = job / (a.S / 2);
             col = 2 * (job - img * (a.S / 2));
@@ -594,7 +618,8 @@ k_tc4096(TcArgs a) {
                     const int n = rr + 64 * (8 * kg + j);
                     float2 z;
                     if constexpr (MODE == TCM_R2C) {
-                        z = make_float2(zin[n].x - mean.x, zin[n].y - mean.y);
+                        const float* za = reinterpret_cast<const float*>(zin);
+                        z = make_float2(za[n] - mean.x, za[N + n] - mean.y);
                     } else {
                         const int q = n <= N / 2 ? n : N - n;
                         if (q == N / 2) {
@@ -660,11 +685,13 @@ k_tc4096(TcArgs a) {
                     make_float4(0.5f * (zl.x + zm.x), 0.5f * (zl.y - zm.y), 0.5f * (zl.y + zm.y), -0.5f * (zl.x - zm.x));
             }
         } else {
-            float* dst = a.map + (size_t)img * a.Hp * a.S + col;
+            float* da = a.map + ((size_t)img * a.S + col) * a.Hp;    // column-major: map column col
+            float* db = da + a.Hp;                                    // and col + 1
             const float sc = un / (float)a.Hp;
             for (int t = gt; t < N; t += T) {
                 const float2 y = y_at(t);
-                *reinterpret_cast<float2*>(dst + (size_t)t * a.S) = make_float2(y.x * sc, y.y * sc);
+                da[t] = y.x * sc;
+                db[t] = y.y * sc;
             }
         }
         group_sync(bar);                                // stage is the next job's input
@@ -710,20 +737,20 @@ cudaError_t launch_nvmt_rows_tc4096(float2* ws, int W, int Hp, int L, int interp
                                       : go_tc_prec<TCM_ROWS_CUBIC>(prec, a, st);
 }
 
-cudaError_t launch_col_r2c_tc4096(const float* img, int H, int W, int row0, float2* ws, int L, int S, int prec,
+cudaError_t launch_col_r2c_tc4096(const float* img_cm, int H, int W, int row0, float2* ws, int L, int S, int prec,
                                   unsigned* err, int batch, cudaStream_t st) {
     if (H <= 0 || H > TCR_S || W <= 0 || (W & 1) || L != TCR_S / 2 + 1 || S < W) return cudaErrorInvalidValue;
     cudaError_t e = ensure_w64();
     if (e != cudaSuccess) return e;
-    TcArgs a{ws, img, nullptr, W, H, TCR_S, L, S, row0, batch * (W / 2), err};
+    TcArgs a{ws, img_cm, nullptr, W, H, TCR_S, L, S, row0, batch * (W / 2), err};
     return go_tc_prec<TCM_R2C>(prec, a, st);
 }
 
-cudaError_t launch_col_c2r_tc4096(const float2* ws, int L, int S, float* map, int prec, unsigned* err, int batch,
+cudaError_t launch_col_c2r_tc4096(const float2* ws, int L, int S, float* map_cm, int prec, unsigned* err, int batch,
                                   cudaStream_t st) {
     if (L != TCR_S / 2 + 1 || S <= 0 || (S & 1)) return cudaErrorInvalidValue;
     cudaError_t e = ensure_w64();
     if (e != cudaSuccess) return e;
-    TcArgs a{const_cast<float2*>(ws), nullptr, map, 0, 0, TCR_S, L, S, 0, batch * (S / 2), err};
+    TcArgs a{const_cast<float2*>(ws), nullptr, map_cm, 0, 0, TCR_S, L, S, 0, batch * (S / 2), err};
     return go_tc_prec<TCM_C2R>(prec, a, st);
 }

@@ -496,17 +496,36 @@ int ft_peaks_launches(ft_plan p, int batch) {
     return 2 * (use_lanes(p, batch) ? FT_LANES : 1);
 }
 
-static ft_status forward_part(ft_plan p, const float* src, float* d_map, float2* ws, int nb, cudaStream_t st) {
-    // split precision: the length-4096 column transforms on the tensor cores too
-    const bool tc_cols = p->precision != FT_PRECISION_FP32 && p->Hp == 4096;
+// split precision: the length-4096 column transforms on the tensor cores too,
+// through a column-major copy (cm) so that their column pairs are contiguous rows
+static bool tc_columns(ft_plan p) { return p->precision != FT_PRECISION_FP32 && p->Hp == 4096; }
+static size_t cm_elems(ft_plan p) {
+    const size_t a = (size_t)p->H * p->W, b = (size_t)p->Hp * p->S;
+    return a > b ? a : b;
+}
+
+static cudaError_t tc_r2c(ft_plan p, const float* src, float2* ws, float* cm, int nb, cudaStream_t st) {
+    cudaError_t e = launch_transpose(src, cm, p->H, p->W, nb, st);
+    if (e != cudaSuccess) return e;
+    return launch_col_r2c_tc4096(cm, p->H, p->W, p->top, ws, p->L, p->S, p->precision, p->d_tc_err, nb, st);
+}
+
+static cudaError_t tc_c2r(ft_plan p, const float2* ws, float* d_map, float* cm, int nb, cudaStream_t st) {
+    cudaError_t e = launch_col_c2r_tc4096(ws, p->L, p->S, cm, p->precision, p->d_tc_err, nb, st);
+    if (e != cudaSuccess) return e;
+    return launch_transpose(cm, d_map, p->S, p->Hp, nb, st);
+}
+
+static ft_status forward_part(ft_plan p, const float* src, float* d_map, float2* ws, float* cm, int nb,
+                              cudaStream_t st) {
+    const bool tc_cols = tc_columns(p);
     FT_LAUNCH(p, FT_KERNEL_COL_R2C, st,
-              tc_cols ? launch_col_r2c_tc4096(src, p->H, p->W, p->top, ws, p->L, p->S, p->precision, p->d_tc_err, nb,
-                                              st)
+              tc_cols ? tc_r2c(p, src, ws, cm, nb, st)
                       : col_r2c(p, src, p->H, p->W, p->W, (size_t)p->H * p->W, p->top, ws, 1.f, 1.f, nb, st),
               "step 1 (column R2C)");
     FT_LAUNCH(p, FT_KERNEL_NVMT_ROWS, st, nvmt_rows(p, ws, nb, st), "steps 2-3 (NVMT + row FFT)");
     FT_LAUNCH(p, FT_KERNEL_COL_C2R, st,
-              tc_cols ? launch_col_c2r_tc4096(ws, p->L, p->S, d_map, p->precision, p->d_tc_err, nb, st)
+              tc_cols ? tc_c2r(p, ws, d_map, cm, nb, st)
                       : col_c2r(p, ws, p->S, 1.f, d_map, 0, p->Hp, p->S, (size_t)p->Hp * p->S, 1.f / (float)p->Hp,
                                 nb, st),
               "step 4 (column C2R)");
@@ -517,22 +536,25 @@ ft_status ft_forward(ft_plan p, const float* d_img, float* d_map, int batch, voi
     if (!p || batch < 0 || batch > 65535) return FT_ERR_INVALID_ARG;
     if (batch == 0) return FT_OK;
     if (!d_img || !d_map || ((uintptr_t)d_img & 7) || ((uintptr_t)d_map & 7)) return FT_ERR_INVALID_ARG;
-    ft_status s = ensure(&p->d_ws, &p->ws_bytes, aux_off(p, batch), "cudaMalloc(workspace)");
+    // the column-major copies of the split-precision path live in the aux region
+    const size_t cm_bytes = tc_columns(p) ? (size_t)batch * cm_elems(p) * sizeof(float) : 0;
+    ft_status s = ensure(&p->d_ws, &p->ws_bytes, aux_off(p, batch) + cm_bytes, "cudaMalloc(workspace)");
     if (s != FT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     float2* ws = (float2*)p->d_ws;
+    float* cm = (float*)((char*)p->d_ws + aux_off(p, batch));
     const float* src = d_img;
     if (p->space == FT_SPACE_INVERSE) {
         float* tp = (float*)((char*)p->d_ws + tposed_off(p, batch));
         FT_CUDA(launch_transpose(d_img, tp, p->img_H, p->img_W, batch, st), "transpose (inverse space)");
         src = tp;
     }
-    if (!use_lanes(p, batch)) return forward_part(p, src, d_map, ws, batch, st);
+    if (!use_lanes(p, batch)) return forward_part(p, src, d_map, ws, cm, batch, st);
     if ((s = lanes_fork(p, st)) != FT_OK) return s;
     for (int j = 0; j < FT_LANES; ++j) {
         const int b0 = batch * j / FT_LANES, b1 = batch * (j + 1) / FT_LANES;
         s = forward_part(p, src + (size_t)b0 * p->H * p->W, d_map + (size_t)b0 * p->Hp * p->S,
-                         ws + (size_t)b0 * p->L * p->S, b1 - b0, p->lane_streams[j]);
+                         ws + (size_t)b0 * p->L * p->S, cm + (size_t)b0 * cm_elems(p), b1 - b0, p->lane_streams[j]);
         if (s != FT_OK) return s;
     }
     return lanes_join(p, st);
