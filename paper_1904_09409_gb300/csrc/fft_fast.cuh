@@ -57,9 +57,11 @@ __host__ __device__ constexpr int fs_twoff(int N, int s) {
     return o;
 }
 __host__ __device__ constexpr int fs_twsize(int N) { return fs_twoff(N, fs_nst(N)); }
-// transforms per block for the column kernels (512 threads) and the row kernels (256)
+// transforms per block for the column kernels (512 threads; for N >= 4096,
+// 1024 threads so that a block still reads 4 column pairs = 32-byte row
+// segments) and the row kernels (256)
 __host__ __device__ constexpr int fs_clampB(int v, int hi) { return v < 1 ? 1 : (v > hi ? hi : v); }
-__host__ __device__ constexpr int fs_Bcol(int N) { return fs_clampB(512 / fs_T(N), 32); }
+__host__ __device__ constexpr int fs_Bcol(int N) { return fs_T(N) >= 256 ? 1024 / fs_T(N) : fs_clampB(512 / fs_T(N), 32); }
 __host__ __device__ constexpr int fs_Brow(int N) { return fs_clampB(256 / fs_T(N), 16); }
 // padded shared-memory slot of sample n (one spare slot every 16 samples
 // spreads the strided stores of the first pass over the banks)
