@@ -52,18 +52,21 @@ def band_profile(img: np.ndarray, t: int, s: int, n_slope: int, n_intercept: int
     if inverse:
         a = a.T
     H, W = a.shape
-    slope, offset = band_geometry(t, s, n_slope, n_intercept, H, W)
+    m = s - n_slope // 2
+    top = (n_intercept - H) // 2
     h = half_width
     sums = np.zeros(2 * h + 1)
     counts = np.zeros(2 * h + 1, dtype=np.int64)
     for u in range(W):
-        vc = slope * u + offset
+        # v_c(u) = (2m/S)(u - W/2) + n + H'/2 - top = m (2u - W) / S + t - top,
+        # split exactly into an integer floor and a fraction
+        num = m * (2 * u - W)
+        q = num // n_slope
+        f = (num - q * n_slope) / n_slope
         for j, d in enumerate(range(-h, h + 1)):
-            v = vc + d
-            v0 = int(np.floor(v))
+            v0 = q + t - top + d
             if v0 < 0 or v0 + 1 > H - 1:
                 continue
-            f = v - v0
             sums[j] += (1.0 - f) * a[v0, u] + f * a[v0 + 1, u]
             counts[j] += 1
     prof = np.where(counts > 0, sums / np.maximum(counts, 1), 0.0)
