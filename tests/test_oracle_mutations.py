@@ -85,3 +85,87 @@ def test_planted_step4_weight_is_caught(monkeypatch):
 
     monkeypatch.setattr(fr, "inverse_fourier_omega2", halved)
     assert not _brute_force_agrees()
+
+
+# ------------------------------------------------- line verification (Sec. 4.5)
+import inspect                                                     # noqa: E402
+import json                                                        # noqa: E402
+import os                                                          # noqa: E402
+
+from oracle import verification as vr                              # noqa: E402
+
+
+def _mutant(old, new):
+    """band_profile with one line of its source replaced."""
+    src = inspect.getsource(vr.band_profile)
+    assert old in src, old
+    ns = dict(vr.__dict__)
+    exec(src.replace(old, new), ns)
+    return ns["band_profile"]
+
+
+def _verification_pins_hold(band_profile):
+    """The closed forms of test_oracle_verify and the Fig. 9 example, for a
+    given band_profile."""
+    # horizontal ridge on row 11 of a 30-row image in a 64-row frame
+    img = np.zeros((30, 48))
+    img[11, :] = 2.5
+    prof, length = band_profile(img, 11 + 17, 24, 48, 64, 3)
+    if not (np.allclose(prof, [0, 0, 0, 2.5, 0, 0, 0]) and length == 48):
+        return False
+    # step edge: dark rows above, bright from row 16
+    img = np.zeros((32, 32))
+    img[16:, :] = 0.8
+    prof, _ = band_profile(img, 15, 16, 32, 32, 3)
+    if not np.allclose(prof, [0, 0, 0, 0, 0.8, 0.8, 0.8]):
+        return False
+    # linear ramp: p[d] is the mean centre row + d (interpolation and slope)
+    img = np.repeat(np.arange(50, dtype=np.float64)[:, None], 40, axis=1)
+    prof, _ = band_profile(img, 31, 27, 40, 64, 2)
+    slope, offset = vr.band_geometry(31, 27, 40, 64, 50, 40)
+    for j, d in enumerate(range(-2, 3)):
+        vs = [slope * u + offset + d for u in range(40)]
+        vs = [v for v in vs if 0 <= np.floor(v) and np.floor(v) + 1 <= 49]
+        if abs(prof[j] - np.mean(vs)) > 1e-9:
+            return False
+    # a line leaving the image at the bottom: the centre line counts only
+    # columns whose two taps are both inside
+    img = np.repeat(np.arange(50, dtype=np.float64)[:, None], 40, axis=1)
+    t, s = 32 + 13 + 7, 20 + 8                       # k = 0.4, centre row 0.4 (u - 20) + 45
+    _, length = band_profile(img, t, s, 40, 64, 1)
+    slope, offset = vr.band_geometry(t, s, 40, 64, 50, 40)
+    if length != sum(1 for u in range(40) if 0 <= np.floor(slope * u + offset) <= 48):
+        return False
+    # Fig. 9: the inverse-space peak's line is in the image
+    with open(os.path.join(os.path.dirname(__file__), "golden", "fig9_wrapped_peak.json")) as f:
+        g = json.load(f)
+    W, H = g["width_M"], g["height_N"]
+    img = ridge_image(H, W, g["expanded_length"], [(g["slope_k"], float(g["regular_peak_mn"][1]))])
+    m_i, n_i = g["inverse_peak_mn"]
+    prof, _ = band_profile(img, m_i + (W + H) // 2, n_i + H // 2, H, W + H, 2, inverse=True)
+    return vr.contrast(prof) > 0.5 and int(np.argmax(prof)) == 2
+
+
+def test_unmutated_verification_passes():
+    assert _verification_pins_hold(vr.band_profile)
+
+
+@pytest.mark.parametrize("name,old,new", [
+    ("slope sign", "m = s - n_slope // 2", "m = n_slope // 2 - s"),
+    ("expansion offset dropped", "top = (n_intercept - H) // 2", "top = 0"),
+    ("nearest row instead of interpolation", "f = (num - q * n_slope) / n_slope", "f = 0.0"),
+    ("inverse space not transposed", "        a = a.T", "        a = a"),
+    ("band offsets reversed", "v0 = q + t - top + d", "v0 = q + t - top - d"),
+    ("samples outside the image counted", "if v0 < 0 or v0 + 1 > H - 1:", "if v0 < 0 or v0 > H - 1:"),
+])
+def test_planted_verification_mistake_is_caught(name, old, new):
+    if name == "samples outside the image counted":
+        # the mutant reads the row below the image: clamp that tap so it can run
+        src = inspect.getsource(vr.band_profile).replace(old, new).replace(
+            "sums[j] += (1.0 - f) * a[v0, u] + f * a[v0 + 1, u]",
+            "sums[j] += (1.0 - f) * a[v0, u] + f * a[min(v0 + 1, H - 1), u]")
+        ns = dict(vr.__dict__)
+        exec(src, ns)
+        assert not _verification_pins_hold(ns["band_profile"]), name
+        return
+    assert not _verification_pins_hold(_mutant(old, new)), name

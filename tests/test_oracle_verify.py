@@ -71,3 +71,18 @@ def test_fig9_wrapping_peak_is_rejected_and_inverse_peak_verified():
     assert not ok_r and vr.contrast(prof_r) < 0.05       # the line of slope -0.73 is not in the image
     assert ok_i and vr.contrast(prof_i) > 0.5            # the line of slope 3.27 is
     assert int(np.argmax(prof_i)) == 2 and len_i > 300   # centred on the band, along most of the rows
+
+
+def test_line_leaving_the_image_counts_inside_samples_only():
+    """Centre row 0.4 (u - 20) + 45 of a 50-row image (in a 64-row frame, top 7):
+    it leaves the image at the bottom, and only columns whose two taps are both
+    inside count."""
+    H, W, Hp, S = 50, 40, 64, 40
+    img = np.repeat(np.arange(H, dtype=np.float64)[:, None], W, axis=1)
+    t, s = 32 + 13 + 7, 20 + 8
+    slope, offset = vr.band_geometry(t, s, S, Hp, H, W)
+    assert abs(slope - 0.4) < 1e-15 and abs(offset - 37.0) < 1e-12
+    prof, length = vr.band_profile(img, t, s, S, Hp, 1)
+    inside = [u for u in range(W) if 0 <= np.floor(slope * u + offset) <= H - 2]
+    assert length == len(inside) and 0 < length < W
+    assert abs(prof[1] - np.mean([slope * u + offset for u in inside])) < 1e-9
