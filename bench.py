@@ -3,8 +3,9 @@
 
 Workload: 64 synthetic 1024 x 1024 FP32 images per GPU (1-20 ridge/step lines,
 occluders, noise), map 1024 x 1024 (n_slope = W, n_intercept = H), top-32
-peaks per image.  One step = ft_forward (Sec. 3.1 steps 1-4) + ft_peaks
-(Sec. 4.4) over the resident batch.  Metric: megapixels (input pixels) per
+peaks per image.  One step = ft_detect over the resident batch: Sec. 3.1
+steps 1-4 (step 4 also writes the maximum of |P| per tile) and the peak
+detection of Sec. 4.4, which reads only the tiles that can hold a top-32 peak.  Metric: megapixels (input pixels) per
 second, whole job.  Inputs (268 MB) and maps (268 MB) exceed the 129 MB L2.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -132,14 +133,21 @@ def measured_peaks():
 
 def kernel_bytes(name: str, H: int, W: int, S: int, Hp: int, K: int) -> float:
     """Algorithmic DRAM bytes per image of each kernel (compulsory reads and
-    writes of its own inputs and outputs)."""
+    writes of its own inputs and outputs).  The peak pass from tile maxima reads
+    the tile maxima and the cells of the tiles it tests, at least the first
+    R = ceil(K / 32) * 32 tiles (more when its bound needs them)."""
     L = Hp // 2 + 1
     ntiles = ((Hp + 31) // 32) * ((S + 63) // 64)
     kt = min(K, 512)
+    # tiles of step 4's maxima at H' = 1024: 64 rows x 16 columns
+    c2r_tiles = (Hp // 64) * ((S + 15) // 16)
+    R = min(c2r_tiles, (K + 31) // 32 * 32)
     return {
         "k_col_r2c": 4.0 * H * W + 8.0 * L * W,          # image in, half spectrum out
         "k_nvmt_rows": 8.0 * L * W + 8.0 * L * S,        # spectrum rows in, G rows out
-        "k_col_c2r": 8.0 * L * S + 4.0 * Hp * S,         # G in, map out
+        "k_col_c2r": 8.0 * L * S + 4.0 * Hp * S + 4.0 * c2r_tiles,   # G in, map and tile maxima out
+        "k_peak_sparse": 4.0 * c2r_tiles + 4.0 * R * 64 * 16 + 20.0 * K + 4.0,
+        "k_tile_max": 4.0 * Hp * S + 4.0 * ((Hp + 31) // 32) * ((S + 31) // 32),
         "k_peak_tiles": 4.0 * Hp * S + 8.0 * ntiles * kt,  # map in, tile keys out
         "k_peak_select": 8.0 * ntiles * kt + 20.0 * K + 4.0,
     }.get(name, 0.0)
@@ -277,8 +285,7 @@ def time_precision(f, imgs, steps, stream, dev):
         cn = torch.empty(B, dtype=torch.int32, device=dev)
 
         def step():
-            f.ft_forward(plan, x, m, stream=stream)
-            f.ft_peaks(plan, m, K, out=pk, count=cn, stream=stream)
+            f.ft_detect(plan, x, m, K, out=pk, count=cn, stream=stream)
 
         for _ in range(3):
             step()
@@ -313,7 +320,7 @@ def time_precision(f, imgs, steps, stream, dev):
     del maps, x
     torch.cuda.empty_cache()
     return {"workload": "8 x 4096^2 images, 100 lines each (mixed edge types, noise 0.2), n_slope = "
-                        "n_intercept = 4096, linear NVMT: ft_forward + top-100 peaks; the three length-4096 "
+                        "n_intercept = 4096, linear NVMT: ft_detect with top-100 peaks; the three length-4096 "
                         "transforms (steps 1, 3, 4) in FP32 (FFT) or as split-precision four-step DFTs on "
                         "the tensor cores",
             "variants": out}
@@ -458,8 +465,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        f.ft_forward(plan, x, m, stream=stream)
-        f.ft_peaks(plan, m, TOP_K, out=pk, count=cnt, stream=stream)
+        f.ft_detect(plan, x, m, TOP_K, out=pk, count=cnt, stream=stream)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -594,14 +600,12 @@ def run_extras(f, args, plan, imgs, lines, x, stream, dev, rank, ws, vl_imgs, vl
     pk = torch.empty(BATCH * TOP_K * f.PEAK_DTYPE.itemsize, dtype=torch.uint8, device=dev)
     cn = torch.empty(BATCH, dtype=torch.int32, device=dev)
     for _ in range(3):
-        f.ft_forward(fplan, x, mf, stream=stream)
-        f.ft_peaks(fplan, mf, TOP_K, out=pk, count=cn, stream=stream)
+        f.ft_detect(fplan, x, mf, TOP_K, out=pk, count=cn, stream=stream)
     fo_steps = max(3, min(args.steps, 50))
     q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     q0.record(stream)
     for _ in range(fo_steps):
-        f.ft_forward(fplan, x, mf, stream=stream)
-        f.ft_peaks(fplan, mf, TOP_K, out=pk, count=cn, stream=stream)
+        f.ft_detect(fplan, x, mf, TOP_K, out=pk, count=cn, stream=stream)
     q1.record(stream)
     torch.cuda.synchronize(dev)
     fo_ms = replicas.max_over_ranks(q0.elapsed_time(q1) / fo_steps, dev)
@@ -612,8 +616,7 @@ def run_extras(f, args, plan, imgs, lines, x, stream, dev, rank, ws, vl_imgs, vl
     pk_b = torch.empty(BATCH * TOP_K * f.PEAK_DTYPE.itemsize, dtype=torch.uint8, device=dev)
     cn_b = torch.empty(BATCH, dtype=torch.int32, device=dev)
     mv = torch.empty((BATCH, SIDE, SIDE), dtype=torch.float32, device=dev)
-    f.ft_forward(plan, x, mv, stream=stream)
-    f.ft_peaks(plan, mv, TOP_K, out=pk_b, count=cn_b, stream=stream)
+    f.ft_detect(plan, x, mv, TOP_K, out=pk_b, count=cn_b, stream=stream)
     for _ in range(3):
         f.ft_verify(plan, x, pk_b, cn_b, TOP_K, 2, 0.05, 64, stream=stream)
     v_steps = max(3, min(args.steps, 50))
@@ -655,7 +658,7 @@ def run_extras(f, args, plan, imgs, lines, x, stream, dev, rank, ws, vl_imgs, vl
         "precision_4096": precision,
         "fourier_interp": {"value": px_step / (fo_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": fo_ms,
                            "steps": fo_steps,
-                           "workload": "the same 64 x 1024^2 step (forward + top-32 peaks) with the band-limited "
+                           "workload": "the same 64 x 1024^2 step (ft_detect, top-32 peaks) with the band-limited "
                                        "(chirp-z, Sec. IV) interpolator instead of the linear one"},
         "fwd_bwd": {"value": px_step / (fb_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": fb_ms,
                     "steps": fb_steps, "kernels_us": fb_kernels,

@@ -129,9 +129,27 @@ ft_status ft_backward(ft_plan plan, const float* d_grad_map, float* d_grad_img, 
  * ascending; the neighbourhood wraps around both axes), with |P| >= threshold,
  * the first top_k of them in that order.  d_out: [batch][top_k] ft_peak;
  * d_count: [batch] int32, the number of peaks written (< top_k when fewer pass
- * the threshold; unused slots are zeroed).  1 <= top_k <= FT_MAX_TOPK. */
+ * the threshold; unused slots are zeroed).  1 <= top_k <= FT_MAX_TOPK; a NaN
+ * threshold is FT_ERR_INVALID_ARG.  Two launches: the maximum of |P| per 32 x 32
+ * tile (one read of the maps), then one block per map that tests only the tiles
+ * whose maximum can reach the top_k (a peak never exceeds its tile's maximum),
+ * brightest tiles first. */
 ft_status ft_peaks(ft_plan plan, const float* d_map, int batch, int top_k, float threshold,
                    ft_peak* d_out, int32_t* d_count, void* stream);
+
+/* Detection on device buffers: ft_forward (d_img -> d_map) followed by ft_peaks
+ * on d_map, with the same arguments, layouts, rules and results (d_map holds
+ * the map afterwards).  Where step 4 runs the fixed-length FP32 kernel on the
+ * caller's stream (n_intercept with a fixed-length schedule, FP32 precision, no
+ * lanes), it also writes the maximum of |P| of every tile of its output and the
+ * peak pass reads only the tiles whose maximum can reach the top_k: a peak
+ * never exceeds its tile's maximum, so once top_k peaks are known, tiles below
+ * the top_k-th value cannot contribute; the list is the same as ft_peaks'
+ * (Sec. 4.4; checked equal element by element).  4 launches then (5 in the
+ * inverse space), else those of ft_forward and ft_peaks.  threshold must not be
+ * NaN (FT_ERR_INVALID_ARG, as for ft_peaks). */
+ft_status ft_detect(ft_plan plan, const float* d_img, float* d_map, int batch, int top_k, float threshold,
+                    ft_peak* d_out, int32_t* d_count, void* stream);
 
 /* Loss for fitting by gradient through ft_backward (the paper fits nothing by
  * gradient; this is the loss of the differentiable workload): with
@@ -157,7 +175,7 @@ ft_status ft_abs_mse_backward(ft_plan plan, const float* d_map, const float* d_t
                               float* d_loss, float* d_grad_img, void* stream);
 
 /* End-to-end detection from host memory: copies h_img ([batch][H][W]) to a
- * plan-owned device buffer, runs ft_forward and ft_peaks, copies the peaks and
+ * plan-owned device buffer, runs ft_detect (ft_forward and ft_peaks), copies the peaks and
  * counts back to h_out ([batch][top_k]) and h_count ([batch]) and synchronises
  * `stream` before returning.  The batch is processed in chunks of 8 images: a
  * plan-owned copy stream uploads the next chunk while `stream` transforms the
@@ -186,7 +204,7 @@ ft_status ft_detect_host(ft_plan plan, const float* h_img, int batch, int top_k,
  * device, under a lock); make that first call before any stream capture.  All
  * calls share the one array, so calls whose work overlaps on the GPU (other
  * streams, other threads) race on it; calls in order on one stream are safe.
- * n_intercept, n_slope >= 2; 1 <= top_k <= FT_MAX_TOPK. */
+ * n_intercept, n_slope >= 2; 1 <= top_k <= FT_MAX_TOPK; threshold not NaN. */
 #define FT_NOALLOC_SCRATCH_BYTES (16u << 20)
 ft_status ft_peaks_noalloc(const float* d_map, int n_intercept, int n_slope, int batch, int top_k,
                            float threshold, ft_peak* d_out, int32_t* d_count, void* stream);
@@ -212,7 +230,7 @@ int ft_plan_get_variant(ft_plan plan);
  * elements}); peaks are written as [n][top_k] rows and counts as [n] in the same
  * packed order.  Equal shapes are contiguous, largest first.
  *
- * ft_batch_run enqueues every group's ft_forward (and ft_peaks when top_k > 0)
+ * ft_batch_run enqueues every group's ft_detect (ft_forward alone when top_k = 0)
  * on up to 8 side streams forked from and joined back into `stream`.
  *   FT_BATCH_GRAPH: capture that sequence once into a CUDA graph (after an
  *     uncaptured run that allocates every workspace and synchronises `stream`)
@@ -317,6 +335,8 @@ size_t ft_workspace_bytes(ft_plan plan, int batch);
  * halves overlapping); by default everything runs on the caller's stream. */
 int ft_forward_launches(ft_plan plan, int batch);
 int ft_peaks_launches(ft_plan plan, int batch);
+/* The same for ft_detect with this batch and top_k (0 for an invalid top_k). */
+int ft_detect_launches(ft_plan plan, int batch, int top_k);
 
 /* Kernel identifiers of the per-launch timing below. */
 typedef enum {
@@ -328,7 +348,9 @@ typedef enum {
     FT_KERNEL_NVMT_ROWS_ADJ = 5,   /* transpose of steps 2-3 */
     FT_KERNEL_LOSS = 6,            /* ft_abs_mse_grad */
     FT_KERNEL_VERIFY = 7,          /* ft_verify, Sec. 4.5 */
-    FT_KERNEL_COUNT = 8
+    FT_KERNEL_PEAK_SPARSE = 8,     /* Sec. 4.4 from tile maxima (ft_peaks, ft_detect) */
+    FT_KERNEL_TILE_MAX = 9,        /* tile maxima of a given map (ft_peaks) */
+    FT_KERNEL_COUNT = 10
 } ft_kernel_id;
 
 /* Per-launch timing (a measurement aid, off by default).  While enabled, every

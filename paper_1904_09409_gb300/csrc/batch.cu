@@ -152,10 +152,11 @@ static ft_status enqueue(ft_batch_s* b, const float* imgs, float* maps, int top_
     for (size_t gi = 0; gi < b->groups.size(); ++gi) {
         const Group& g = b->groups[gi];
         cudaStream_t gs = b->streams[gi % b->nstreams];
-        ft_status s = ft_forward(g.plan, imgs + b->img_off[g.start], maps + b->map_off[g.start], g.count, gs);
-        if (s == FT_OK && top_k > 0)
-            s = ft_peaks(g.plan, maps + b->map_off[g.start], g.count, top_k, thr, out + (size_t)g.start * top_k,
-                         cnt + g.start, gs);
+        const float* img = imgs + b->img_off[g.start];
+        float* gm = maps + b->map_off[g.start];
+        const ft_status s = top_k > 0 ? ft_detect(g.plan, img, gm, g.count, top_k, thr, out + (size_t)g.start * top_k,
+                                                  cnt + g.start, gs)
+                                      : ft_forward(g.plan, img, gm, g.count, gs);
         if (s != FT_OK) return s;
     }
     for (int s = 0; s < b->nstreams; ++s) {
@@ -182,9 +183,9 @@ static ft_status tune(ft_batch_s* b, const float* imgs, float* maps, int top_k, 
             float* gm = maps + b->map_off[g.start];
             for (int rep = 0; rep < 7 && rs == FT_OK; ++rep) {
                 if (rep == 2) cudaEventRecord(e0, st);
-                rs = ft_forward(g.plan, gi, gm, g.count, st);
-                if (rs == FT_OK && top_k > 0)
-                    rs = ft_peaks(g.plan, gm, g.count, top_k, thr, out + (size_t)g.start * top_k, cnt + g.start, st);
+                rs = top_k > 0 ? ft_detect(g.plan, gi, gm, g.count, top_k, thr, out + (size_t)g.start * top_k,
+                                           cnt + g.start, st)
+                               : ft_forward(g.plan, gi, gm, g.count, st);
             }
             cudaEventRecord(e1, st);
             if (cudaEventSynchronize(e1) != cudaSuccess) {

@@ -287,6 +287,20 @@ cudaError_t launch_peak_select(const unsigned long long* keys, const unsigned* b
                                int top_k, ft_peak* out, int32_t* count, cudaStream_t st);
 size_t peaks_key_bytes(int Hp, int S, int batch, int top_k);
 
+// The same detected list from tile maxima of |map| (k_peak_sparse.cu): tmax
+// [batch][ceil(Hp / tile_rows)][ceil(S / tile_cols)] float bits of the maximum
+// of each tile (the last ones ragged), from step 4 (launch_col_c2r_fast) or
+// launch_tile_max; one block per image reads only the tiles that can hold one
+// of the top_k peaks.  peak_sparse_fits: the tile shape is usable (tile_cols a
+// power of two, tile_rows x tile_cols a multiple of 32) and the pass's shared
+// memory fits the current device.
+bool peak_sparse_fits(int tile_rows, int tile_cols, int top_k);
+cudaError_t launch_peak_sparse(const float* map, const unsigned* tmax, int Hp, int S, int tile_rows, int tile_cols,
+                               int batch, int top_k, float threshold, ft_peak* out, int32_t* count, cudaStream_t st);
+// tile maxima of given maps (map 8-byte aligned) in tiles of tile_max_shape
+void tile_max_shape(int* tile_rows, int* tile_cols);
+cudaError_t launch_tile_max(const float* map, int Hp, int S, int batch, unsigned* tmax, cudaStream_t st);
+
 // the band-limited NVMT fused with step 3 (k_fourier.cu)
 cudaError_t launch_chirp_fft(float2* hc, int L, const FftLen& fm, cudaStream_t st);
 cudaError_t launch_nvmt_rows_fourier_adj(float2* ws, int W, int S, int Hp, int L, const FftLen& fw,

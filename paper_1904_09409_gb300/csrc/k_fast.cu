@@ -79,7 +79,7 @@ template <int N>
 __global__ void __launch_bounds__(fs_T(N) * fs_Bcol(N))
 k_col_c2r_fast(const float2* __restrict__ in, int ncols, int in_pitch, size_t in_img,
                const float2* __restrict__ stw, float mid_scale, float* __restrict__ out, int row0,
-               int rows_out, int out_pitch, size_t out_img, float out_scale) {
+               int rows_out, int out_pitch, size_t out_img, float out_scale, unsigned* __restrict__ tmax) {
     constexpr int B = fs_Bcol(N), E = fs_E(N);
     constexpr int R0 = fs_radix(N, 0), G0 = E / R0;
     constexpr int RL = fs_radix(N, fs_nst(N) - 1), GL = E / RL;
@@ -129,6 +129,35 @@ k_col_c2r_fast(const float2* __restrict__ in, int ncols, int in_pitch, size_t in
         }
     __syncthreads();
     F::template run<0>(v, sm, t, f, stw);
+    if (tmax) {
+        // Tile maxima of |map| for the peak pass: thread t holds rows t + T j,
+        // j = m + GL q, so band j (rows T j .. T j + T - 1) has one element in
+        // every thread; tile (j, blockIdx.x) = band j of the block's 2B columns.
+        // Each thread puts max(|re|, |im|) of its element of band j (the stored,
+        // scaled values; NaN counts as 0, like a cell that is never a peak) at
+        // bm[j][thread] in the exchange buffer, which the FFT no longer reads;
+        // warp w then reduces bands w, w + warps, ... (conflict-free rows, one
+        // redux.sync each).
+        constexpr int NT = fs_T(N) * B;                // threads of the block
+        static_assert(E * NT <= FastFft<N, +1, B>::SLOTS * 2, "band maxima fit the exchange buffer");
+        unsigned* bm = reinterpret_cast<unsigned*>(sm);
+#pragma unroll
+        for (int m = 0; m < GL; ++m)
+#pragma unroll
+            for (int q = 0; q < RL; ++q) {
+                const float a = fabsf(v[m * RL + q].x * out_scale), b = fabsf(v[m * RL + q].y * out_scale);
+                bm[(m + GL * q) * NT + threadIdx.x] = colok ? __float_as_uint(fmaxf(fmaxf(a, b), 0.f)) : 0u;
+            }
+        __syncthreads();
+        const int lane = threadIdx.x & 31;
+        for (int w = threadIdx.x >> 5; w < E; w += NT / 32) {
+            unsigned u = 0u;
+#pragma unroll
+            for (int k = 0; k < NT / 32; ++k) u = max(u, bm[w * NT + 32 * k + lane]);
+            u = __reduce_max_sync(0xffffffffu, u);
+            if (lane == 0) tmax[((size_t)blockIdx.y * E + w) * gridDim.x + blockIdx.x] = u;
+        }
+    }
     if (!colok) return;
     float* dst = out + (size_t)blockIdx.y * out_img + c;
 #pragma unroll
@@ -413,14 +442,14 @@ static cudaError_t go_r2c_loss(const float* map, const float* target, int ncols,
 template <int N>
 static cudaError_t go_c2r(const float2* in, int ncols, int in_pitch, size_t in_img, const float2* stw,
                           float mid, float* out, int row0, int rows_out, int out_pitch, size_t out_img,
-                          float os, int batch, cudaStream_t st) {
+                          float os, unsigned* tmax, int batch, cudaStream_t st) {
     constexpr int B = fs_Bcol(N);
     const size_t sm = (size_t)FastFft<N, +1, B>::SLOTS * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_col_c2r_fast<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     dim3 grid((ncols + 2 * B - 1) / (2 * B), batch);
     k_col_c2r_fast<N><<<grid, fs_T(N) * B, sm, st>>>(in, ncols, in_pitch, in_img, stw, mid, out, row0,
-                                                     rows_out, out_pitch, out_img, os);
+                                                     rows_out, out_pitch, out_img, os, tmax);
     return cudaGetLastError();
 }
 
@@ -498,14 +527,24 @@ cudaError_t launch_col_r2c_loss_fast(const float* map, const float* target, int 
 cudaError_t launch_col_c2r_fast(const float2* in, int ncols, int in_pitch, size_t in_img,
                                 const FftLen& f, float mid_scale, float* out, int row0, int rows_out,
                                 int out_pitch, size_t out_img, float out_scale, int batch,
-                                cudaStream_t st) {
+                                cudaStream_t st, unsigned* tmax) {
+    if (tmax && (row0 != 0 || rows_out != f.N)) return cudaErrorInvalidValue;
     switch (f.N) {
 #define X(n) case n: return go_c2r<n>(in, ncols, in_pitch, in_img, f.stw, mid_scale, out, row0, rows_out, \
-                                      out_pitch, out_img, out_scale, batch, st);
+                                      out_pitch, out_img, out_scale, tmax, batch, st);
         FT_FAST_LENGTHS(X)
 #undef X
     }
     return cudaErrorNotSupported;
+}
+
+bool c2r_tile_shape(int N, int* rows, int* cols, int* bands) {
+    switch (N) {
+#define X(n) case n: *rows = fs_T(n); *cols = 2 * fs_Bcol(n); *bands = fs_E(n); return true;
+        FT_FAST_LENGTHS(X)
+#undef X
+    }
+    return false;
 }
 
 cudaError_t launch_nvmt_rows_fast(float2* ws, int W, int Hp, int L, int interp, const FftLen& fx,

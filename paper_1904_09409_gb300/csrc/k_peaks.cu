@@ -148,22 +148,7 @@ k_peak_select(const u64* __restrict__ keys, const unsigned* __restrict__ bounds,
         if (i >= cnt) sel[i] = 0ull;
     __syncthreads();
     bitonic_desc(sel, Kp);
-    for (int i = threadIdx.x; i < K; i += blockDim.x) {
-        ft_peak p;
-        if (i < cnt) {
-            const u64 key = sel[i];
-            const unsigned lin = 0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFull);
-            p.t = (int)(lin / (unsigned)S);
-            p.s = (int)(lin % (unsigned)S);
-            p.value = __uint_as_float((unsigned)(key >> 32));
-            p.k = 2.0f * (float)(p.s - S / 2) / (float)S;
-            p.b = (float)(p.t - Hp / 2);
-        } else {
-            p.t = 0; p.s = 0; p.value = 0.f; p.k = 0.f; p.b = 0.f;
-        }
-        out[(size_t)blockIdx.x * K + i] = p;
-    }
-    if (threadIdx.x == 0) count[blockIdx.x] = cnt;
+    write_peaks(sel, cnt, K, Hp, S, out, count, blockIdx.x);
 }
 
 #define PF_TS 128

@@ -47,7 +47,8 @@ static cudaError_t scratch_address(void** out) {
 extern "C" ft_status ft_peaks_noalloc(const float* d_map, int n_intercept, int n_slope, int batch,
                                       int top_k, float threshold, ft_peak* d_out, int32_t* d_count,
                                       void* stream) {
-    if (batch < 0 || batch > 65535 || top_k < 1 || top_k > FT_MAX_TOPK) return FT_ERR_INVALID_ARG;
+    if (batch < 0 || batch > 65535 || top_k < 1 || top_k > FT_MAX_TOPK || threshold != threshold)
+        return FT_ERR_INVALID_ARG;
     if (n_intercept < 2 || n_slope < 2) return FT_ERR_UNSUPPORTED_SIZE;
     if ((long long)n_intercept * n_slope > 0xFFFFFFFFll) return FT_ERR_UNSUPPORTED_SIZE;
     if (batch == 0) return FT_OK;

@@ -45,10 +45,11 @@ struct SelState {
     int count;
 };
 
-// Marks the top K non-zero keys of keys[0..n) (any address space): on return
-// every key k != 0 with (k & st.mask) >= st.prefix is selected and there are
-// exactly min(K, #non-zero keys) of them.  Called by the whole block.
-static __device__ void cta_select(const u64* keys, int n, int K, SelState& st) {
+// Marks the top K non-zero keys key_of(0 .. n-1) (distinct unless zero): on
+// return every key k != 0 with (k & st.mask) >= st.prefix is selected and there
+// are exactly min(K, #non-zero keys) of them.  Called by the whole block.
+template <typename KeyOf>
+static __device__ void cta_select_by(int n, int K, SelState& st, KeyOf key_of) {
     if (threadIdx.x == 0) {
         st.prefix = 0ull;
         st.mask = 0ull;
@@ -61,9 +62,14 @@ static __device__ void cta_select(const u64* keys, int n, int K, SelState& st) {
         for (int i = threadIdx.x; i < 256; i += blockDim.x) st.hist[i] = 0u;
         __syncthreads();
         const u64 pf = st.prefix, mk = st.mask;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const u64 key = keys[i];
-            if (key != 0ull && (key & mk) == pf) atomicAdd(&st.hist[(key >> shift) & 255u], 1u);
+        for (int i0 = threadIdx.x & ~31; i0 < n; i0 += blockDim.x) {
+            // keys share their leading digits, so lanes with equal digits add once
+            const int i = i0 + (threadIdx.x & 31);
+            const u64 key = i < n ? key_of(i) : 0ull;
+            const bool in = key != 0ull && (key & mk) == pf;
+            const unsigned d = in ? (unsigned)(key >> shift) & 255u : 256u;
+            const unsigned same = __match_any_sync(0xffffffffu, d);
+            if (in && (threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&st.hist[d], (unsigned)__popc(same));
         }
         __syncthreads();
         if (threadIdx.x < 32) {
@@ -109,7 +115,35 @@ static __device__ void cta_select(const u64* keys, int n, int K, SelState& st) {
     }
 }
 
+// cta_select_by over the array keys[0..n) (any address space)
+static __device__ void cta_select(const u64* keys, int n, int K, SelState& st) {
+    cta_select_by(n, K, st, [keys](int i) { return keys[i]; });
+}
+
 __device__ __forceinline__ bool selected(u64 key, const SelState& st) {
     return key != 0ull && (key & st.mask) >= st.prefix;
+}
+
+// The ft_peak records of image `img` from its cnt best keys sorted descending
+// (sel[0..cnt)): (t, s) from the linear index, value = |P|, k = 2 (s - S/2) / S
+// and b = t - H'/2 (eqs. 22-23); slots cnt .. K-1 zeroed; count[img] = cnt.
+static __device__ void write_peaks(const u64* sel, int cnt, int K, int Hp, int S, ft_peak* out, int32_t* count,
+                                   int img) {
+    for (int i = threadIdx.x; i < K; i += blockDim.x) {
+        ft_peak p;
+        if (i < cnt) {
+            const u64 key = sel[i];
+            const unsigned lin = 0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFull);
+            p.t = (int)(lin / (unsigned)S);
+            p.s = (int)(lin % (unsigned)S);
+            p.value = __uint_as_float((unsigned)(key >> 32));
+            p.k = 2.0f * (float)(p.s - S / 2) / (float)S;
+            p.b = (float)(p.t - Hp / 2);
+        } else {
+            p.t = 0; p.s = 0; p.value = 0.f; p.k = 0.f; p.b = 0.f;
+        }
+        out[(size_t)img * K + i] = p;
+    }
+    if (threadIdx.x == 0) count[img] = cnt;
 }
 

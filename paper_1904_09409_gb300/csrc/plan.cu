@@ -209,11 +209,12 @@ static cudaError_t col_r2c(ft_plan p, const float* in, int rows_in, int ncols, i
 
 static cudaError_t col_c2r(ft_plan p, const float2* in, int ncols, float mid, float* out, int row0,
                            int rows_out, int out_pitch, size_t out_img, float os, int batch,
-                           cudaStream_t st) {
+                           cudaStream_t st, unsigned* tmax = nullptr) {
     const size_t in_img = (size_t)p->L * p->S;
     if (p->use_fast_y)
         return launch_col_c2r_fast(in, ncols, p->S, in_img, p->fy, mid, out, row0, rows_out, out_pitch,
-                                   out_img, os, batch, st);
+                                   out_img, os, batch, st, tmax);
+    if (tmax) return cudaErrorInvalidValue;
     return launch_col_c2r(in, ncols, p->S, in_img, p->fy, p->col_logB_y, mid, out, row0, rows_out,
                           out_pitch, out_img, os, batch, st);
 }
@@ -496,9 +497,45 @@ int ft_peaks_launches(ft_plan p, int batch) {
     return 2 * (use_lanes(p, batch) ? FT_LANES : 1);
 }
 
+// split precision: the length-4096 column transforms on the tensor cores too
+bool tc_columns(ft_plan p);
+
+// The tile shape of ft_detect's peak pass (the tiles whose maxima step 4
+// writes), or false when ft_detect runs ft_forward and ft_peaks instead: step 4
+// must be the fixed-length FP32 kernel on the caller's stream, and the pass's
+// shared memory must fit.
+static bool sparse_peaks(ft_plan p, int batch, int top_k, int* rows, int* cols, int* bands) {
+    if (!p->use_fast_y || tc_columns(p) || use_lanes(p, batch)) return false;
+    if (!c2r_tile_shape(p->Hp, rows, cols, bands)) return false;
+    return peak_sparse_fits(*rows, *cols, top_k);
+}
+
+// scratch of ft_peaks: tile maxima, or the per-tile keys where the pass from
+// tile maxima does not fit
+static size_t peaks_scratch_bytes(ft_plan p, int batch, int top_k) {
+    int tr, tc;
+    tile_max_shape(&tr, &tc);
+    if (!peak_sparse_fits(tr, tc, top_k)) return peaks_key_bytes(p->Hp, p->S, batch, top_k);
+    return (size_t)batch * ((p->Hp + tr - 1) / tr) * ((p->S + tc - 1) / tc) * sizeof(unsigned);
+}
+
+// bytes of ft_detect's tile maxima for this batch (0 when it runs ft_peaks)
+static size_t tmax_bytes(ft_plan p, int batch, int top_k) {
+    int rows, cols, bands;
+    if (!sparse_peaks(p, batch, top_k, &rows, &cols, &bands)) return 0;
+    return (size_t)batch * bands * ((p->S + cols - 1) / cols) * sizeof(unsigned);
+}
+
+int ft_detect_launches(ft_plan p, int batch, int top_k) {
+    if (!p || batch <= 0 || top_k < 1 || top_k > FT_MAX_TOPK) return 0;
+    int rows, cols, bands;
+    if (sparse_peaks(p, batch, top_k, &rows, &cols, &bands)) return (p->space == FT_SPACE_INVERSE ? 1 : 0) + 4;
+    return ft_forward_launches(p, batch) + ft_peaks_launches(p, batch);
+}
+
 // split precision: the length-4096 column transforms on the tensor cores too,
 // through a column-major copy (cm) so that their column pairs are contiguous rows
-static bool tc_columns(ft_plan p) { return p->precision != FT_PRECISION_FP32 && p->Hp == 4096; }
+bool tc_columns(ft_plan p) { return p->precision != FT_PRECISION_FP32 && p->Hp == 4096; }
 static size_t cm_elems(ft_plan p) {
     const size_t a = (size_t)p->H * p->W, b = (size_t)p->Hp * p->S;
     return a > b ? a : b;
@@ -516,8 +553,10 @@ static cudaError_t tc_c2r(ft_plan p, const float2* ws, float* d_map, float* cm, 
     return launch_transpose(cm, d_map, p->S, p->Hp, nb, st);
 }
 
+// Steps 1-4 of nb images; tmax (fixed-length FP32 step 4 only, else NULL) gets
+// the tile maxima of |map| for the peak pass of ft_detect.
 static ft_status forward_part(ft_plan p, const float* src, float* d_map, float2* ws, float* cm, int nb,
-                              cudaStream_t st) {
+                              cudaStream_t st, unsigned* tmax = nullptr) {
     const bool tc_cols = tc_columns(p);
     FT_LAUNCH(p, FT_KERNEL_COL_R2C, st,
               tc_cols ? tc_r2c(p, src, ws, cm, nb, st)
@@ -527,7 +566,7 @@ static ft_status forward_part(ft_plan p, const float* src, float* d_map, float2*
     FT_LAUNCH(p, FT_KERNEL_COL_C2R, st,
               tc_cols ? tc_c2r(p, ws, d_map, cm, nb, st)
                       : col_c2r(p, ws, p->S, 1.f, d_map, 0, p->Hp, p->S, (size_t)p->Hp * p->S, 1.f / (float)p->Hp,
-                                nb, st),
+                                nb, st, tmax),
               "step 4 (column C2R)");
     return FT_OK;
 }
@@ -630,14 +669,20 @@ ft_status ft_abs_mse_backward(ft_plan p, const float* d_map, const float* d_targ
 ft_status ft_peaks(ft_plan p, const float* d_map, int batch, int top_k, float threshold,
                    ft_peak* d_out, int32_t* d_count, void* stream) {
     if (!p || batch < 0 || batch > 65535) return FT_ERR_INVALID_ARG;
-    if (top_k < 1 || top_k > FT_MAX_TOPK) return FT_ERR_INVALID_ARG;
+    if (top_k < 1 || top_k > FT_MAX_TOPK || threshold != threshold) return FT_ERR_INVALID_ARG;
     if (batch == 0) return FT_OK;
     if (!d_map || !d_out || !d_count) return FT_ERR_INVALID_ARG;
-    // the key buffer lives after the spectrum workspace of this batch
-    const size_t keys = peaks_key_bytes(p->Hp, p->S, batch, top_k);
+    // Tile maxima of the maps (one streaming read), then the peak pass that reads
+    // only the tiles able to hold one of the top_k peaks; the per-tile key kernels
+    // where that pass does not fit.  Scratch after the spectrum workspace.
+    int tr, tc;
+    tile_max_shape(&tr, &tc);
+    const bool sparse = peak_sparse_fits(tr, tc, top_k);
+    const size_t tpi = (size_t)((p->Hp + tr - 1) / tr) * ((p->S + tc - 1) / tc);     // tiles per map
     const size_t off = aux_off(p, batch);
-    ft_status s = ensure(&p->d_ws, &p->ws_bytes, off + keys, "cudaMalloc(workspace)");
+    ft_status s = ensure(&p->d_ws, &p->ws_bytes, off + peaks_scratch_bytes(p, batch, top_k), "cudaMalloc(workspace)");
     if (s != FT_OK) return s;
+    unsigned* tmax = (unsigned*)((char*)p->d_ws + off);
     unsigned long long* kbuf = (unsigned long long*)((char*)p->d_ws + off);
     cudaStream_t st = (cudaStream_t)stream;
     unsigned* bounds = peaks_bounds(kbuf, p->Hp, p->S, batch, top_k);
@@ -648,6 +693,16 @@ ft_status ft_peaks(ft_plan p, const float* d_map, int batch, int top_k, float th
         const int b0 = batch * j / lanes, b1 = batch * (j + 1) / lanes;
         cudaStream_t ls = lanes > 1 ? p->lane_streams[j] : st;
         const float* m = d_map + (size_t)b0 * p->Hp * p->S;
+        if (sparse) {
+            FT_LAUNCH(p, FT_KERNEL_TILE_MAX, ls,
+                      launch_tile_max(m, p->Hp, p->S, b1 - b0, tmax + b0 * tpi, ls),
+                      "peak detection (tile maxima)");
+            FT_LAUNCH(p, FT_KERNEL_PEAK_SPARSE, ls,
+                      launch_peak_sparse(m, tmax + b0 * tpi, p->Hp, p->S, tr, tc, b1 - b0, top_k, threshold,
+                                         d_out + (size_t)b0 * top_k, d_count + b0, ls),
+                      "peak detection (from tile maxima)");
+            continue;
+        }
         FT_LAUNCH(p, FT_KERNEL_PEAK_TILES, ls,
                   launch_peak_tiles(m, p->Hp, p->S, b1 - b0, top_k, threshold, kbuf + b0 * kpi, bounds + 2 * b0,
                                     ls),
@@ -658,6 +713,38 @@ ft_status ft_peaks(ft_plan p, const float* d_map, int batch, int top_k, float th
                   "peak detection (select)");
     }
     if (lanes > 1) return lanes_join(p, st);
+    return FT_OK;
+}
+
+ft_status ft_detect(ft_plan p, const float* d_img, float* d_map, int batch, int top_k, float threshold,
+                    ft_peak* d_out, int32_t* d_count, void* stream) {
+    if (!p || batch < 0 || batch > 65535) return FT_ERR_INVALID_ARG;
+    if (top_k < 1 || top_k > FT_MAX_TOPK || threshold != threshold) return FT_ERR_INVALID_ARG;
+    if (batch == 0) return FT_OK;
+    if (!d_img || !d_map || !d_out || !d_count || ((uintptr_t)d_img & 7) || ((uintptr_t)d_map & 7))
+        return FT_ERR_INVALID_ARG;
+    int rows, cols, bands;
+    if (!sparse_peaks(p, batch, top_k, &rows, &cols, &bands)) {
+        const ft_status s = ft_forward(p, d_img, d_map, batch, stream);
+        return s != FT_OK ? s : ft_peaks(p, d_map, batch, top_k, threshold, d_out, d_count, stream);
+    }
+    // the tile maxima [batch][bands][column blocks] live in the aux region
+    const size_t off = aux_off(p, batch);
+    ft_status s = ensure(&p->d_ws, &p->ws_bytes, off + tmax_bytes(p, batch, top_k), "cudaMalloc(workspace)");
+    if (s != FT_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    float2* ws = (float2*)p->d_ws;
+    unsigned* tmax = (unsigned*)((char*)p->d_ws + off);
+    const float* src = d_img;
+    if (p->space == FT_SPACE_INVERSE) {
+        float* tp = (float*)((char*)p->d_ws + tposed_off(p, batch));
+        FT_CUDA(launch_transpose(d_img, tp, p->img_H, p->img_W, batch, st), "transpose (inverse space)");
+        src = tp;
+    }
+    if ((s = forward_part(p, src, d_map, ws, nullptr, batch, st, tmax)) != FT_OK) return s;
+    FT_LAUNCH(p, FT_KERNEL_PEAK_SPARSE, st,
+              launch_peak_sparse(d_map, tmax, p->Hp, p->S, rows, cols, batch, top_k, threshold, d_out, d_count, st),
+              "peak detection (tile maxima)");
     return FT_OK;
 }
 
@@ -750,13 +837,16 @@ const char* ft_kernel_name(int id) {
         case FT_KERNEL_NVMT_ROWS_ADJ: return "k_nvmt_rows_adjoint";
         case FT_KERNEL_LOSS: return "k_abs_mse_grad";
         case FT_KERNEL_VERIFY: return "k_verify";
+        case FT_KERNEL_PEAK_SPARSE: return "k_peak_sparse";
+        case FT_KERNEL_TILE_MAX: return "k_tile_max";
     }
     return "unknown";
 }
 
 ft_status ft_detect_host(ft_plan p, const float* h_img, int batch, int top_k, float threshold,
                          ft_peak* h_out, int32_t* h_count, void* stream) {
-    if (!p || batch < 0 || batch > 65535 || top_k < 1 || top_k > FT_MAX_TOPK) return FT_ERR_INVALID_ARG;
+    if (!p || batch < 0 || batch > 65535 || top_k < 1 || top_k > FT_MAX_TOPK || threshold != threshold)
+        return FT_ERR_INVALID_ARG;
     if (batch == 0) return FT_OK;
     if (!h_img || !h_out || !h_count) return FT_ERR_INVALID_ARG;
     const size_t img_px = (size_t)p->img_H * p->img_W;
@@ -783,8 +873,11 @@ ft_status ft_detect_host(ft_plan p, const float* h_img, int batch, int top_k, fl
         FT_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
         p->chunk_events.push_back(e);
     }
-    // size the workspace for one chunk before any copy is in flight
-    const size_t need = aux_off(p, chunk) + peaks_key_bytes(p->Hp, p->S, chunk, top_k);
+    // size the workspace for one chunk before any copy is in flight (the larger
+    // of the two peak passes' scratch: tile maxima or per-tile keys)
+    const size_t tmax_b = tmax_bytes(p, chunk, top_k);
+    const size_t peak_b = peaks_scratch_bytes(p, chunk, top_k);
+    const size_t need = aux_off(p, chunk) + (tmax_b > peak_b ? tmax_b : peak_b);
     if ((s = ensure(&p->d_ws, &p->ws_bytes, need, "cudaMalloc(workspace)")) != FT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     FT_CUDA(cudaEventRecord(p->start_event, st), "event");
@@ -799,10 +892,8 @@ ft_status ft_detect_host(ft_plan p, const float* h_img, int batch, int top_k, fl
     for (int c = 0; c < nchunks; ++c) {
         const int b0 = c * chunk, nb = (batch - b0) < chunk ? (batch - b0) : chunk;
         FT_CUDA(cudaStreamWaitEvent(st, p->chunk_events[c], 0), "wait for chunk");
-        if ((s = ft_forward(p, p->d_img_host + b0 * img_px, p->d_map_host + b0 * map_px, nb, stream)) != FT_OK)
-            return s;
-        if ((s = ft_peaks(p, p->d_map_host + b0 * map_px, nb, top_k, threshold, p->d_peaks_host + (size_t)b0 * top_k,
-                          p->d_count_host + b0, stream)) != FT_OK)
+        if ((s = ft_detect(p, p->d_img_host + b0 * img_px, p->d_map_host + b0 * map_px, nb, top_k, threshold,
+                           p->d_peaks_host + (size_t)b0 * top_k, p->d_count_host + b0, stream)) != FT_OK)
             return s;
         FT_CUDA(cudaMemcpyAsync(h_out + (size_t)b0 * top_k, p->d_peaks_host + (size_t)b0 * top_k,
                                 (size_t)nb * top_k * sizeof(ft_peak), cudaMemcpyDeviceToHost, st),

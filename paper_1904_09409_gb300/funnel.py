@@ -38,7 +38,7 @@ EXPORTED = (
     "ft_batch_create", "ft_batch_destroy", "ft_batch_layout", "ft_batch_group_count",
     "ft_batch_group_info", "ft_batch_group_tuned_ms", "ft_batch_run", "ft_tc_dft64",
     "ft_plan_set_precision", "ft_plan_get_precision", "ft_plan_tc_errors", "ft_verify",
-    "ft_abs_mse_backward",
+    "ft_abs_mse_backward", "ft_detect", "ft_detect_launches",
 )
 FT_PRECISION_FP32 = 0
 FT_PRECISION_BF16X3 = 1
@@ -52,7 +52,7 @@ FT_SPACE_REGULAR = 0
 FT_SPACE_INVERSE = 1
 SPACE_NAMES = {"regular": FT_SPACE_REGULAR, "inverse": FT_SPACE_INVERSE}
 FT_NOALLOC_SCRATCH_BYTES = 16 << 20
-FT_KERNEL_COUNT = 8
+FT_KERNEL_COUNT = 10
 
 
 class FtPeak(ctypes.Structure):
@@ -129,6 +129,10 @@ def lib() -> ctypes.CDLL:
     L.ft_verify.restype = ci
     L.ft_abs_mse_backward.argtypes = [vp, vp, vp, ci, cf, vp, vp, vp]
     L.ft_abs_mse_backward.restype = ci
+    L.ft_detect.argtypes = [vp, vp, vp, ci, ci, cf, vp, vp, vp]
+    L.ft_detect.restype = ci
+    L.ft_detect_launches.argtypes = [vp, ci, ci]
+    L.ft_detect_launches.restype = ci
     for name in ("ft_plan_variant_count", "ft_plan_set_variant", "ft_plan_get_variant", "ft_batch_create",
                  "ft_batch_destroy", "ft_batch_layout", "ft_batch_group_count", "ft_batch_group_info",
                  "ft_batch_run"):
@@ -257,6 +261,25 @@ def ft_peaks(plan: Plan, fmap, top_k: int, threshold: float = float("-inf"), out
     return out, count
 
 
+def ft_detect(plan: Plan, img, out_map, top_k: int, threshold: float = float("-inf"), out=None, count=None,
+              batch: Optional[int] = None, stream=None):
+    """ft_forward (img -> out_map) and ft_peaks of that map in one call (same
+    results); returns (peaks, count) like ft_peaks."""
+    import torch
+    b = img.shape[0] if batch is None else int(batch)
+    ip = _dev_ptr(img, "float32", b * plan.H * plan.W, "img")
+    mp = _dev_ptr(out_map, "float32", b * plan.Hp * plan.S, "map")
+    if out is None:
+        out = torch.empty(b * top_k * PEAK_DTYPE.itemsize, dtype=torch.uint8, device=out_map.device)
+    if count is None:
+        count = torch.empty(b, dtype=torch.int32, device=out_map.device)
+    op = _dev_ptr(out, "uint8", b * top_k * PEAK_DTYPE.itemsize, "out")
+    cp = _dev_ptr(count, "int32", b, "count")
+    _check(lib().ft_detect(plan.handle, ip, mp, b, int(top_k), float(threshold), op, cp, _stream_ptr(stream)),
+           "ft_detect")
+    return out, count
+
+
 def ft_verify(plan: Plan, img, peaks, count, top_k: int, half_width: int = 2, min_contrast: float = 0.1,
               min_length: int = 16, batch: Optional[int] = None, stream=None):
     """Line verification (Sec. 4.5) of the peaks ft_peaks wrote for this plan.
@@ -372,6 +395,10 @@ def ft_forward_launches(plan: Plan, batch: int) -> int:
 
 def ft_peaks_launches(plan: Plan, batch: int) -> int:
     return int(lib().ft_peaks_launches(plan.handle, int(batch)))
+
+
+def ft_detect_launches(plan: Plan, batch: int, top_k: int) -> int:
+    return int(lib().ft_detect_launches(plan.handle, int(batch), int(top_k)))
 
 
 def ft_profile_enable(plan: Plan, enable: bool = True) -> None:

@@ -77,6 +77,11 @@ def test_invalid_arguments(L):
     assert L.ft_backward(None, None, None, 1, None) == f.FT_ERR_INVALID_ARG
     assert L.ft_peaks(None, None, 1, 3, 0.0, None, None, None) == f.FT_ERR_INVALID_ARG
     assert L.ft_detect_host(None, None, 1, 3, 0.0, None, None, None) == f.FT_ERR_INVALID_ARG
+    assert L.ft_detect(None, None, None, 1, 3, 0.0, None, None, None) == f.FT_ERR_INVALID_ARG
+    assert L.ft_detect_launches(None, 4, 32) == 0
+    # a NaN threshold is an argument error (checked before any GPU work)
+    assert L.ft_peaks_noalloc(ctypes.c_void_p(256), 16, 16, 1, 3, float("nan"), ctypes.c_void_p(256),
+                              ctypes.c_void_p(256), None) == f.FT_ERR_INVALID_ARG
     assert L.ft_plan_destroy(None) == f.FT_OK
     assert L.ft_workspace_bytes(None, 4) == 0
     assert L.ft_forward_launches(None, 4) == 0

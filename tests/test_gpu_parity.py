@@ -186,6 +186,114 @@ def test_peaks_dense_tile_with_k_1024(torch, Hp, S):
     assert got[0] == ref
 
 
+# ft_detect: forward + peaks in one call; where step 4 writes tile maxima the
+# peak pass reads only the tiles that can hold one of the top_k.  H, W, S, H',
+# top_k, threshold; the c2r tile of each H' in the comment.
+DETECT_CASES = [
+    (256, 256, 256, 256, 3, float("-inf")),      # 16 x 64 tiles, the single-image workload
+    (1024, 1024, 1024, 1024, 32, float("-inf")),  # 64 x 16 tiles, the batch workload
+    (200, 200, 216, 256, 40, float("-inf")),      # S = 216 ragged against 64-column tiles
+    (100, 96, 96, 192, 17, float("-inf")),        # H' = 192: 12 bands of 16 rows
+    (128, 200, 216, 4096, 100, float("-inf")),    # 256 x 8 tiles, ragged S
+    (64, 16, 16, 8192, 5, float("-inf")),         # 512 x 4 tiles
+    (256, 256, 256, 256, 1024, float("-inf")),    # top_k above the number of tiles
+    (256, 256, 256, 256, 64, 30.0),               # a threshold few peaks pass
+    (48, 40, 64, 72, 8, float("-inf")),           # H' = 72 has no fixed-length kernel: forward + peaks
+]
+
+
+@pytest.mark.parametrize("H,W,S,Hp,K,thr", DETECT_CASES)
+def test_detect_matches_forward_and_peaks(torch, H, W, S, Hp, K, thr):
+    from paper_1904_09409_gb300 import funnel as f
+    imgs = inputs(H, W, 3, H + W + S + K)
+    x = torch.from_numpy(imgs).cuda()
+    with make_plan(H, W, S, Hp) as plan:
+        ref_map = _gpu.forward(plan, imgs)
+        m = torch.full((3, Hp, S), float("nan"), dtype=torch.float32, device="cuda")
+        out, cnt = f.ft_detect(plan, x, m, K, thr)
+        torch.cuda.synchronize()
+        n_launch = f.ft_detect_launches(plan, 3, K)
+    assert n_launch == (4 if Hp != 72 else 3 + 2)
+    assert np.array_equal(m.cpu().numpy(), ref_map)
+    got = [[(int(p["t"]), int(p["s"]), float(p["value"])) for p in r] for r in f.peaks_to_numpy(out, cnt, K)]
+    for i in range(3):
+        assert got[i] == oracle.peaks_ref(np.abs(ref_map[i]).astype(np.float64), K, thr), i
+
+
+def test_detect_zero_image_all_ties(torch):
+    """A zero image has a zero map (row l = 0 is dropped): every cell ties, so
+    the only strict local maximum under the total order is cell (0, 0), and the
+    pass must visit every tile before it knows that."""
+    from paper_1904_09409_gb300 import funnel as f
+    x = torch.zeros((2, 256, 256), dtype=torch.float32, device="cuda")
+    with make_plan(256, 256, 256, 256) as plan:
+        m = torch.empty((2, 256, 256), dtype=torch.float32, device="cuda")
+        out, cnt = f.ft_detect(plan, x, m, 8)
+        torch.cuda.synchronize()
+    assert not m.abs().max().item()
+    res = f.peaks_to_numpy(out, cnt, 8)
+    for r in res:
+        assert [(int(p["t"]), int(p["s"])) for p in r] == [(0, 0)]
+
+
+def test_detect_inverse_space(torch):
+    from paper_1904_09409_gb300 import funnel as f
+    imgs = inputs(64, 48, 2, 11)
+    with f.Plan(64, 48, 64, 128, "linear", "inverse") as plan:       # transposed frame: H' = 128 >= 48
+        ref_map = _gpu.forward(plan, imgs)
+        m = torch.empty((2, plan.Hp, plan.S), dtype=torch.float32, device="cuda")
+        out, cnt = f.ft_detect(plan, torch.from_numpy(imgs).cuda(), m, 12)
+        torch.cuda.synchronize()
+        assert f.ft_detect_launches(plan, 2, 12) == 5
+    assert np.array_equal(m.cpu().numpy(), ref_map)
+    got = [[(int(p["t"]), int(p["s"]), float(p["value"])) for p in r] for r in f.peaks_to_numpy(out, cnt, 12)]
+    for i in range(2):
+        assert got[i] == oracle.peaks_ref(np.abs(ref_map[i]).astype(np.float64), 12), i
+
+
+def test_detect_nan_threshold_rejected(torch):
+    from paper_1904_09409_gb300 import funnel as f
+    x = torch.zeros((1, 32, 32), dtype=torch.float32, device="cuda")
+    m = torch.empty((1, 32, 32), dtype=torch.float32, device="cuda")
+    with make_plan(32, 32, 32, 32) as plan:
+        for call in (lambda: f.ft_detect(plan, x, m, 4, float("nan")), lambda: f.ft_peaks(plan, m, 4, float("nan"))):
+            with pytest.raises(f.FunnelError) as e:
+                call()
+            assert e.value.status == f.FT_ERR_INVALID_ARG
+
+
+def _certification_map(kind, rng, Hp, S):
+    """Maps that stress the tile bound of the peak pass (32 x 32 tiles for
+    ft_peaks): plateaus of equal values across tile borders, every tile's
+    maximum on its border next to a brighter cell of the next tile, and ramps
+    whose maxima sit at the wrap."""
+    if kind == "plateaus":
+        blocks = rng.integers(0, 6, size=(Hp // 24 + 1, S // 24 + 1)).astype(np.float32)
+        return np.kron(blocks, np.ones((24, 24), np.float32))[:Hp, :S] + 0.0
+    if kind == "border_max":
+        m = rng.uniform(0.0, 1.0, size=(Hp, S)).astype(np.float32)
+        for t0 in range(0, Hp, 32):
+            for s0 in range(0, S, 32):
+                m[t0 + 31, s0 + 5] = 50.0 + t0 + s0 / 1000.0          # last row of the tile
+                m[(t0 + 32) % Hp, s0 + 5] = 60.0 + t0 + s0 / 1000.0   # first row of the tile below: brighter
+        return m
+    t = np.arange(Hp)[:, None]
+    s_ = np.arange(S)[None, :]
+    return ((t // 3) + (s_ // 5)).astype(np.float32)
+
+
+@pytest.mark.parametrize("kind", ["plateaus", "border_max", "ramps"])
+@pytest.mark.parametrize("K", [1, 8, 64, 300])
+def test_peaks_tile_bound_edge_cases(torch, kind, K):
+    rng = np.random.default_rng(K)
+    maps = np.stack([_certification_map(kind, rng, 256, 192), -_certification_map(kind, rng, 256, 192)])
+    with make_plan(256, 192, 192, 256) as plan:
+        for thr in (float("-inf"), 3.0):
+            got, _ = _gpu.peaks(plan, maps, K, thr)
+            for i in range(2):
+                assert got[i] == oracle.peaks_ref(np.abs(maps[i]).astype(np.float64), K, thr), (i, thr)
+
+
 def test_lane_split_gives_identical_results(torch, monkeypatch):
     """FT_LANES=2 splits a batch over two plan-owned streams: maps and peaks are
     bit-identical to the single-stream run."""
