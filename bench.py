@@ -42,7 +42,7 @@ WORKLOAD = "64 x 1024x1024 FP32 synthetic line images, map 1024x1024, top-32 pea
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -134,20 +134,21 @@ def measured_peaks():
 def kernel_bytes(name: str, H: int, W: int, S: int, Hp: int, K: int) -> float:
     """Algorithmic DRAM bytes per image of each kernel (compulsory reads and
     writes of its own inputs and outputs).  The peak pass from tile maxima reads
-    the tile maxima and the cells of the tiles it tests, at least the first
-    R = ceil(K / 32) * 32 tiles (more when its bound needs them)."""
+    the tile maxima and the cells of the tiles it tests, at least the 32 it
+    starts with (more when its bound needs them)."""
     L = Hp // 2 + 1
     ntiles = ((Hp + 31) // 32) * ((S + 63) // 64)
     kt = min(K, 512)
-    # tiles of step 4's maxima at H' = 1024: 64 rows x 16 columns
-    c2r_tiles = (Hp // 64) * ((S + 15) // 16)
-    R = min(c2r_tiles, (K + 31) // 32 * 32)
+    # tiles of step 4's maxima at H' = 1024: 16 rows x 16 columns; the first 32
+    # (one per warp) are read with their one-cell halo
+    c2r_tiles = (Hp // 16) * ((S + 15) // 16)
+    R = min(c2r_tiles, 32)
     return {
         "k_col_r2c": 4.0 * H * W + 8.0 * L * W,          # image in, half spectrum out
         "k_nvmt_rows": 8.0 * L * W + 8.0 * L * S,        # spectrum rows in, G rows out
         "k_col_c2r": 8.0 * L * S + 4.0 * Hp * S + 4.0 * c2r_tiles,   # G in, map and tile maxima out
-        "k_peak_sparse": 4.0 * c2r_tiles + 4.0 * R * 64 * 16 + 20.0 * K + 4.0,
-        "k_tile_max": 4.0 * Hp * S + 4.0 * ((Hp + 31) // 32) * ((S + 31) // 32),
+        "k_peak_sparse": 4.0 * c2r_tiles + 4.0 * R * 18 * 18 + 20.0 * K + 4.0,
+        "k_tile_max": 4.0 * Hp * S + 4.0 * ((Hp + 15) // 16) * ((S + 15) // 16),
         "k_peak_tiles": 4.0 * Hp * S + 8.0 * ntiles * kt,  # map in, tile keys out
         "k_peak_select": 8.0 * ntiles * kt + 20.0 * K + 4.0,
     }.get(name, 0.0)

@@ -130,10 +130,14 @@ ft_status ft_backward(ft_plan plan, const float* d_grad_map, float* d_grad_img, 
  * the first top_k of them in that order.  d_out: [batch][top_k] ft_peak;
  * d_count: [batch] int32, the number of peaks written (< top_k when fewer pass
  * the threshold; unused slots are zeroed).  1 <= top_k <= FT_MAX_TOPK; a NaN
- * threshold is FT_ERR_INVALID_ARG.  Two launches: the maximum of |P| per 32 x 32
- * tile (one read of the maps), then one block per map that tests only the tiles
- * whose maximum can reach the top_k (a peak never exceeds its tile's maximum),
- * brightest tiles first. */
+ * threshold is FT_ERR_INVALID_ARG.  Two launches, one of two passes with the
+ * same result, whichever a cost model measured on GB300 expects to be faster
+ * for this batch, map size and top_k (FT_PEAKS=sparse or dense in the
+ * environment at plan creation fixes it): either the maximum of |P| per 16 x 16
+ * tile (one read of the maps), then one block per map that tests only the
+ * tiles whose maximum can reach the top_k (a peak never exceeds its tile's
+ * maximum), brightest tiles first; or every tile's strict local maxima over
+ * the whole GPU, then a per-map selection. */
 ft_status ft_peaks(ft_plan plan, const float* d_map, int batch, int top_k, float threshold,
                    ft_peak* d_out, int32_t* d_count, void* stream);
 
@@ -141,7 +145,8 @@ ft_status ft_peaks(ft_plan plan, const float* d_map, int batch, int top_k, float
  * on d_map, with the same arguments, layouts, rules and results (d_map holds
  * the map afterwards).  Where step 4 runs the fixed-length FP32 kernel on the
  * caller's stream (n_intercept with a fixed-length schedule, FP32 precision, no
- * lanes), it also writes the maximum of |P| of every tile of its output and the
+ * lanes) and ft_peaks' cost model prefers the pass from tile maxima, step 4 also
+ * writes the maximum of |P| of every 256-cell tile of its output and the
  * peak pass reads only the tiles whose maximum can reach the top_k: a peak
  * never exceeds its tile's maximum, so once top_k peaks are known, tiles below
  * the top_k-th value cannot contribute; the list is the same as ft_peaks'

@@ -248,6 +248,9 @@ ft_status ft_batch_create(ft_batch* out, int n, const int32_t* H, const int32_t*
             Group g{H[i], W[i], j, 0, nullptr, 0.f};
             st = ft_plan_create(&g.plan, H[i], W[i], W[i], H[i], interp);
             if (st != FT_OK) break;
+            // the groups run side by side: the peak pass that occupies one
+            // multiprocessor per image (unless FT_PEAKS fixed it)
+            if (g.plan->peak_mode == 0) g.plan->peak_mode = 1;
             const int v = cached.empty() ? -1 : cached_variant(cached, cache_key(b, g));
             if (v >= 0) ft_plan_set_variant(g.plan, v);
             b->groups.push_back(g);

@@ -209,14 +209,16 @@ cudaError_t launch_col_r2c_loss_fast(const float* map, const float* target, int 
                                      float2* out, int out_pitch, size_t out_img, float end_scale, float mid_scale,
                                      float scale, float gscale, float* partial, int batch, cudaStream_t st);
 // tmax (may be NULL; only with row0 = 0 and rows_out = N): the maxima of |out| per
-// tile of c2r_tile_shape rows x columns, [batch][bands][ceil(ncols / cols)] as
+// tile of c2r_tile_shape rows x columns, [batch][N / rows][ceil(ncols / cols)] as
 // float bits
 cudaError_t launch_col_c2r_fast(const float2* in, int ncols, int in_pitch, size_t in_img,
                                 const FftLen& f, float mid_scale, float* out, int row0, int rows_out,
                                 int out_pitch, size_t out_img, float out_scale, int batch,
                                 cudaStream_t st, unsigned* tmax = nullptr);
 // tiles of the tile maxima of launch_col_c2r_fast for length N: rows x cols
-// cells, bands = N / rows tiles per column block; false without a schedule
+// cells, bands = N / rows tiles per column block; false without a schedule.
+// A tile is 256 cells: 128 / B rows of one column block of 2B columns.
+__host__ __device__ constexpr int c2r_tile_rows(int N) { return 128 / fs_Bcol(N); }
 bool c2r_tile_shape(int N, int* rows, int* cols, int* bands);
 cudaError_t launch_nvmt_rows_fast(float2* ws, int W, int Hp, int L, int interp, const FftLen& fx,
                                   int batch, cudaStream_t st);

@@ -213,6 +213,8 @@ struct ft_plan_s {
     int col_logB_max, row_logB_max;  // the largest that fit the shared-memory budget
     int use_fast_y, use_fast_x;      // fixed-length kernels in use for H' / S
     int variant;            // see ft_plan_set_variant
+    int peak_mode;          // peak pass: 0 = the faster one by the cost model, 1 = from tile maxima, 2 = per-tile keys
+    int num_sms;            // multiprocessors of the plan's device
     int precision;          // ft_precision of step 3 (ft_plan_set_precision)
     unsigned* d_tc_err;     // error flags of the tensor-core kernels (allocated with the first split precision)
     // band-limited (chirp-z) interpolator: lengths W and M >= W + S, chirp tables

@@ -131,14 +131,18 @@ k_col_c2r_fast(const float2* __restrict__ in, int ncols, int in_pitch, size_t in
     F::template run<0>(v, sm, t, f, stw);
     if (tmax) {
         // Tile maxima of |map| for the peak pass: thread t holds rows t + T j,
-        // j = m + GL q, so band j (rows T j .. T j + T - 1) has one element in
-        // every thread; tile (j, blockIdx.x) = band j of the block's 2B columns.
-        // Each thread puts max(|re|, |im|) of its element of band j (the stored,
-        // scaled values; NaN counts as 0, like a cell that is never a peak) at
-        // bm[j][thread] in the exchange buffer, which the FFT no longer reads;
-        // warp w then reduces bands w, w + warps, ... (conflict-free rows, one
-        // redux.sync each).
+        // j = m + GL q, of its column pair.  A tile is RS = c2r_tile_rows(N)
+        // consecutive rows of one band (rows T j + RS u .. T j + RS u + RS - 1,
+        // u < T / RS) of the block's 2B columns, 256 cells held by the RS B
+        // consecutive threads t = RS u .. RS u + RS - 1.  Each thread puts
+        // max(|re|, |im|) of its element of band j (the stored, scaled values;
+        // NaN counts as 0, like a cell that is never a peak) at bm[j][thread] in
+        // the exchange buffer, which the FFT no longer reads; then every warp
+        // reduces tiles w, w + warps, ...: 4 conflict-free words per lane and
+        // one redux.sync.
         constexpr int NT = fs_T(N) * B;                // threads of the block
+        constexpr int RS = c2r_tile_rows(N), TPB = fs_T(N) / RS;   // tile rows, tiles per band
+        static_assert(RS * B == 128, "a tile is 128 threads' values");
         static_assert(E * NT <= FastFft<N, +1, B>::SLOTS * 2, "band maxima fit the exchange buffer");
         unsigned* bm = reinterpret_cast<unsigned*>(sm);
 #pragma unroll
@@ -150,12 +154,12 @@ k_col_c2r_fast(const float2* __restrict__ in, int ncols, int in_pitch, size_t in
             }
         __syncthreads();
         const int lane = threadIdx.x & 31;
-        for (int w = threadIdx.x >> 5; w < E; w += NT / 32) {
-            unsigned u = 0u;
-#pragma unroll
-            for (int k = 0; k < NT / 32; ++k) u = max(u, bm[w * NT + 32 * k + lane]);
-            u = __reduce_max_sync(0xffffffffu, u);
-            if (lane == 0) tmax[((size_t)blockIdx.y * E + w) * gridDim.x + blockIdx.x] = u;
+        for (int w = threadIdx.x >> 5; w < E * TPB; w += NT / 32) {
+            const int j = w / TPB, u = w - j * TPB;
+            const unsigned* src = bm + j * NT + u * 128 + lane;
+            unsigned x = max(max(src[0], src[32]), max(src[64], src[96]));
+            x = __reduce_max_sync(0xffffffffu, x);
+            if (lane == 0) tmax[((size_t)blockIdx.y * E * TPB + w) * gridDim.x + blockIdx.x] = x;
         }
     }
     if (!colok) return;
@@ -232,12 +236,14 @@ k_col_r2c_loss_fast(const float* __restrict__ map, const float* __restrict__ tar
     r2c_finish<N>(v, sm, t, f, stw, colok, out + (size_t)blockIdx.y * out_img + c, out_pitch, end_scale, mid_scale);
 }
 
-// row pitch (complex) of the staged spectrum rows: W + 2 keeps 16-byte
-// alignment for cp.async and shifts successive rows by 4 banks
-__host__ __device__ constexpr int srow_pitch(int W) { return W + 2; }
+// row pitch (complex) of the staged spectrum rows: W samples between two zero
+// samples on each side (so a clamped tap index needs no bounds test); W + 4
+// keeps 16-byte alignment for cp.async and shifts successive rows by 8 banks
+__host__ __device__ constexpr int srow_pitch(int W) { return W + 4; }
 
+// at most 64 registers, so that 4 blocks of 256 threads share a multiprocessor
 template <int N, int INTERP>
-__global__ void __launch_bounds__(fs_T(N) * fs_Brow(N))
+__global__ void __launch_bounds__(fs_T(N) * fs_Brow(N), 1024 / (fs_T(N) * fs_Brow(N)))
 k_nvmt_rows_fast(float2* __restrict__ ws, int W, int Hp, int L, const float2* __restrict__ stw) {
     constexpr int B = fs_Brow(N), E = fs_E(N), T = N / E;
     constexpr int R0 = fs_radix(N, 0), G0 = E / R0;
@@ -245,8 +251,9 @@ k_nvmt_rows_fast(float2* __restrict__ ws, int W, int Hp, int L, const float2* __
     constexpr int STEPX = N / R0;                      // x' distance between a thread's elements
     using F = FastFft<N, +1, B>;
     extern __shared__ float2 sm[];
-    // [B][W + 2] input rows (16-byte aligned) in the FFT's own exchange buffer:
-    // they are read only by the gather, which ends before the first exchange
+    // [B][W + 4] input rows (sample x at 2 + x, 16-byte aligned, two zeros on
+    // each side) in the FFT's own exchange buffer: they are read only by the
+    // gather, which ends before the first exchange
     float2* srow = sm;
     const int WP = srow_pitch(W);
     const int f = threadIdx.x % B;
@@ -257,15 +264,19 @@ k_nvmt_rows_fast(float2* __restrict__ ws, int W, int Hp, int L, const float2* __
 
     // stage the block's B spectrum rows (W complex each) with 16-byte async copies
     const int chunks = W >> 1;                         // two complex per 16 bytes
-    for (int idx = threadIdx.x; idx < B * chunks; idx += blockDim.x) {
-        const int r = idx / chunks;
-        const int c = idx - r * chunks;
-        float2* dst = srow + r * WP + 2 * c;
+    if (threadIdx.x < 2 * B) {
+        const int r = threadIdx.x >> 1;
+        *reinterpret_cast<float4*>(srow + r * WP + ((threadIdx.x & 1) ? W + 2 : 0)) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+        float2* dst = srow + r * WP + 2;
+        const float2* src = base + (size_t)(l0 + r) * N;
         if (l0 + r < L) {
-            cp_async16(dst, base + (size_t)(l0 + r) * N + 2 * c);
+            for (int c = threadIdx.x; c < chunks; c += fs_T(N) * B) cp_async16(dst + 2 * c, src + 2 * c);
         } else {
-            dst[0] = make_float2(0.f, 0.f);
-            dst[1] = make_float2(0.f, 0.f);
+            for (int c = threadIdx.x; c < chunks; c += fs_T(N) * B)
+                *reinterpret_cast<float4*>(dst + 2 * c) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
     cp_async_wait_all();
@@ -275,7 +286,7 @@ k_nvmt_rows_fast(float2* __restrict__ ws, int W, int Hp, int L, const float2* __
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = make_float2(0.f, 0.f);
     if (l >= 1 && l < L) {
-        const float2* myrow = srow + f * WP;
+        const float2* myrow = srow + f * WP + 2;
         const int den = 2 * l;
         const float inv = 1.f / (float)den;
         const int step = STEPX * Hp;
@@ -294,8 +305,9 @@ k_nvmt_rows_fast(float2* __restrict__ ws, int W, int Hp, int L, const float2* __
                 const int c0 = qf + halfW;
                 float2 acc;
                 if constexpr (INTERP == FT_INTERP_LINEAR) {
-                    const float2 a0 = (unsigned)c0 < (unsigned)W ? myrow[c0] : zero;
-                    const float2 a1 = (unsigned)(c0 + 1) < (unsigned)W ? myrow[c0 + 1] : zero;
+                    // taps c0, c0 + 1; outside 0 .. W-1 the padding's zeros
+                    const int cc = min(max(c0, -2), W);
+                    const float2 a0 = myrow[cc], a1 = myrow[cc + 1];
                     acc = make_float2(fmaf(fr, a1.x - a0.x, a0.x), fmaf(fr, a1.y - a0.y, a0.y));
                 } else {
                     acc = zero;
@@ -540,7 +552,7 @@ cudaError_t launch_col_c2r_fast(const float2* in, int ncols, int in_pitch, size_
 
 bool c2r_tile_shape(int N, int* rows, int* cols, int* bands) {
     switch (N) {
-#define X(n) case n: *rows = fs_T(n); *cols = 2 * fs_Bcol(n); *bands = fs_E(n); return true;
+#define X(n) case n: *rows = c2r_tile_rows(n); *cols = 2 * fs_Bcol(n); *bands = n / c2r_tile_rows(n); return true;
         FT_FAST_LENGTHS(X)
 #undef X
     }

@@ -273,29 +273,29 @@ k_peak_sparse(const float* __restrict__ map, const unsigned* __restrict__ tmax, 
 }
 
 // Tile maxima of given maps: one warp per tile of PT_ROWS x PT_COLS cells (the
-// last row / column of tiles ragged), lane l reading columns 2 (l mod 16) + 0, 1
-// of rows l / 16 + 2 j (8-byte loads, 128 bytes per row, all 16 in flight);
-// NaN counts as 0.  tmax[b][ceil(Hp / PT_ROWS)][ceil(S / PT_COLS)].
-#define PT_ROWS 32
-#define PT_COLS 32
+// last row / column of tiles ragged), lane l reading columns 2 (l mod 8) + 0, 1
+// of rows l / 8 + 4 j (8-byte loads, 64 bytes per row, all 4 in flight); NaN
+// counts as 0.  tmax[b][ceil(Hp / PT_ROWS)][ceil(S / PT_COLS)].
+#define PT_ROWS 16
+#define PT_COLS 16
 __global__ void __launch_bounds__(256)
 k_tile_max(const float* __restrict__ map, int Hp, int S, int nty, int ntx, unsigned* __restrict__ tmax) {
     const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (tile >= nty * ntx) return;
     const int lane = threadIdx.x & 31;
     const int ty = tile / ntx, tx = tile - ty * ntx;
-    const int s = tx * PT_COLS + 2 * (lane & 15);
-    const int t0 = ty * PT_ROWS + (lane >> 4);
+    const int s = tx * PT_COLS + 2 * (lane & 7);
+    const int t0 = ty * PT_ROWS + (lane >> 3);
     const float* m = map + (size_t)blockIdx.y * Hp * S + s;
-    float2 v[PT_ROWS / 2];
+    float2 v[PT_ROWS / 4];
 #pragma unroll
-    for (int j = 0; j < PT_ROWS / 2; ++j) {            // S is even, so s < S means s + 1 < S
-        const int t = t0 + 2 * j;
+    for (int j = 0; j < PT_ROWS / 4; ++j) {            // S is even, so s < S means s + 1 < S
+        const int t = t0 + 4 * j;
         v[j] = (s < S && t < Hp) ? __ldg(reinterpret_cast<const float2*>(m + (size_t)t * S)) : make_float2(0.f, 0.f);
     }
     float mx = 0.f;
 #pragma unroll
-    for (int j = 0; j < PT_ROWS / 2; ++j) mx = fmaxf(mx, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
+    for (int j = 0; j < PT_ROWS / 4; ++j) mx = fmaxf(mx, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
     const unsigned u = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
     if (lane == 0) tmax[((size_t)blockIdx.y * nty + ty) * ntx + tx] = u;
 }

@@ -353,6 +353,10 @@ ft_status ft_plan_create_space(ft_plan* out, int img_H, int img_W, int n_slope, 
     p->variant = generic ? 1 : 0;
     const char* lanes = getenv("FT_LANES");
     p->lanes = lanes && atoi(lanes) > 1 ? FT_LANES : 1;
+    const char* pm = getenv("FT_PEAKS");
+    p->peak_mode = pm && !strcmp(pm, "sparse") ? 1 : (pm && !strcmp(pm, "dense") ? 2 : 0);
+    if (cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess || p->num_sms < 1)
+        p->num_sms = 1;
     *out = p;
     return FT_OK;
 }
@@ -504,19 +508,48 @@ bool tc_columns(ft_plan p);
 // writes), or false when ft_detect runs ft_forward and ft_peaks instead: step 4
 // must be the fixed-length FP32 kernel on the caller's stream, and the pass's
 // shared memory must fit.
+// Whether the pass from tile maxima beats the per-tile key kernels for this
+// call.  It runs one block per image, so it costs about one image's work per
+// wave of images: selecting among the tiles, then batches of 32 tiles (one at
+// 1024^2 with top_k = 32, over 20 at 4096^2 with top_k = 100: the batch count
+// grows with tiles x top_k), plus, for ft_peaks, one streaming read for the tile
+// maxima; the key kernels spread every cell over the whole GPU.  Constants in
+// microseconds, measured on GB300 (64 x 1024^2 and 8 x 4096^2 maps).  The pass
+// from tile maxima occupies only one multiprocessor per image, so plans whose
+// calls share the GPU with others (ft_batch) always take it.  FT_PEAKS=sparse /
+// dense at plan creation fixes the choice.
+static bool sparse_is_faster(ft_plan p, int batch, int top_k, bool with_tile_max) {
+    if (p->peak_mode) return p->peak_mode == 1;
+    const double cells = (double)p->Hp * p->S, tiles = cells / 256.0;
+    const int waves = (batch + p->num_sms - 1) / p->num_sms;
+    const double batches = 1.0 + tiles * top_k / 3.0e5;
+    const double sparse = waves * (8.0 + 1.2e-3 * tiles + 12.0 * batches) + (with_tile_max ? 0.7e-6 * cells * batch : 0.0);
+    const double dense = 1.6e-6 * cells * batch + 5.0;
+    return sparse < dense;
+}
+
 static bool sparse_peaks(ft_plan p, int batch, int top_k, int* rows, int* cols, int* bands) {
     if (!p->use_fast_y || tc_columns(p) || use_lanes(p, batch)) return false;
     if (!c2r_tile_shape(p->Hp, rows, cols, bands)) return false;
-    return peak_sparse_fits(*rows, *cols, top_k);
+    return peak_sparse_fits(*rows, *cols, top_k) && sparse_is_faster(p, batch, top_k, false);
+}
+
+// ft_peaks takes the pass from tile maxima (tiles of tile_max_shape)
+static bool peaks_use_tile_max(ft_plan p, int batch, int top_k) {
+    int tr, tc;
+    tile_max_shape(&tr, &tc);
+    return peak_sparse_fits(tr, tc, top_k) && sparse_is_faster(p, batch, top_k, true);
 }
 
 // scratch of ft_peaks: tile maxima, or the per-tile keys where the pass from
 // tile maxima does not fit
-static size_t peaks_scratch_bytes(ft_plan p, int batch, int top_k) {
+static size_t tile_max_bytes(ft_plan p, int batch) {
     int tr, tc;
     tile_max_shape(&tr, &tc);
-    if (!peak_sparse_fits(tr, tc, top_k)) return peaks_key_bytes(p->Hp, p->S, batch, top_k);
     return (size_t)batch * ((p->Hp + tr - 1) / tr) * ((p->S + tc - 1) / tc) * sizeof(unsigned);
+}
+static size_t peaks_scratch_bytes(ft_plan p, int batch, int top_k) {
+    return peaks_use_tile_max(p, batch, top_k) ? tile_max_bytes(p, batch) : peaks_key_bytes(p->Hp, p->S, batch, top_k);
 }
 
 // bytes of ft_detect's tile maxima for this batch (0 when it runs ft_peaks)
@@ -677,7 +710,7 @@ ft_status ft_peaks(ft_plan p, const float* d_map, int batch, int top_k, float th
     // where that pass does not fit.  Scratch after the spectrum workspace.
     int tr, tc;
     tile_max_shape(&tr, &tc);
-    const bool sparse = peak_sparse_fits(tr, tc, top_k);
+    const bool sparse = peaks_use_tile_max(p, batch, top_k);
     const size_t tpi = (size_t)((p->Hp + tr - 1) / tr) * ((p->S + tc - 1) / tc);     // tiles per map
     const size_t off = aux_off(p, batch);
     ft_status s = ensure(&p->d_ws, &p->ws_bytes, off + peaks_scratch_bytes(p, batch, top_k), "cudaMalloc(workspace)");
@@ -875,9 +908,11 @@ ft_status ft_detect_host(ft_plan p, const float* h_img, int batch, int top_k, fl
     }
     // size the workspace for one chunk before any copy is in flight (the larger
     // of the two peak passes' scratch: tile maxima or per-tile keys)
-    const size_t tmax_b = tmax_bytes(p, chunk, top_k);
-    const size_t peak_b = peaks_scratch_bytes(p, chunk, top_k);
-    const size_t need = aux_off(p, chunk) + (tmax_b > peak_b ? tmax_b : peak_b);
+    // (a smaller last chunk may take the other peak pass: room for every kind)
+    size_t peak_b = tmax_bytes(p, chunk, top_k);
+    if (tile_max_bytes(p, chunk) > peak_b) peak_b = tile_max_bytes(p, chunk);
+    if (peaks_key_bytes(p->Hp, p->S, chunk, top_k) > peak_b) peak_b = peaks_key_bytes(p->Hp, p->S, chunk, top_k);
+    const size_t need = aux_off(p, chunk) + peak_b;
     if ((s = ensure(&p->d_ws, &p->ws_bytes, need, "cudaMalloc(workspace)")) != FT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     FT_CUDA(cudaEventRecord(p->start_event, st), "event");

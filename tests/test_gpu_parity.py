@@ -22,6 +22,13 @@ def torch():
     return _gpu.torch_cuda()
 
 
+@pytest.fixture(params=["sparse", "dense"])
+def peak_mode(request, monkeypatch):
+    """Both peak passes (from tile maxima / per-tile keys), fixed at plan creation."""
+    monkeypatch.setenv("FT_PEAKS", request.param)
+    return request.param
+
+
 def make_plan(H, W, S, Hp, interp="linear"):
     from paper_1904_09409_gb300 import funnel as f
     return f.Plan(H, W, S, Hp, interp)
@@ -133,7 +140,7 @@ def test_full_size_batch_sampled(torch):
 # ------------------------------------------------------------------- peaks
 @pytest.mark.parametrize("Hp,S", [(2, 2), (4, 6), (8, 8), (48, 72), (64, 128), (96, 216), (32, 384), (128, 256)])
 @pytest.mark.parametrize("K", [1, 5, 64])
-def test_peaks_exact_with_ties(torch, Hp, S, K):
+def test_peaks_exact_with_ties(torch, peak_mode, Hp, S, K):
     rng = np.random.default_rng(Hp * 1000 + S + K)
     maps = rng.integers(-3, 4, size=(3, Hp, S)).astype(np.float32)   # many equal |values|
     with make_plan(Hp, S, S, Hp) as plan:
@@ -146,7 +153,7 @@ def test_peaks_exact_with_ties(torch, Hp, S, K):
 
 @pytest.mark.parametrize("K", [32, 513, 1024])
 @pytest.mark.parametrize("Hp,S", [(256, 192), (256, 256)])     # generic and register-only tiles
-def test_peaks_exact_large_k(torch, K, Hp, S):
+def test_peaks_exact_large_k(torch, peak_mode, K, Hp, S):
     rng = np.random.default_rng(K)
     maps = rng.standard_normal((2, Hp, S)).astype(np.float32)
     with make_plan(Hp, S, S, Hp) as plan:
@@ -157,7 +164,7 @@ def test_peaks_exact_large_k(torch, K, Hp, S):
 
 
 @pytest.mark.parametrize("K,thr", [(200, float("-inf")), (1024, float("-inf")), (300, 2.5)])
-def test_peaks_exact_appended_key_lists(torch, K, thr):
+def test_peaks_exact_appended_key_lists(torch, peak_mode, K, thr):
     """Maps large enough that the register tiles append their keys to one list
     per image (256 tiles x K keys above the fixed-slot limit), with ties and a
     threshold, against the list procedure."""
@@ -172,7 +179,7 @@ def test_peaks_exact_appended_key_lists(torch, K, thr):
 
 
 @pytest.mark.parametrize("Hp,S", [(256, 256), (256, 192)])     # 32 x 128 and 32 x 64 tiles
-def test_peaks_dense_tile_with_k_1024(torch, Hp, S):
+def test_peaks_dense_tile_with_k_1024(torch, peak_mode, Hp, S):
     """Every (even, even) cell a strict local maximum (1024 in a 32 x 128 tile,
     the most a tile can hold), one tile much brighter than the rest: the top
     1024 peaks all come from that tile."""
@@ -203,7 +210,7 @@ DETECT_CASES = [
 
 
 @pytest.mark.parametrize("H,W,S,Hp,K,thr", DETECT_CASES)
-def test_detect_matches_forward_and_peaks(torch, H, W, S, Hp, K, thr):
+def test_detect_matches_forward_and_peaks(torch, peak_mode, H, W, S, Hp, K, thr):
     from paper_1904_09409_gb300 import funnel as f
     imgs = inputs(H, W, 3, H + W + S + K)
     x = torch.from_numpy(imgs).cuda()
@@ -213,14 +220,14 @@ def test_detect_matches_forward_and_peaks(torch, H, W, S, Hp, K, thr):
         out, cnt = f.ft_detect(plan, x, m, K, thr)
         torch.cuda.synchronize()
         n_launch = f.ft_detect_launches(plan, 3, K)
-    assert n_launch == (4 if Hp != 72 else 3 + 2)
+    assert n_launch == (4 if Hp != 72 and peak_mode == "sparse" else 3 + 2)
     assert np.array_equal(m.cpu().numpy(), ref_map)
     got = [[(int(p["t"]), int(p["s"]), float(p["value"])) for p in r] for r in f.peaks_to_numpy(out, cnt, K)]
     for i in range(3):
         assert got[i] == oracle.peaks_ref(np.abs(ref_map[i]).astype(np.float64), K, thr), i
 
 
-def test_detect_zero_image_all_ties(torch):
+def test_detect_zero_image_all_ties(torch, peak_mode):
     """A zero image has a zero map (row l = 0 is dropped): every cell ties, so
     the only strict local maximum under the total order is cell (0, 0), and the
     pass must visit every tile before it knows that."""
@@ -236,7 +243,7 @@ def test_detect_zero_image_all_ties(torch):
         assert [(int(p["t"]), int(p["s"])) for p in r] == [(0, 0)]
 
 
-def test_detect_inverse_space(torch):
+def test_detect_inverse_space(torch, peak_mode):
     from paper_1904_09409_gb300 import funnel as f
     imgs = inputs(64, 48, 2, 11)
     with f.Plan(64, 48, 64, 128, "linear", "inverse") as plan:       # transposed frame: H' = 128 >= 48
@@ -244,7 +251,7 @@ def test_detect_inverse_space(torch):
         m = torch.empty((2, plan.Hp, plan.S), dtype=torch.float32, device="cuda")
         out, cnt = f.ft_detect(plan, torch.from_numpy(imgs).cuda(), m, 12)
         torch.cuda.synchronize()
-        assert f.ft_detect_launches(plan, 2, 12) == 5
+        assert f.ft_detect_launches(plan, 2, 12) == (5 if peak_mode == "sparse" else 6)
     assert np.array_equal(m.cpu().numpy(), ref_map)
     got = [[(int(p["t"]), int(p["s"]), float(p["value"])) for p in r] for r in f.peaks_to_numpy(out, cnt, 12)]
     for i in range(2):
@@ -284,7 +291,7 @@ def _certification_map(kind, rng, Hp, S):
 
 @pytest.mark.parametrize("kind", ["plateaus", "border_max", "ramps"])
 @pytest.mark.parametrize("K", [1, 8, 64, 300])
-def test_peaks_tile_bound_edge_cases(torch, kind, K):
+def test_peaks_tile_bound_edge_cases(torch, peak_mode, kind, K):
     rng = np.random.default_rng(K)
     maps = np.stack([_certification_map(kind, rng, 256, 192), -_certification_map(kind, rng, 256, 192)])
     with make_plan(256, 192, 192, 256) as plan:
@@ -311,7 +318,7 @@ def test_lane_split_gives_identical_results(torch, monkeypatch):
     assert got_pk == ref_pk
 
 
-def test_peaks_fewer_than_k(torch):
+def test_peaks_fewer_than_k(torch, peak_mode):
     maps = np.zeros((1, 16, 16), np.float32)
     maps[0, 3, 4] = 5.0
     maps[0, 10, 12] = -4.0
