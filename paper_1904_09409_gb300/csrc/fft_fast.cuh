@@ -57,11 +57,14 @@ __host__ __device__ constexpr int fs_twoff(int N, int s) {
     return o;
 }
 __host__ __device__ constexpr int fs_twsize(int N) { return fs_twoff(N, fs_nst(N)); }
-// transforms per block for the column kernels (512 threads; for N >= 4096,
+// transforms per block for the column R2C kernels (512 threads; for N >= 4096,
 // 1024 threads so that a block still reads 4 column pairs = 32-byte row
-// segments) and the row kernels (256)
+// segments), the column C2R kernel (256 threads, at least 4 column pairs, so
+// 512 threads for N = 1536, 2048; measured faster than 512 for N = 1024 while
+// the R2C kernel is faster with 512) and the row kernels (256)
 __host__ __device__ constexpr int fs_clampB(int v, int hi) { return v < 1 ? 1 : (v > hi ? hi : v); }
 __host__ __device__ constexpr int fs_Bcol(int N) { return fs_T(N) >= 256 ? 1024 / fs_T(N) : fs_clampB(512 / fs_T(N), 32); }
+__host__ __device__ constexpr int fs_Bc2r(int N) { return fs_T(N) >= 256 ? 1024 / fs_T(N) : fs_clampB(256 / fs_T(N) < 4 ? 4 : 256 / fs_T(N), 32); }
 __host__ __device__ constexpr int fs_Brow(int N) { return fs_clampB(256 / fs_T(N), 16); }
 // padded shared-memory slot of sample n (one spare slot every 16 samples
 // spreads the strided stores of the first pass over the banks)
@@ -218,7 +221,7 @@ cudaError_t launch_col_c2r_fast(const float2* in, int ncols, int in_pitch, size_
 // tiles of the tile maxima of launch_col_c2r_fast for length N: rows x cols
 // cells, bands = N / rows tiles per column block; false without a schedule.
 // A tile is 256 cells: 128 / B rows of one column block of 2B columns.
-__host__ __device__ constexpr int c2r_tile_rows(int N) { return 128 / fs_Bcol(N); }
+__host__ __device__ constexpr int c2r_tile_rows(int N) { return 128 / fs_Bc2r(N); }
 bool c2r_tile_shape(int N, int* rows, int* cols, int* bands);
 cudaError_t launch_nvmt_rows_fast(float2* ws, int W, int Hp, int L, int interp, const FftLen& fx,
                                   int batch, cudaStream_t st);

@@ -48,7 +48,7 @@ __device__ __forceinline__ void r2c_finish(float2 (&v)[fs_E(N)], float2* sm, int
 // loads of its column pair): staging the image tile through shared memory first
 // measured slower on GB300 (67 vs 60 us for 32 images of 1024^2).
 template <int N>
-__global__ void __launch_bounds__(fs_T(N) * fs_Bcol(N))
+__global__ void __launch_bounds__(fs_T(N) * fs_Bcol(N), 1024 / (fs_T(N) * fs_Bcol(N)))
 k_col_r2c_fast(const float* __restrict__ in, int rows_in, int ncols, int in_pitch, size_t in_img,
                int row0, const float2* __restrict__ stw, float2* __restrict__ out, int out_pitch,
                size_t out_img, float end_scale, float mid_scale) {
@@ -76,11 +76,11 @@ k_col_r2c_fast(const float* __restrict__ in, int rows_in, int ncols, int in_pitc
 }
 
 template <int N>
-__global__ void __launch_bounds__(fs_T(N) * fs_Bcol(N))
+__global__ void __launch_bounds__(fs_T(N) * fs_Bc2r(N), 1024 / (fs_T(N) * fs_Bc2r(N)))
 k_col_c2r_fast(const float2* __restrict__ in, int ncols, int in_pitch, size_t in_img,
                const float2* __restrict__ stw, float mid_scale, float* __restrict__ out, int row0,
                int rows_out, int out_pitch, size_t out_img, float out_scale, unsigned* __restrict__ tmax) {
-    constexpr int B = fs_Bcol(N), E = fs_E(N);
+    constexpr int B = fs_Bc2r(N), E = fs_E(N);
     constexpr int R0 = fs_radix(N, 0), G0 = E / R0;
     constexpr int RL = fs_radix(N, fs_nst(N) - 1), GL = E / RL;
     using F = FastFft<N, +1, B>;
@@ -184,7 +184,7 @@ k_col_c2r_fast(const float2* __restrict__ in, int ncols, int in_pitch, size_t in
 // cell is loaded by exactly one thread, so the partials of an image's blocks
 // add up to its sum of r^2.  Everything after the load is r2c_finish.
 template <int N>
-__global__ void __launch_bounds__(fs_T(N) * fs_Bcol(N))
+__global__ void __launch_bounds__(fs_T(N) * fs_Bcol(N), 1024 / (fs_T(N) * fs_Bcol(N)))
 k_col_r2c_loss_fast(const float* __restrict__ map, const float* __restrict__ target, int ncols, size_t img_cells,
                     const float2* __restrict__ stw, float2* __restrict__ out, int out_pitch, size_t out_img,
                     float end_scale, float mid_scale, float scale, float gscale, float* __restrict__ partial) {
@@ -455,7 +455,7 @@ template <int N>
 static cudaError_t go_c2r(const float2* in, int ncols, int in_pitch, size_t in_img, const float2* stw,
                           float mid, float* out, int row0, int rows_out, int out_pitch, size_t out_img,
                           float os, unsigned* tmax, int batch, cudaStream_t st) {
-    constexpr int B = fs_Bcol(N);
+    constexpr int B = fs_Bc2r(N);
     const size_t sm = (size_t)FastFft<N, +1, B>::SLOTS * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_col_c2r_fast<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -552,7 +552,7 @@ cudaError_t launch_col_c2r_fast(const float2* in, int ncols, int in_pitch, size_
 
 bool c2r_tile_shape(int N, int* rows, int* cols, int* bands) {
     switch (N) {
-#define X(n) case n: *rows = c2r_tile_rows(n); *cols = 2 * fs_Bcol(n); *bands = n / c2r_tile_rows(n); return true;
+#define X(n) case n: *rows = c2r_tile_rows(n); *cols = 2 * fs_Bc2r(n); *bands = n / c2r_tile_rows(n); return true;
         FT_FAST_LENGTHS(X)
 #undef X
     }
