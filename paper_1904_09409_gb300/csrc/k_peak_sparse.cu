@@ -238,8 +238,14 @@ k_peak_sparse(const float* __restrict__ map, const unsigned* __restrict__ tmax, 
     __syncthreads();
     run_list();
 
-    // round 2: every other tile that can still hold one of the top_k peaks
-    for (int base = 0; base < ntiles; base += SP_LIST) {
+    // round 2: every other tile that can still hold one of the top_k peaks (the
+    // whole round is skipped when no tile's maximum reaches the bound)
+    bool any = false;
+    for (int i = threadIdx.x; i < ntiles && !any; i += blockDim.x) {
+        const u64 k = tkey(i);
+        any = k != 0ull && !selected(k, sh.tiles) && __uint_as_float(__ldg(tm + i)) >= sh.bound;
+    }
+    for (int base = 0; __syncthreads_or(any) && base < ntiles; base += SP_LIST) {
         __syncthreads();
         if (threadIdx.x == 0) sh.nlist = 0;
         __syncthreads();
@@ -262,13 +268,32 @@ k_peak_sparse(const float* __restrict__ map, const unsigned* __restrict__ tmax, 
         if (sh.nlist) run_list();
     }
 
-    // the list: the best min(K, ncand) keys, sorted descending
+    // the list: the best min(K, ncand) keys, sorted descending (up to 32 keys in
+    // one warp's registers, more in shared memory)
     __syncthreads();
     const int n = sh.ncand;                            // <= K after the last compaction
-    const int Kp = next_pow2(n > 0 ? n : 1);
-    for (int i = threadIdx.x; i < Kp; i += blockDim.x) keep[i] = i < n ? cand[i] : 0ull;
-    __syncthreads();
-    bitonic_desc(keep, Kp);
+    if (n <= 32) {
+        if (warp == 0) {
+            u64 key = lane < n ? cand[lane] : 0ull;
+#pragma unroll
+            for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    const u64 other = __shfl_xor_sync(0xffffffffu, key, j);
+                    // blocks of k lanes alternate descending / ascending; the
+                    // last merge (k = 32) is descending
+                    const bool keep_max = ((lane & j) == 0) == ((lane & k) == 0);
+                    key = keep_max ? (key > other ? key : other) : (key < other ? key : other);
+                }
+            if (lane < n) keep[lane] = key;          // the zero padding sorts last
+        }
+        __syncthreads();
+    } else {
+        const int Kp = next_pow2(n);
+        for (int i = threadIdx.x; i < Kp; i += blockDim.x) keep[i] = i < n ? cand[i] : 0ull;
+        __syncthreads();
+        bitonic_desc(keep, Kp);
+    }
     write_peaks(keep, n, K, Hp, S, out, count, img);
 }
 
