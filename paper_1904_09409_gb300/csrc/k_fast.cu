@@ -31,16 +31,26 @@ __device__ __forceinline__ void r2c_finish(float2 (&v)[fs_E(N)], float2* sm, int
         for (int q = 0; q < RL; ++q) sm[spos(F::out_pos(t, m, q)) * B + f] = v[m * RL + q];
     __syncthreads();
     if (!colok) return;
-    for (int l = t; l <= N / 2; l += T) {
+    auto split = [&](int l, int lm, float s) {
         const float2 zl = sm[spos(l) * B + f];
-        const float2 zm = sm[spos(l == 0 ? 0 : N - l) * B + f];
-        const float s = (l == 0 || l == N / 2) ? end_scale : mid_scale;
+        const float2 zm = sm[spos(lm) * B + f];
         float4 o;
         o.x = 0.5f * s * (zl.x + zm.x);
         o.y = 0.5f * s * (zl.y - zm.y);
         o.z = 0.5f * s * (zl.y + zm.y);
         o.w = -0.5f * s * (zl.x - zm.x);
         *reinterpret_cast<float4*>(dst + (size_t)l * out_pitch) = o;
+    };
+    // thread t writes l = t + T j; only t = 0 meets the end bins 0 and N/2
+    // (N/2 is a multiple of T), so the others need no tests
+    if (t != 0) {
+#pragma unroll
+        for (int j = 0; j < E / 2; ++j) split(t + T * j, N - t - T * j, mid_scale);
+    } else {
+        split(0, 0, end_scale);
+#pragma unroll
+        for (int j = 1; j < E / 2; ++j) split(T * j, N - T * j, mid_scale);
+        split(N / 2, N / 2, end_scale);
     }
 }
 
@@ -63,15 +73,25 @@ k_col_r2c_fast(const float* __restrict__ in, int rows_in, int ncols, int in_pitc
     const float* src = in + (size_t)blockIdx.y * in_img + c;
 
     float2 v[E];
+    if (colok && row0 == 0 && rows_in == N) {          // every row is an image row
 #pragma unroll
-    for (int m = 0; m < G0; ++m)
+        for (int m = 0; m < G0; ++m)
 #pragma unroll
-        for (int q = 0; q < R0; ++q) {
-            const int row = F::template in_pos<0>(t, m, q) - row0;
-            float2 x = make_float2(0.f, 0.f);
-            if (colok && row >= 0 && row < rows_in) x = __ldg(reinterpret_cast<const float2*>(src + (size_t)row * in_pitch));
-            v[m * R0 + q] = x;
-        }
+            for (int q = 0; q < R0; ++q)
+                v[m * R0 + q] = __ldg(reinterpret_cast<const float2*>(
+                    src + (size_t)F::template in_pos<0>(t, m, q) * in_pitch));
+    } else {
+#pragma unroll
+        for (int m = 0; m < G0; ++m)
+#pragma unroll
+            for (int q = 0; q < R0; ++q) {
+                const int row = F::template in_pos<0>(t, m, q) - row0;
+                float2 x = make_float2(0.f, 0.f);
+                if (colok && row >= 0 && row < rows_in)
+                    x = __ldg(reinterpret_cast<const float2*>(src + (size_t)row * in_pitch));
+                v[m * R0 + q] = x;
+            }
+    }
     r2c_finish<N>(v, sm, t, f, stw, colok, out + (size_t)blockIdx.y * out_img + c, out_pitch, end_scale, mid_scale);
 }
 
