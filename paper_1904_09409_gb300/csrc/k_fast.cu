@@ -363,7 +363,7 @@ k_nvmt_rows_fast(float2* __restrict__ ws, int W, int Hp, int L, const float2* __
 }
 
 template <int N, int INTERP>
-__global__ void __launch_bounds__(fs_T(N) * fs_Brow(N))
+__global__ void __launch_bounds__(fs_T(N) * fs_Brow(N), 1024 / (fs_T(N) * fs_Brow(N)))
 k_nvmt_rows_adjoint_fast(float2* __restrict__ ws, int W, int Hp, int L, const float2* __restrict__ stw) {
     constexpr int B = fs_Brow(N), E = fs_E(N), T = N / E;
     constexpr int R0 = fs_radix(N, 0), G0 = E / R0;

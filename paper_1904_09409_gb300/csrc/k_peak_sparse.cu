@@ -48,12 +48,15 @@ static __host__ __device__ int next_pow2(int v) {
 }
 
 // Shared memory of a block of nw warps: cand[top_k + nw cells / 4],
-// keep[next_pow2(top_k)], list[SP_LIST], then one staged tile with its one-cell
-// halo per warp, (rows + 2) x (cols + 2) floats.
-static size_t sparse_smem(int rows, int cols, int K, int nw) {
+// keep[next_pow2(top_k)], list[SP_LIST], one staged tile with its one-cell halo
+// per warp, (rows + 2) x (cols + 2) floats, then the image's tile maxima when
+// there are at most SP_TM_SMEM tiles (they are read on every selection pass).
+#define SP_TM_SMEM 8192
+static size_t sparse_smem(int rows, int cols, int K, int nw, int ntiles) {
     const size_t cand = (size_t)K + (size_t)nw * rows * cols / 4;
     const size_t stage = (size_t)nw * (rows + 2) * (cols + 2) * sizeof(float);
-    return (cand + next_pow2(K)) * sizeof(u64) + SP_LIST * sizeof(int) + stage;
+    const size_t tms = ntiles <= SP_TM_SMEM ? (size_t)ntiles * sizeof(unsigned) : 0;
+    return (cand + next_pow2(K)) * sizeof(u64) + SP_LIST * sizeof(int) + stage + tms;
 }
 
 
@@ -72,16 +75,22 @@ k_peak_sparse(const float* __restrict__ map, const unsigned* __restrict__ tmax, 
     int* list = reinterpret_cast<int*>(keep + next_pow2(K));
     const int img = blockIdx.x;
     const float* m = map + (size_t)img * Hp * S;
-    const unsigned* tm = tmax + (size_t)img * nty * ntx;
     const int ntiles = nty * ntx;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float* stg = reinterpret_cast<float*>(list + SP_LIST) + (size_t)warp * (TH + 2) * pitch;
+    float* stg0 = reinterpret_cast<float*>(list + SP_LIST);
+    float* stg = stg0 + (size_t)warp * (TH + 2) * pitch;
+    const unsigned* tm = tmax + (size_t)img * nty * ntx;
+    if (ntiles <= SP_TM_SMEM) {                        // the tile maxima, copied once
+        unsigned* tms = reinterpret_cast<unsigned*>(stg0 + (size_t)nw * (TH + 2) * pitch);
+        for (int i = threadIdx.x; i < ntiles; i += blockDim.x) tms[i] = tm[i];
+        tm = tms;                                      // visible after the first selection barrier
+    }
     // test layout: rpp row groups of cw lanes, one column each (TW / cw columns per lane)
     const int cw = min(TW, 32), rpp = 32 / cw, cl = lane & (cw - 1);
 
     // round-1 key of tile i: (M, i) for tiles that reach the threshold, else 0
     auto tkey = [&](int i) -> u64 {
-        const unsigned b = __ldg(tm + i);
+        const unsigned b = tm[i];
         return __uint_as_float(b) >= thr ? ((u64)b << 32) | (u64)(0xFFFFFFFFu - (unsigned)i) : 0ull;
     };
 
@@ -218,7 +227,7 @@ k_peak_sparse(const float* __restrict__ map, const unsigned* __restrict__ tmax, 
             const int j = b0 + warp;
             if (j < nl) {
                 const int tile = list[j];
-                if (__uint_as_float(__ldg(tm + tile)) >= bound) scan_tile(tile, bound);
+                if (__uint_as_float(tm[tile]) >= bound) scan_tile(tile, bound);
             }
             __syncthreads();
             compact();
@@ -243,7 +252,7 @@ k_peak_sparse(const float* __restrict__ map, const unsigned* __restrict__ tmax, 
     bool any = false;
     for (int i = threadIdx.x; i < ntiles && !any; i += blockDim.x) {
         const u64 k = tkey(i);
-        any = k != 0ull && !selected(k, sh.tiles) && __uint_as_float(__ldg(tm + i)) >= sh.bound;
+        any = k != 0ull && !selected(k, sh.tiles) && __uint_as_float(tm[i]) >= sh.bound;
     }
     for (int base = 0; __syncthreads_or(any) && base < ntiles; base += SP_LIST) {
         __syncthreads();
@@ -254,7 +263,7 @@ k_peak_sparse(const float* __restrict__ map, const unsigned* __restrict__ tmax, 
             bool want = false;
             if (i < ntiles) {
                 const u64 k = tkey(i);
-                want = k != 0ull && !selected(k, sh.tiles) && __uint_as_float(__ldg(tm + i)) >= sh.bound;
+                want = k != 0ull && !selected(k, sh.tiles) && __uint_as_float(tm[i]) >= sh.bound;
             }
             const unsigned bal = __ballot_sync(0xffffffffu, want);
             if (bal) {
@@ -346,7 +355,9 @@ static int sparse_warps(int rows, int cols, int top_k) {
     if ((rows * cols) % 32 != 0 || (cols & (cols - 1)) != 0) return 0;
     if (rows * (cols < 32 ? cols : 32) > 64 * 32) return 0;      // a lane's rows fit one 64-bit mask
     for (int nw = 32; nw >= 8; nw /= 2)
-        if (sparse_smem(rows, cols, top_k, nw) + sizeof(SparseShared) <= (size_t)optin) return nw;
+        if (sparse_smem(rows, cols, top_k, nw, 0) + sizeof(SparseShared) + SP_TM_SMEM * sizeof(unsigned) <=
+            (size_t)optin)
+            return nw;
     return 0;
 }
 
@@ -359,7 +370,7 @@ cudaError_t launch_peak_sparse(const float* map, const unsigned* tmax, int Hp, i
     int logTW = 0;
     while ((1 << logTW) < tile_cols) ++logTW;
     const int nty = (Hp + tile_rows - 1) / tile_rows, ntx = (S + tile_cols - 1) / tile_cols;
-    const size_t sm = sparse_smem(tile_rows, tile_cols, top_k, nw);
+    const size_t sm = sparse_smem(tile_rows, tile_cols, top_k, nw, nty * ntx);
     cudaError_t e = cudaFuncSetAttribute(k_peak_sparse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     k_peak_sparse<<<batch, nw * 32, sm, st>>>(map, tmax, Hp, S, tile_rows, logTW, nty, ntx, top_k, threshold, out,
