@@ -111,42 +111,43 @@ k_col_c2r_fast(const float2* __restrict__ in, int ncols, int in_pitch, size_t in
     const bool colok = c < ncols;
 
     // stage the Hermitian half (rows 0 .. N/2, 2B complex each) with 16-byte async
-    // copies; every row is read once and serves both n and N - n
+    // copies; every row is read once and serves both n and N - n.  Thread (t, f)
+    // copies the column pair f of rows t, t + T, ...
     float2* stg = sm;                                  // [N/2 + 1][2B]
     {
-        const int cb = blockIdx.x * 2 * B;
-        const float2* g0 = in + (size_t)blockIdx.y * in_img;
-        for (int idx = threadIdx.x; idx < (N / 2 + 1) * B; idx += blockDim.x) {
-            const int r = idx / B;
-            const int j = idx - r * B;
-            const int col = cb + 2 * j;
-            float2* dst = stg + r * 2 * B + 2 * j;
-            if (col < ncols)
-                cp_async16(dst, g0 + (size_t)r * in_pitch + col);
+        const float2* src = in + (size_t)blockIdx.y * in_img + c + (size_t)t * in_pitch;
+        float2* dst = stg + t * 2 * B + 2 * f;
+        for (int r = t; r <= N / 2; r += fs_T(N), src += (size_t)fs_T(N) * in_pitch, dst += fs_T(N) * 2 * B) {
+            if (colok)
+                cp_async16(dst, src);
             else
                 *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         cp_async_wait_all();
         __syncthreads();
     }
+    // sample n = t + T (m + G0 q) comes from row n when m + G0 q < E/2 and from
+    // row N - n otherwise (the two agree at n = N/2); the end bins 0 and N/2,
+    // which only thread t = 0 holds, enter through their real parts
     float2 v[E];
 #pragma unroll
     for (int m = 0; m < G0; ++m)
 #pragma unroll
         for (int q = 0; q < R0; ++q) {
             const int n = F::template in_pos<0>(t, m, q);
-            const int r = n <= N / 2 ? n : N - n;
-            float4 g = *reinterpret_cast<const float4*>(stg + r * 2 * B + 2 * f);
-            float2 z;
-            if (r == 0 || r == N / 2) {
-                z = make_float2(g.x, g.z);                               // Re A + i Re B
-            } else {
-                g.x *= mid_scale; g.y *= mid_scale; g.z *= mid_scale; g.w *= mid_scale;
-                z = (n <= N / 2) ? make_float2(g.x - g.w, g.y + g.z)      // A + i B
-                                 : make_float2(g.x + g.w, g.z - g.y);     // conj A + i conj B
-            }
-            v[m * R0 + q] = z;
+            const bool up = m + G0 * q < E / 2;
+            float4 g = *reinterpret_cast<const float4*>(stg + (up ? n : N - n) * 2 * B + 2 * f);
+            g.x *= mid_scale; g.y *= mid_scale; g.z *= mid_scale; g.w *= mid_scale;
+            v[m * R0 + q] = up ? make_float2(g.x - g.w, g.y + g.z)      // A + i B
+                               : make_float2(g.x + g.w, g.z - g.y);     // conj A + i conj B
         }
+    if (t == 0) {
+        constexpr int mh = (E / 2) % G0, qh = (E / 2) / G0;          // the element of n = N/2
+        const float4 g0 = *reinterpret_cast<const float4*>(stg + 2 * f);
+        const float4 gh = *reinterpret_cast<const float4*>(stg + (N / 2) * 2 * B + 2 * f);
+        v[0] = make_float2(g0.x, g0.z);                               // Re A + i Re B
+        v[mh * R0 + qh] = make_float2(gh.x, gh.z);
+    }
     __syncthreads();
     F::template run<0>(v, sm, t, f, stw);
     if (tmax) {
