@@ -31,8 +31,7 @@ __device__ __forceinline__ void r2c_finish(float2 (&v)[fs_E(N)], float2* sm, int
         for (int q = 0; q < RL; ++q) sm[spos(F::out_pos(t, m, q)) * B + f] = v[m * RL + q];
     __syncthreads();
     if (!colok) return;
-    auto split = [&](int l, int lm, float s) {
-        const float2 zl = sm[spos(l) * B + f];
+    auto split_z = [&](int l, float2 zl, int lm, float s) {
         const float2 zm = sm[spos(lm) * B + f];
         float4 o;
         o.x = 0.5f * s * (zl.x + zm.x);
@@ -41,11 +40,13 @@ __device__ __forceinline__ void r2c_finish(float2 (&v)[fs_E(N)], float2* sm, int
         o.w = -0.5f * s * (zl.x - zm.x);
         *reinterpret_cast<float4*>(dst + (size_t)l * out_pitch) = o;
     };
+    auto split = [&](int l, int lm, float s) { split_z(l, sm[spos(l) * B + f], lm, s); };
     // thread t writes l = t + T j; only t = 0 meets the end bins 0 and N/2
-    // (N/2 is a multiple of T), so the others need no tests
+    // (N/2 is a multiple of T), so the others need no tests.  Z[t + T j] is the
+    // thread's own output element (j mod GL, j / GL), so only Z[N - l] is read back.
     if (t != 0) {
 #pragma unroll
-        for (int j = 0; j < E / 2; ++j) split(t + T * j, N - t - T * j, mid_scale);
+        for (int j = 0; j < E / 2; ++j) split_z(t + T * j, v[(j % GL) * RL + j / GL], N - t - T * j, mid_scale);
     } else {
         split(0, 0, end_scale);
 #pragma unroll
@@ -184,13 +185,14 @@ k_col_c2r_fast(const float2* __restrict__ in, int ncols, int in_pitch, size_t in
         }
     }
     if (!colok) return;
+    // row n of the result goes to output row n - row0 when that is in range
     float* dst = out + (size_t)blockIdx.y * out_img + c;
 #pragma unroll
     for (int m = 0; m < GL; ++m)
 #pragma unroll
         for (int q = 0; q < RL; ++q) {
             const int rr = F::out_pos(t, m, q) - row0;
-            if (rr >= 0 && rr < rows_out)
+            if ((unsigned)rr < (unsigned)rows_out)
                 *reinterpret_cast<float2*>(dst + (size_t)rr * out_pitch) =
                     make_float2(v[m * RL + q].x * out_scale, v[m * RL + q].y * out_scale);
         }
