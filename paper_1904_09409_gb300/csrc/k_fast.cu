@@ -25,14 +25,20 @@ __device__ __forceinline__ void r2c_finish(float2 (&v)[fs_E(N)], float2* sm, int
     constexpr int RL = fs_radix(N, fs_nst(N) - 1), GL = E / RL;
     using F = FastFft<N, -1, B>;
     F::template run<0>(v, sm, t, f, stw);
+    // Sample t + T j is the thread's element (j mod GL, j / GL).  Thread t != 0
+    // writes l = t + T j (j < E/2) and needs Z[N - l] = Z[(T - t) + T (E - 1 - j)],
+    // element E - 1 - j >= E/2 of thread T - t; thread 0 writes l = T j
+    // (j <= E/2) and needs Z[N - l], its own element E - j (element 0 for l = 0).
+    // So only elements j >= E/2 go through shared memory.
 #pragma unroll
     for (int m = 0; m < GL; ++m)
 #pragma unroll
-        for (int q = 0; q < RL; ++q) sm[spos(F::out_pos(t, m, q)) * B + f] = v[m * RL + q];
+        for (int q = 0; q < RL; ++q)
+            if (m + GL * q >= E / 2) sm[spos(F::out_pos(t, m, q)) * B + f] = v[m * RL + q];
     __syncthreads();
     if (!colok) return;
-    auto split_z = [&](int l, float2 zl, int lm, float s) {
-        const float2 zm = sm[spos(lm) * B + f];
+    auto el = [&](int j) -> float2 { return v[(j % GL) * RL + j / GL]; };
+    auto split_z = [&](int l, float2 zl, float2 zm, float s) {
         float4 o;
         o.x = 0.5f * s * (zl.x + zm.x);
         o.y = 0.5f * s * (zl.y - zm.y);
@@ -40,18 +46,16 @@ __device__ __forceinline__ void r2c_finish(float2 (&v)[fs_E(N)], float2* sm, int
         o.w = -0.5f * s * (zl.x - zm.x);
         *reinterpret_cast<float4*>(dst + (size_t)l * out_pitch) = o;
     };
-    auto split = [&](int l, int lm, float s) { split_z(l, sm[spos(l) * B + f], lm, s); };
-    // thread t writes l = t + T j; only t = 0 meets the end bins 0 and N/2
-    // (N/2 is a multiple of T), so the others need no tests.  Z[t + T j] is the
-    // thread's own output element (j mod GL, j / GL), so only Z[N - l] is read back.
+    // only t = 0 meets the end bins 0 and N/2 (N/2 is a multiple of T)
     if (t != 0) {
 #pragma unroll
-        for (int j = 0; j < E / 2; ++j) split_z(t + T * j, v[(j % GL) * RL + j / GL], N - t - T * j, mid_scale);
+        for (int j = 0; j < E / 2; ++j)
+            split_z(t + T * j, el(j), sm[spos(N - t - T * j) * B + f], mid_scale);
     } else {
-        split(0, 0, end_scale);
+        split_z(0, el(0), el(0), end_scale);
 #pragma unroll
-        for (int j = 1; j < E / 2; ++j) split(T * j, N - T * j, mid_scale);
-        split(N / 2, N / 2, end_scale);
+        for (int j = 1; j < E / 2; ++j) split_z(T * j, el(j), el(E - j), mid_scale);
+        split_z(N / 2, el(E / 2), el(E / 2), end_scale);
     }
 }
 
