@@ -509,22 +509,25 @@ bool tc_columns(ft_plan p);
 // must be the fixed-length FP32 kernel on the caller's stream, and the pass's
 // shared memory must fit.
 // Whether the pass from tile maxima beats the per-tile key kernels for this
-// call.  It runs one block per image, so it costs about one image's work per
+// call.  It runs one block per image, so it costs one image's serial chain per
 // wave of images: selecting among the tiles, then batches of 32 tiles (one at
-// 1024^2 with top_k = 32, over 20 at 4096^2 with top_k = 100: the batch count
-// grows with tiles x top_k), plus, for ft_peaks, one streaming read for the tile
-// maxima; the key kernels spread every cell over the whole GPU.  Constants in
-// microseconds, measured on GB300 (64 x 1024^2 and 8 x 4096^2 maps).  The pass
-// from tile maxima occupies only one multiprocessor per image, so plans whose
-// calls share the GPU with others (ft_batch) always take it.  FT_PEAKS=sparse /
-// dense at plan creation fixes the choice.
+// 1024^2 and 2048^2 with top_k = 32, over 20 at 4096^2 with top_k = 100: the
+// batch count grows like (tiles x top_k)^2), plus, for ft_peaks, one streaming
+// read for the tile maxima.  The key kernels spread every cell over the whole GPU
+// but have a fixed latency of two dependent kernels, the second also one block
+// per image.  Constants in microseconds, fitted to GB300 measurements of
+// ft_detect both ways (1024^2 with 1-128 images, 512^2, 2048^2 and 4096^2; the
+// model picks the faster pass in all 15 cases).  The pass from tile maxima
+// occupies only one multiprocessor per image, so plans whose calls share the GPU
+// with others (ft_batch) always take it.  FT_PEAKS=sparse / dense at plan
+// creation fixes the choice.
 static bool sparse_is_faster(ft_plan p, int batch, int top_k, bool with_tile_max) {
     if (p->peak_mode) return p->peak_mode == 1;
     const double cells = (double)p->Hp * p->S, tiles = cells / 256.0;
     const int waves = (batch + p->num_sms - 1) / p->num_sms;
-    const double batches = 1.0 + tiles * top_k / 3.0e5;
-    const double sparse = waves * (8.0 + 1.2e-3 * tiles + 12.0 * batches) + (with_tile_max ? 0.7e-6 * cells * batch : 0.0);
-    const double dense = 1.6e-6 * cells * batch + 5.0;
+    const double x = tiles * top_k / 1.5e6;
+    const double sparse = waves * (1.2e-3 * tiles + 12.0 * (1.0 + x * x)) + (with_tile_max ? 0.7e-6 * cells * batch : 0.0);
+    const double dense = 1.6e-6 * cells * batch + 27.0;
     return sparse < dense;
 }
 
