@@ -502,7 +502,7 @@ int ft_peaks_launches(ft_plan p, int batch) {
 }
 
 // split precision: the length-4096 column transforms on the tensor cores too
-bool tc_columns(ft_plan p);
+static bool tc_columns(ft_plan p);
 
 // The tile shape of ft_detect's peak pass (the tiles whose maxima step 4
 // writes), or false when ft_detect runs ft_forward and ft_peaks instead: step 4
@@ -571,7 +571,7 @@ int ft_detect_launches(ft_plan p, int batch, int top_k) {
 
 // split precision: the length-4096 column transforms on the tensor cores too,
 // through a column-major copy (cm) so that their column pairs are contiguous rows
-bool tc_columns(ft_plan p) { return p->precision != FT_PRECISION_FP32 && p->Hp == 4096; }
+static bool tc_columns(ft_plan p) { return p->precision != FT_PRECISION_FP32 && p->Hp == 4096; }
 static size_t cm_elems(ft_plan p) {
     const size_t a = (size_t)p->H * p->W, b = (size_t)p->Hp * p->S;
     return a > b ? a : b;
