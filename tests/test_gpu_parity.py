@@ -152,7 +152,7 @@ def test_peaks_exact_with_ties(torch, peak_mode, Hp, S, K):
 
 
 @pytest.mark.parametrize("K", [32, 513, 1024])
-@pytest.mark.parametrize("Hp,S", [(256, 192), (256, 256)])     # generic and register-only tiles
+@pytest.mark.parametrize("Hp,S", [(256, 192), (256, 256)])     # per-tile key pass: generic and register tiles
 def test_peaks_exact_large_k(torch, peak_mode, K, Hp, S):
     rng = np.random.default_rng(K)
     maps = rng.standard_normal((2, Hp, S)).astype(np.float32)
@@ -178,7 +178,7 @@ def test_peaks_exact_appended_key_lists(torch, peak_mode, K, thr):
         assert got[i] == ref, i
 
 
-@pytest.mark.parametrize("Hp,S", [(256, 256), (256, 192)])     # 32 x 128 and 32 x 64 tiles
+@pytest.mark.parametrize("Hp,S", [(256, 256), (256, 192)])     # per-tile key pass: 32 x 128 and 32 x 64 tiles
 def test_peaks_dense_tile_with_k_1024(torch, peak_mode, Hp, S):
     """Every (even, even) cell a strict local maximum (1024 in a 32 x 128 tile,
     the most a tile can hold), one tile much brighter than the rest: the top
@@ -197,12 +197,12 @@ def test_peaks_dense_tile_with_k_1024(torch, peak_mode, Hp, S):
 # peak pass reads only the tiles that can hold one of the top_k.  H, W, S, H',
 # top_k, threshold; the c2r tile of each H' in the comment.
 DETECT_CASES = [
-    (256, 256, 256, 256, 3, float("-inf")),      # 16 x 64 tiles, the single-image workload
-    (1024, 1024, 1024, 1024, 32, float("-inf")),  # 64 x 16 tiles, the batch workload
-    (200, 200, 216, 256, 40, float("-inf")),      # S = 216 ragged against 64-column tiles
-    (100, 96, 96, 192, 17, float("-inf")),        # H' = 192: 12 bands of 16 rows
-    (128, 200, 216, 4096, 100, float("-inf")),    # 256 x 8 tiles, ragged S
-    (64, 16, 16, 8192, 5, float("-inf")),         # 512 x 4 tiles
+    (256, 256, 256, 256, 3, float("-inf")),      # 8 x 32 tiles, the single-image workload
+    (1024, 1024, 1024, 1024, 32, float("-inf")),  # 32 x 8 tiles, the batch workload
+    (200, 200, 216, 256, 40, float("-inf")),      # S = 216 ragged against 32-column tiles
+    (100, 96, 96, 192, 17, float("-inf")),        # H' = 192 (3-smooth): 8 x 32 tiles
+    (128, 200, 216, 4096, 100, float("-inf")),    # 32 x 8 tiles, expansion H' > H
+    (64, 16, 16, 8192, 5, float("-inf")),         # 64 x 4 tiles
     (256, 256, 256, 256, 1024, float("-inf")),    # top_k above the number of tiles
     (256, 256, 256, 256, 64, 30.0),               # a threshold few peaks pass
     (48, 40, 64, 72, 8, float("-inf")),           # H' = 72 has no fixed-length kernel: forward + peaks
