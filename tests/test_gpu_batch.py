@@ -111,3 +111,34 @@ def test_autotuner_and_cache(torch, tmp_path):
     assert len(entries) == len(tuned)
     with f.Batch(SHAPES, tune_cache=cache) as b2:          # choices come back from the cache
         assert {(g["H"], g["W"]): g["variant"] for g in b2.groups()} == tuned
+
+
+LARGE_SHAPES = [(2048, 2048), (1536, 1536), (2048, 1536), (1536, 2048), (128, 2048), (2048, 128),
+                (768, 1536), (1536, 768), (2048, 2048)]
+
+
+def test_batch_with_1536_and_2048_matches_oracle(torch):
+    """The mixed-size workload's longest sides (the fixed-length schedules of
+    1536 = 4^4 * 2 * 3 and 2048 = 16 * 16 * 8) in one batch: every map against
+    the FP64 oracle, every peak list against the oracle's list procedure on the
+    same FP32 map."""
+    from paper_1904_09409_gb300 import funnel as f
+    imgs = [synth.varlen_image(500 + i, h, w).img for i, (h, w) in enumerate(LARGE_SHAPES)]
+    with f.Batch(LARGE_SHAPES) as b:
+        x = torch.from_numpy(b.pack(imgs)).cuda()
+        m = torch.full((b.map_total,), float("nan"), device="cuda")
+        out = torch.zeros(b.n * TOP_K * f.PEAK_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        cnt = torch.zeros(b.n, dtype=torch.int32, device="cuda")
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            b.run(x, m, TOP_K, out=out, count=cnt, stream=s)
+        s.synchronize()
+        maps = b.unpack_maps(m.cpu().numpy())
+        recs = out.cpu().numpy().view(f.PEAK_DTYPE).reshape(b.n, TOP_K)
+        cnts = cnt.cpu().numpy()
+        order = list(b.order)
+    for j, i in enumerate(order):
+        h, w = LARGE_SHAPES[i]
+        assert _gpu.rel_l2(maps[i], oracle.funnel_ref(imgs[i], w, h)) <= 1e-5, (h, w)
+        got = [(int(r["t"]), int(r["s"]), float(r["value"])) for r in recs[j, :cnts[j]]]
+        assert got == oracle.peaks_ref(np.abs(maps[i]).astype(np.float64), TOP_K), (h, w)

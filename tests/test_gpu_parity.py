@@ -59,6 +59,11 @@ FORWARD_CASES = [
     (384, 384, 384, 384),
     (200, 300, 384, 512),  # W not a multiple of the column block
     (768, 768, 768, 768),
+    (1536, 1536, 1536, 1536),  # fixed-length schedules of the mixed-size workload: 4^4 * 2 * 3
+    (2048, 2048, 2048, 2048),  # 16 * 16 * 8
+    (1000, 1536, 2048, 1536),  # expansion to 1536 rows, zero insertion to 2048 slopes
+    (2048, 128, 128, 2048),    # tall: length-2048 columns, length-128 rows
+    (128, 2048, 2048, 128),    # wide: length-128 columns, length-2048 rows
     (64, 16, 16, 8192),    # longest column transform
     (8, 16, 8192, 8),      # longest row transform
 ]
@@ -78,7 +83,8 @@ def test_forward_matches_oracle(torch, H, W, S, Hp):
 
 
 @pytest.mark.parametrize("H,W,S,Hp", [(32, 32, 32, 32), (48, 40, 64, 72), (256, 256, 256, 256),
-                                      (128, 96, 192, 144)])
+                                      (128, 96, 192, 144), (1536, 1536, 1536, 1536), (2048, 2048, 2048, 2048),
+                                      (1000, 1536, 2048, 1536)])
 def test_forward_cubic_matches_oracle(torch, H, W, S, Hp):
     imgs = inputs(H, W, 2, seed=99)
     with make_plan(H, W, S, Hp, "cubic") as plan:
@@ -331,7 +337,9 @@ def test_peaks_fewer_than_k(torch, peak_mode):
 # ----------------------------------------------------------------- adjoint
 @pytest.mark.parametrize("H,W,S,Hp,interp", [(32, 32, 32, 32, "linear"), (48, 40, 64, 72, "linear"),
                                              (48, 40, 64, 72, "cubic"), (256, 256, 256, 256, "linear"),
-                                             (100, 96, 96, 192, "cubic")])
+                                             (100, 96, 96, 192, "cubic"), (1536, 1536, 1536, 1536, "linear"),
+                                             (2048, 2048, 2048, 2048, "cubic"), (1000, 1536, 2048, 1536, "linear"),
+                                             (2048, 128, 128, 2048, "cubic")])
 def test_backward_matches_oracle_adjoint(torch, H, W, S, Hp, interp):
     rng = np.random.default_rng(H + W)
     g = rng.standard_normal((2, Hp, S)).astype(np.float32)

@@ -169,3 +169,51 @@ def test_planted_verification_mistake_is_caught(name, old, new):
         assert not _verification_pins_hold(ns["band_profile"]), name
         return
     assert not _verification_pins_hold(_mutant(old, new)), name
+
+
+# ------------------------------------------------ Keys' cubic kernel (step 2)
+import importlib                                                   # noqa: E402
+fd = importlib.import_module("oracle.funnel_direct")
+from tests._keys import keys_failures                               # noqa: E402
+
+
+def _keys_mutant(old, new):
+    """keys_cubic with one piece of its source replaced."""
+    src = inspect.getsource(fr.keys_cubic)
+    assert old in src, old
+    ns = dict(fr.__dict__)
+    exec(src.replace(old, new), ns)
+    return ns["keys_cubic"]
+
+
+def test_unmutated_keys_kernels_pass():
+    assert keys_failures(fr.keys_cubic) == []
+    assert keys_failures(np.vectorize(fd._keys)) == []
+
+
+@pytest.mark.parametrize("name,old,new", [
+    ("a = -0.75", "a: float = KEYS_A", "a: float = -0.75"),
+    ("8a term typed as 6a", "8.0 * a * s[m2]", "6.0 * a * s[m2]"),
+    ("(a + 2) and (a + 3) swapped", "(a + 2.0) * s[m1] ** 3 - (a + 3.0)", "(a + 3.0) * s[m1] ** 3 - (a + 2.0)"),
+    ("outer piece sign of 4a", "- 4.0 * a", "+ 4.0 * a"),
+    ("outer piece on |s| <= 3", "(s > 1.0) & (s < 2.0)", "(s > 1.0) & (s < 3.0)"),
+])
+def test_planted_keys_mistake_is_caught(name, old, new):
+    assert keys_failures(_keys_mutant(old, new)), name
+
+
+def test_planted_cubic_tap_order_is_caught(monkeypatch):
+    """Weights attached to the wrong taps (k(f) and k(f + 1) exchanged) break the
+    Catmull-Rom / quadratic-reproduction pin of step 2."""
+    orig = fr.interp_weights
+
+    def swapped(i0, frac, interp):
+        taps, w = orig(i0, frac, interp)
+        if interp == "cubic":
+            w = w[:, [1, 0, 2, 3]]
+        return taps, w
+
+    monkeypatch.setattr(fr, "interp_weights", swapped)
+    from tests import test_oracle_pins as pins
+    with pytest.raises(AssertionError):
+        pins.test_cubic_nvmt_row_is_catmull_rom_and_exact_on_quadratics()

@@ -124,6 +124,44 @@ def test_nyquist_row_is_identity_resampling():
         assert np.all(V[0] == 0)
 
 
+@pytest.mark.parametrize("which", ["transform.keys_cubic", "funnel_direct._keys"])
+def test_keys_kernel_properties(which):
+    """Keys' kernel with a = -1/2 (the cubic interpolator of step 2), in both
+    oracle forms: interpolating, even, support |s| < 2, partition of unity,
+    exact on linear and quadratic sequences, C1 at |s| = 0, 1, 2, and equal
+    to the Catmull-Rom spline (midpoint weights -1/16, 9/16, 9/16, -1/16)."""
+    import importlib
+    from tests._keys import keys_failures
+    fd = importlib.import_module("oracle.funnel_direct")
+    k = fr.keys_cubic if which.startswith("transform") else np.vectorize(fd._keys)
+    assert keys_failures(k) == []
+
+
+def test_cubic_nvmt_row_is_catmull_rom_and_exact_on_quadratics():
+    """Step 2 with the cubic interpolator: wherever the four taps lie inside the
+    row, the sample at p = x' H' / (2 l) is the Catmull-Rom spline through the
+    row at p, and a quadratic row a + b x + c x^2 comes out as a + b p + c p^2."""
+    from tests._keys import catmull_rom
+    W, S, Hp = 24, 40, 36
+    xs = np.arange(W) - W // 2
+    row = RNG.standard_normal(W) + 1j * RNG.standard_normal(W)
+    quad = 0.3 - 1.7 * xs + 0.25 * xs ** 2 + 0j
+    checked = 0
+    for l in (5, 9, 13, 18):
+        i0, frac = fr.nvmt_positions(l, S, Hp)
+        V = fr.nvmt_row(row, l, S, Hp, "cubic")
+        Q = fr.nvmt_row(quad, l, S, Hp, "cubic")
+        inside = (i0 - 1 >= -W // 2) & (i0 + 2 <= W // 2 - 1)
+        checked += int(inside.sum())
+        c = i0 + W // 2
+        for j in np.flatnonzero(inside):
+            cr = catmull_rom(row[c[j] - 1], row[c[j]], row[c[j] + 1], row[c[j] + 2], frac[j])
+            assert abs(V[j] - cr) <= 1e-12
+            p = (j - S // 2) * Hp / (2.0 * l)
+            assert abs(Q[j] - (0.3 - 1.7 * p + 0.25 * p * p)) <= 1e-9
+    assert checked >= 40
+
+
 def test_linearity():
     H, W, S, Hp = 16, 16, 20, 24
     a, b = RNG.standard_normal((2, H, W))
