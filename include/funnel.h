@@ -200,15 +200,21 @@ ft_status ft_detect_host(ft_plan plan, const float* h_img, int batch, int top_k,
  * written to d_out ([batch][top_k]) and d_count ([batch]), but no plan is
  * needed and nothing is allocated: the per-tile keys go to one fixed array of
  * FT_NOALLOC_SCRATCH_BYTES bytes inside the library, which every GPU that loads
- * libfunnel.so holds until the process exits.  A call whose keys would not fit
- * (about batch x ceil(n_intercept/32) x ceil(n_slope/64) x min(top_k, 512) x 8
- * bytes; 64 maps of 1024 x 1024 with top_k = 32 use 8 MiB) returns
- * FT_ERR_UNSUPPORTED_SIZE and ft_last_error() says why.
+ * libfunnel.so holds until the process exits.  A call needs at most
+ * batch x ceil(n_intercept/32) x ceil(n_slope/64) x min(top_k, 512) x 8 bytes
+ * plus 8 bytes per map (an upper bound for both tile kinds: maps with
+ * n_slope % 128 == 0 and n_intercept % 32 == 0 use tiles of 32 or 64 x 128
+ * cells keeping min(top_k, 32 x rows) keys each, i.e. at most half of it;
+ * 64 maps of 1024 x 1024 with top_k = 32 use 2 MiB).  A call whose keys would
+ * not fit returns FT_ERR_UNSUPPORTED_SIZE and ft_last_error() says why.
  *
- * The first call on a device looks up the array's device address (once per
- * device, under a lock); make that first call before any stream capture.  All
- * calls share the one array, so calls whose work overlaps on the GPU (other
- * streams, other threads) race on it; calls in order on one stream are safe.
+ * The first call in a CUDA context looks up the array's device address in that
+ * context (under a lock; again after cudaDeviceReset or in another context on
+ * the same device, since the address belongs to the context); make that first
+ * call before any stream capture.  Later calls issue only stream work
+ * (a cudaMemsetAsync and two kernel launches).  All calls share the one array,
+ * so calls whose work overlaps on the GPU (other streams, other threads) race
+ * on it; calls in order on one stream are safe.
  * n_intercept, n_slope >= 2; 1 <= top_k <= FT_MAX_TOPK; threshold not NaN. */
 #define FT_NOALLOC_SCRATCH_BYTES (16u << 20)
 ft_status ft_peaks_noalloc(const float* d_map, int n_intercept, int n_slope, int batch, int top_k,

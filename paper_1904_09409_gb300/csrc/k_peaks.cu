@@ -15,12 +15,13 @@
 //                 512 per tile; neighbour indices are computed only to break exact
 //                 ties), and keep the best min(top_k, 512) by radix selection.
 //  k_peak_tiles_fast  the same for maps with S % 128 == 0 and H' % 32 == 0, one
-//                 block per 32 x 128 tile (image index fastest in the grid): the
+//                 block per tile of 64 x 128 cells (32 x 128 when H' is not a
+//                 multiple of 64; image index fastest in the grid): the
 //                 tile and its halo are copied with cp.async, each lane tests 4
 //                 columns of 4 rows against the max of their 8 neighbours (exact
 //                 ties alone take the index comparison), candidates are appended
-//                 per warp with one scan (at most 1024 per tile).  The tile's best
-//                 min(top_k, 512) keys go to the tile's own slots or, for large
+//                 per warp with one scan (at most rows x 32 per tile).  The tile's
+//                 best min(top_k, rows x 32) keys go to the tile's own slots or, for large
 //                 maps, are appended to the image's key list (one atomic per
 //                 tile); a per-image running bound of the top_k-th value lets
 //                 later tiles drop dimmer candidates early.

@@ -9,11 +9,13 @@
 // workspace, which it may grow with cudaMalloc.  This entry point instead uses
 // the fixed array below, which the library image holds on every GPU that loads
 // it until the process exits, and needs no plan at all.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "ft_internal.cuh"
 
-#define FT_NOALLOC_MAX_DEVICES 64
+#define FT_NOALLOC_CACHE 64
 
 // Scratch for the per-tile keys and one running bound per map.  Every call
 // writes all the key slots it reads (padding included) and clears the bounds
@@ -22,25 +24,70 @@
 // overlaps on the GPU (other streams, or other host threads) race on it.
 static __device__ __align__(256) unsigned char g_peak_scratch[FT_NOALLOC_SCRATCH_BYTES];
 
-static std::mutex g_setup_mutex;
-static void* g_scratch_addr[FT_NOALLOC_MAX_DEVICES];
+// The array's device address belongs to the module loaded in one CUDA context:
+// a cudaDeviceReset, or another context made current on the same device, gives
+// it another address.  The cache is therefore keyed by the context's unique id
+// (cuCtxGetId, never reused within a process), not by the device ordinal.
+typedef CUresult (*ctx_current_fn)(CUcontext*);
+typedef CUresult (*ctx_id_fn)(CUcontext, unsigned long long*);
 
-// Device address of g_peak_scratch on the current device, looked up once per
-// device.  In host code the symbol names a host-side stand-in, so the address
-// must come from cudaGetSymbolAddress with the device current.
-static cudaError_t scratch_address(void** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= FT_NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_peak_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
+static std::mutex g_setup_mutex;
+static ctx_current_fn g_ctx_current = nullptr;
+static ctx_id_fn g_ctx_id = nullptr;
+static unsigned long long g_cache_ctx[FT_NOALLOC_CACHE];
+static void* g_cache_addr[FT_NOALLOC_CACHE];
+static int g_cache_next = 0;
+
+// Id of the current context (the device's primary context is created first if
+// no context is current).  Host-side queries only: no stream work, so it is
+// also safe while a stream is being captured.
+static cudaError_t current_context_id(unsigned long long* id) {
+    {
+        std::lock_guard<std::mutex> lock(g_setup_mutex);
+        if (!g_ctx_current || !g_ctx_id) {
+            cudaDriverEntryPointQueryResult q1, q2;
+            void *f1 = nullptr, *f2 = nullptr;
+            cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+            if (e == cudaSuccess) e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+            if (e != cudaSuccess) return e;
+            if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+                return cudaErrorNotSupported;
+            g_ctx_current = (ctx_current_fn)f1;
+            g_ctx_id = (ctx_id_fn)f2;
+        }
     }
-    *out = g_scratch_addr[dev];
+    CUcontext ctx = nullptr;
+    if (g_ctx_current(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+    if (!ctx) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaSetDevice(dev);      // creates the primary context
+        if (e != cudaSuccess) return e;
+        if (g_ctx_current(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorDeviceUninitialized;
+    }
+    return g_ctx_id(ctx, id) == CUDA_SUCCESS ? cudaSuccess : cudaErrorDeviceUninitialized;
+}
+
+// Device address of g_peak_scratch in the current context, looked up once per
+// context.  In host code the symbol names a host-side stand-in, so the address
+// must come from cudaGetSymbolAddress with that context current.
+static cudaError_t scratch_address(void** out) {
+    unsigned long long id = 0;
+    cudaError_t e = current_context_id(&id);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    for (int i = 0; i < FT_NOALLOC_CACHE; ++i)
+        if (g_cache_addr[i] && g_cache_ctx[i] == id) {
+            *out = g_cache_addr[i];
+            return cudaSuccess;
+        }
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_peak_scratch);
+    if (e != cudaSuccess) return e;
+    g_cache_ctx[g_cache_next] = id;
+    g_cache_addr[g_cache_next] = p;
+    g_cache_next = (g_cache_next + 1) % FT_NOALLOC_CACHE;
+    *out = p;
     return cudaSuccess;
 }
 

@@ -306,17 +306,27 @@ def ft_peaks_noalloc(fmap, top_k: int, threshold: float = float("-inf"), out=Non
     """ft_peaks without a plan and without any device allocation inside the
     library (fixed scratch of FT_NOALLOC_SCRATCH_BYTES).  fmap: (batch, H', S)
     CUDA float32.  Returns (peaks, count) like ft_peaks; pass preallocated
-    ``out``/``count`` to avoid allocations on the Python side too."""
+    ``out``/``count`` to avoid allocations on the Python side too.  The call
+    runs with fmap's device current (on ``stream``, by default that device's
+    current stream); ``out`` and ``count`` must be on the same device."""
     import torch
+    if not isinstance(fmap, torch.Tensor) or not fmap.is_cuda:
+        raise TypeError("map must be a CUDA tensor")
+    dev = fmap.device
+    for t, what in ((out, "out"), (count, "count")):
+        if t is not None and (not isinstance(t, torch.Tensor) or t.device != dev):
+            raise TypeError(f"{what} must be a CUDA tensor on the map's device {dev}")
     b, Hp, S = (int(v) for v in fmap.shape)
-    mp = _dev_ptr(fmap, "float32", b * Hp * S, "map")
-    if out is None:
-        out = torch.empty(b * top_k * PEAK_DTYPE.itemsize, dtype=torch.uint8, device=fmap.device)
-    if count is None:
-        count = torch.empty(b, dtype=torch.int32, device=fmap.device)
-    op = _dev_ptr(out, "uint8", b * top_k * PEAK_DTYPE.itemsize, "out")
-    cp = _dev_ptr(count, "int32", b, "count")
-    st = lib().ft_peaks_noalloc(mp, Hp, S, b, int(top_k), float(threshold), op, cp, _stream_ptr(stream))
+    with torch.cuda.device(dev):
+        mp = _dev_ptr(fmap, "float32", b * Hp * S, "map")
+        if out is None:
+            out = torch.empty(b * top_k * PEAK_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        if count is None:
+            count = torch.empty(b, dtype=torch.int32, device=dev)
+        op = _dev_ptr(out, "uint8", b * top_k * PEAK_DTYPE.itemsize, "out")
+        cp = _dev_ptr(count, "int32", b, "count")
+        sp = torch.cuda.current_stream(dev).cuda_stream if stream is None else _stream_ptr(stream)
+        st = lib().ft_peaks_noalloc(mp, Hp, S, b, int(top_k), float(threshold), op, cp, sp)
     if st == FT_ERR_UNSUPPORTED_SIZE:
         raise FunnelError(st, "ft_peaks_noalloc", ft_last_error())
     _check(st, "ft_peaks_noalloc")

@@ -65,3 +65,45 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(torch):
     with pytest.raises(f.FunnelError, match="FT_NOALLOC_SCRATCH_BYTES"):
         # 2 maps of 2048 x 8192 with top-512: 2 x 64 x 128 tiles x 512 keys x 8 B = 64 MiB
         f.ft_peaks_noalloc(torch.zeros((2, 2048, 8192), device="cuda"), 512)
+
+
+def test_noalloc_after_device_reset():
+    """The scratch array's device address belongs to one CUDA context; after
+    cudaDeviceReset the next call must look it up again in the new context.
+    Runs in a child process (the reset would invalidate this process's torch
+    memory)."""
+    import os
+    import subprocess
+    import sys
+    _gpu.torch_cuda()                                   # builds the library if needed
+    child = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_noalloc_reset_child.py")
+    r = subprocess.run([sys.executable, child], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.strip().endswith("OK"), r.stdout + r.stderr
+
+
+def test_noalloc_inside_stream_capture(torch):
+    """One warm-up call, then a call captured into a CUDA graph on a static map;
+    the graph replayed on new map contents gives ft_peaks' result byte for byte."""
+    from paper_1904_09409_gb300 import funnel as f
+    Hp, S, batch, K = 512, 384, 3, 40
+    rng = np.random.default_rng(3)
+    m = torch.from_numpy(rng.standard_normal((batch, Hp, S)).astype(np.float32)).cuda()
+    out = torch.zeros(batch * K * f.PEAK_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(batch, dtype=torch.int32, device="cuda")
+    f.ft_peaks_noalloc(m, K, out=out, count=cnt)        # warm-up before any capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        f.ft_peaks_noalloc(m, K, out=out, count=cnt)
+    new = rng.standard_normal((batch, Hp, S)).astype(np.float32)
+    m.copy_(torch.from_numpy(new).cuda())
+    out.fill_(0xAB)
+    cnt.fill_(-1)
+    g.replay()
+    torch.cuda.synchronize()
+    with f.Plan(Hp, S, S, Hp) as plan:
+        ref_out, ref_cnt = f.ft_peaks(plan, m, K)
+        torch.cuda.synchronize()
+    assert torch.equal(cnt, ref_cnt)
+    assert torch.equal(out, ref_out)
