@@ -57,7 +57,7 @@ typedef enum {
     FT_ERR_UNSUPPORTED_SIZE = 2, /* odd / non 2^a 3^b / too large / n_slope < W ... */
     FT_ERR_OOM = 3,              /* a device or host allocation failed */
     FT_ERR_CUDA = 4,             /* a CUDA runtime call or launch failed */
-    FT_ERR_TIMEOUT = 5           /* reserved for bounded waits */
+    FT_ERR_TIMEOUT = 5           /* a bounded device-side wait gave up (ft_plan_tc_errors) */
 } ft_status;
 
 /* Step 2 interpolator.  Sec. IV adopts a chirp-z (band-limited) interpolator,
@@ -309,10 +309,32 @@ ft_status ft_plan_set_precision(ft_plan plan, int precision);
 int ft_plan_get_precision(ft_plan plan);
 
 /* Error flags of the plan's tensor-core kernels: bit 0 is set when a wait for
- * the tensor cores timed out (about 2 s; the kernel then stops and its rows are
- * incomplete).  Waits for all work on the plan's device, copies the flags to
- * *flags (host) and clears them.  0 when no split precision was ever set. */
+ * the tensor cores timed out (after ft_plan_get_wait_cycles SM cycles, about
+ * 2 s by default).  A row group whose wait gave up sets the bit, waits for its
+ * own issued MMAs with the default bound, frees its tensor memory with the rest
+ * of its block and stops, so the rows it had not finished are left incomplete;
+ * the CUDA context stays usable.  Waits for all work on the plan's device,
+ * copies the flags to *flags (host) and clears them; returns FT_ERR_TIMEOUT
+ * when bit 0 was set (ft_last_error() says so), FT_OK otherwise (flags 0 when
+ * no split precision was ever set). */
 ft_status ft_plan_tc_errors(ft_plan plan, uint32_t* flags);
+
+/* Bound, in SM cycles, of every wait of the plan's tensor-core kernels for
+ * their GEMMs (FT_WAIT_CYCLES_DEFAULT, about 2 s at 2 GHz, after creation).
+ * The limit is checked before each try, so 0 makes every such wait give up at
+ * once: a test setting that runs the timeout path (flag, drain, free, stop)
+ * without any GPU fault.  cycles < 0 is FT_ERR_INVALID_ARG.  Changes later
+ * calls only. */
+#define FT_WAIT_CYCLES_DEFAULT 4000000000ll
+ft_status ft_plan_set_wait_cycles(ft_plan plan, int64_t cycles);
+int64_t ft_plan_get_wait_cycles(ft_plan plan);
+
+/* Failure injection for tests of the error paths: the next `count` device
+ * allocations of this plan's workspace or host-path buffers fail as an
+ * out-of-memory cudaMalloc would (the call returns FT_ERR_OOM, ft_last_error()
+ * names the buffer, nothing is launched); count = 0 clears it.  The plan stays
+ * usable: the next call allocates again. */
+ft_status ft_plan_inject_alloc_failures(ft_plan plan, int count);
 
 /* Line verification (Sec. 4.5, steps 1-4) of detected peaks.  For peak j of
  * image b (d_peaks[b * top_k + j], j < d_count[b], as written by ft_peaks on

@@ -12,6 +12,9 @@
 
 #define FT_MAX_STAGES 16
 #define FT_THREADS 256
+// a wait for the tensor cores that has not completed after this many SM cycles
+// (about 2 s) gives up (ft_plan_set_wait_cycles changes it per plan)
+#define FT_WAIT_CYCLES 4000000000ll
 
 // One FFT length N = 2^a 3^b: its radix sequence and twiddle table
 // tw[t] = exp(-2 pi i t / N), t in [0, N), rounded to FP32 from FP64 values.
@@ -217,6 +220,8 @@ struct ft_plan_s {
     int num_sms;            // multiprocessors of the plan's device
     int precision;          // ft_precision of step 3 (ft_plan_set_precision)
     unsigned* d_tc_err;     // error flags of the tensor-core kernels (allocated with the first split precision)
+    long long tc_wait;      // bound of every tensor-core wait in SM cycles (ft_plan_set_wait_cycles)
+    int alloc_failures;     // device allocations still to fail (ft_plan_inject_alloc_failures)
     // band-limited (chirp-z) interpolator: lengths W and M >= W + S, chirp tables
     FftLen fw, fm;
     float2* d_chirp;        // [L][W+1] pre-chirps, [L][S] post-chirps, [L][M] chirp spectra
@@ -324,12 +329,13 @@ cudaError_t tc_prepare();
 // launch_col_c2r with mid scale 1 and out scale 1/H', but the map written
 // column-major [batch][S][H'])
 // (prec: FT_PRECISION_BF16X3, _FP16X3 or _BF16X6)
-cudaError_t launch_nvmt_rows_tc4096(float2* ws, int W, int Hp, int L, int interp, int prec, unsigned* err, int batch,
-                                    cudaStream_t st);
+// (wait: the bound of every wait for the tensor cores, in SM cycles)
+cudaError_t launch_nvmt_rows_tc4096(float2* ws, int W, int Hp, int L, int interp, int prec, unsigned* err,
+                                    long long wait, int batch, cudaStream_t st);
 cudaError_t launch_col_r2c_tc4096(const float* img_cm, int H, int W, int row0, float2* ws, int L, int S, int prec,
-                                  unsigned* err, int batch, cudaStream_t st);
-cudaError_t launch_col_c2r_tc4096(const float2* ws, int L, int S, float* map_cm, int prec, unsigned* err, int batch,
-                                  cudaStream_t st);
+                                  unsigned* err, long long wait, int batch, cudaStream_t st);
+cudaError_t launch_col_c2r_tc4096(const float2* ws, int L, int S, float* map_cm, int prec, unsigned* err,
+                                  long long wait, int batch, cudaStream_t st);
 
 // line verification of Sec. 4.5 (k_verify.cu): image element (v, u) of the
 // transform's frame at img[v * stride_v + u * stride_u] (image b at b * img_stride)

@@ -358,6 +358,7 @@ struct TcArgs {
     float* map;             // TCM_C2R output, column-major [batch][S][H']
     int W, H, Hp, L, S, row0, total;
     unsigned* err;
+    long long wait;         // bound of each wait for the GEMMs, SM cycles
 };
 
 __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
@@ -439,10 +440,10 @@ k_tc4096(TcArgs a) {
         group_sync(bar);
         tc_fence_after();
         if (gt == 0) issue_split_gemm_k64<FMT, PIECES>(tmem, smem_u32(aop), smem_u32(bop), mb);
-        bool ok = mbar_wait(mb, parity);
+        bool ok = mbar_wait(mb, parity, a.wait);
         if (!ok) {
             atomicOr(a.err, 1u);
-            mbar_wait(mb, parity);                      // let our own MMAs drain
+            mbar_wait(mb, parity);                      // let our own MMAs drain (default bound)
         }
         parity ^= 1u;
         tc_fence_after();
@@ -727,30 +728,31 @@ static cudaError_t go_tc_prec(int prec, const TcArgs& a, cudaStream_t st) {
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_nvmt_rows_tc4096(float2* ws, int W, int Hp, int L, int interp, int prec, unsigned* err, int batch,
-                                    cudaStream_t st) {
-    if (W <= 0 || W > TCR_S || (W & 1)) return cudaErrorInvalidValue;
+cudaError_t launch_nvmt_rows_tc4096(float2* ws, int W, int Hp, int L, int interp, int prec, unsigned* err,
+                                    long long wait, int batch, cudaStream_t st) {
+    if (W <= 0 || W > TCR_S || (W & 1) || wait < 0) return cudaErrorInvalidValue;
     cudaError_t e = ensure_w64();
     if (e != cudaSuccess) return e;
-    TcArgs a{ws, nullptr, nullptr, W, 0, Hp, L, TCR_S, 0, batch * L, err};
+    TcArgs a{ws, nullptr, nullptr, W, 0, Hp, L, TCR_S, 0, batch * L, err, wait};
     return interp == FT_INTERP_LINEAR ? go_tc_prec<TCM_ROWS_LINEAR>(prec, a, st)
                                       : go_tc_prec<TCM_ROWS_CUBIC>(prec, a, st);
 }
 
 cudaError_t launch_col_r2c_tc4096(const float* img_cm, int H, int W, int row0, float2* ws, int L, int S, int prec,
-                                  unsigned* err, int batch, cudaStream_t st) {
-    if (H <= 0 || H > TCR_S || W <= 0 || (W & 1) || L != TCR_S / 2 + 1 || S < W) return cudaErrorInvalidValue;
+                                  unsigned* err, long long wait, int batch, cudaStream_t st) {
+    if (H <= 0 || H > TCR_S || W <= 0 || (W & 1) || L != TCR_S / 2 + 1 || S < W || wait < 0)
+        return cudaErrorInvalidValue;
     cudaError_t e = ensure_w64();
     if (e != cudaSuccess) return e;
-    TcArgs a{ws, img_cm, nullptr, W, H, TCR_S, L, S, row0, batch * (W / 2), err};
+    TcArgs a{ws, img_cm, nullptr, W, H, TCR_S, L, S, row0, batch * (W / 2), err, wait};
     return go_tc_prec<TCM_R2C>(prec, a, st);
 }
 
-cudaError_t launch_col_c2r_tc4096(const float2* ws, int L, int S, float* map_cm, int prec, unsigned* err, int batch,
-                                  cudaStream_t st) {
-    if (L != TCR_S / 2 + 1 || S <= 0 || (S & 1)) return cudaErrorInvalidValue;
+cudaError_t launch_col_c2r_tc4096(const float2* ws, int L, int S, float* map_cm, int prec, unsigned* err,
+                                  long long wait, int batch, cudaStream_t st) {
+    if (L != TCR_S / 2 + 1 || S <= 0 || (S & 1) || wait < 0) return cudaErrorInvalidValue;
     cudaError_t e = ensure_w64();
     if (e != cudaSuccess) return e;
-    TcArgs a{const_cast<float2*>(ws), nullptr, map_cm, 0, 0, TCR_S, L, S, 0, batch * (S / 2), err};
+    TcArgs a{const_cast<float2*>(ws), nullptr, map_cm, 0, 0, TCR_S, L, S, 0, batch * (S / 2), err, wait};
     return go_tc_prec<TCM_C2R>(prec, a, st);
 }

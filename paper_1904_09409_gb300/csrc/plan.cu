@@ -168,7 +168,10 @@ static void free_ws(ft_plan p) {
     p->ws_bytes = 0;
 }
 
-static ft_status ensure(void** ptr, size_t* have, size_t need, const char* what) {
+// Grow a plan-owned device buffer to `need` bytes (synchronise, free, allocate).
+// While the plan has injected failures left (ft_plan_inject_alloc_failures), an
+// allocation fails as cudaMalloc's out-of-memory error would, without calling it.
+static ft_status ensure(ft_plan p, void** ptr, size_t* have, size_t need, const char* what) {
     if (need <= *have && *ptr) return FT_OK;
     if (*ptr) {
         cudaDeviceSynchronize();
@@ -176,7 +179,11 @@ static ft_status ensure(void** ptr, size_t* have, size_t need, const char* what)
         *ptr = nullptr;
         *have = 0;
     }
-    cudaError_t e = cudaMalloc(ptr, need);
+    cudaError_t e = cudaErrorMemoryAllocation;
+    if (p->alloc_failures > 0)
+        --p->alloc_failures;
+    else
+        e = cudaMalloc(ptr, need);
     if (e != cudaSuccess) {
         *ptr = nullptr;
         cuda_fail(e, what);
@@ -226,7 +233,8 @@ static cudaError_t nvmt_rows(ft_plan p, float2* ws, int batch, cudaStream_t st) 
                                         p->d_chirp + nu, p->d_chirp + nu + nx, batch, st);
     }
     if (p->precision != FT_PRECISION_FP32 && p->S == 4096)
-        return launch_nvmt_rows_tc4096(ws, p->W, p->Hp, p->L, p->interp, p->precision, p->d_tc_err, batch, st);
+        return launch_nvmt_rows_tc4096(ws, p->W, p->Hp, p->L, p->interp, p->precision, p->d_tc_err, p->tc_wait,
+                                       batch, st);
     if (p->use_fast_x) return launch_nvmt_rows_fast(ws, p->W, p->Hp, p->L, p->interp, p->fx, batch, st);
     return launch_nvmt_rows(ws, p->W, p->S, p->Hp, p->L, p->interp, p->fx, p->row_logB_x, batch, st);
 }
@@ -292,6 +300,7 @@ ft_status ft_plan_create_space(ft_plan* out, int img_H, int img_W, int n_slope, 
     p->L = n_intercept / 2 + 1;
     p->interp = interp;
     p->top = (n_intercept - H) / 2;
+    p->tc_wait = FT_WAIT_CYCLES;
     p->fy = fy;
     p->fx = fx;
     cudaError_t e = cudaGetDevice(&p->device);
@@ -451,6 +460,23 @@ ft_status ft_plan_tc_errors(ft_plan p, uint32_t* flags) {
     if (e == cudaSuccess) e = cudaMemset(p->d_tc_err, 0, sizeof(unsigned));
     cudaSetDevice(cur);
     FT_CUDA(e, "ft_plan_tc_errors");
+    if (*flags & 1u)
+        return ft_record_error(FT_ERR_TIMEOUT, "ft_plan_tc_errors: a wait for the tensor cores timed out; the rows "
+                                               "of the blocks that gave up are incomplete");
+    return FT_OK;
+}
+
+ft_status ft_plan_set_wait_cycles(ft_plan p, int64_t cycles) {
+    if (!p || cycles < 0) return FT_ERR_INVALID_ARG;
+    p->tc_wait = cycles;
+    return FT_OK;
+}
+
+int64_t ft_plan_get_wait_cycles(ft_plan p) { return p ? (int64_t)p->tc_wait : -1; }
+
+ft_status ft_plan_inject_alloc_failures(ft_plan p, int count) {
+    if (!p || count < 0) return FT_ERR_INVALID_ARG;
+    p->alloc_failures = count;
     return FT_OK;
 }
 
@@ -580,11 +606,12 @@ static size_t cm_elems(ft_plan p) {
 static cudaError_t tc_r2c(ft_plan p, const float* src, float2* ws, float* cm, int nb, cudaStream_t st) {
     cudaError_t e = launch_transpose(src, cm, p->H, p->W, nb, st);
     if (e != cudaSuccess) return e;
-    return launch_col_r2c_tc4096(cm, p->H, p->W, p->top, ws, p->L, p->S, p->precision, p->d_tc_err, nb, st);
+    return launch_col_r2c_tc4096(cm, p->H, p->W, p->top, ws, p->L, p->S, p->precision, p->d_tc_err, p->tc_wait, nb,
+                                 st);
 }
 
 static cudaError_t tc_c2r(ft_plan p, const float2* ws, float* d_map, float* cm, int nb, cudaStream_t st) {
-    cudaError_t e = launch_col_c2r_tc4096(ws, p->L, p->S, cm, p->precision, p->d_tc_err, nb, st);
+    cudaError_t e = launch_col_c2r_tc4096(ws, p->L, p->S, cm, p->precision, p->d_tc_err, p->tc_wait, nb, st);
     if (e != cudaSuccess) return e;
     return launch_transpose(cm, d_map, p->S, p->Hp, nb, st);
 }
@@ -613,7 +640,7 @@ ft_status ft_forward(ft_plan p, const float* d_img, float* d_map, int batch, voi
     if (!d_img || !d_map || ((uintptr_t)d_img & 7) || ((uintptr_t)d_map & 7)) return FT_ERR_INVALID_ARG;
     // the column-major copies of the split-precision path live in the aux region
     const size_t cm_bytes = tc_columns(p) ? (size_t)batch * cm_elems(p) * sizeof(float) : 0;
-    ft_status s = ensure(&p->d_ws, &p->ws_bytes, aux_off(p, batch) + cm_bytes, "cudaMalloc(workspace)");
+    ft_status s = ensure(p, &p->d_ws, &p->ws_bytes, aux_off(p, batch) + cm_bytes, "cudaMalloc(workspace)");
     if (s != FT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     float2* ws = (float2*)p->d_ws;
@@ -653,7 +680,7 @@ ft_status ft_backward(ft_plan p, const float* d_grad_map, float* d_grad_img, int
     if (batch == 0) return FT_OK;
     if (!d_grad_map || !d_grad_img || ((uintptr_t)d_grad_map & 7) || ((uintptr_t)d_grad_img & 7))
         return FT_ERR_INVALID_ARG;
-    ft_status s = ensure(&p->d_ws, &p->ws_bytes, aux_off(p, batch), "cudaMalloc(workspace)");
+    ft_status s = ensure(p, &p->d_ws, &p->ws_bytes, aux_off(p, batch), "cudaMalloc(workspace)");
     if (s != FT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     float2* ws = (float2*)p->d_ws;
@@ -677,7 +704,7 @@ ft_status ft_abs_mse_backward(ft_plan p, const float* d_map, const float* d_targ
     if (!p->use_fast_y) {
         // no fused kernel for this length: the loss gradient through the workspace
         const size_t gbytes = (batch * cells * sizeof(float) + 255) & ~(size_t)255;
-        ft_status s = ensure(&p->d_ws, &p->ws_bytes, off + gbytes + loss_partial_bytes(batch),
+        ft_status s = ensure(p, &p->d_ws, &p->ws_bytes, off + gbytes + loss_partial_bytes(batch),
                              "cudaMalloc(workspace)");
         if (s != FT_OK) return s;
         float* gmap = (float*)((char*)p->d_ws + off);
@@ -688,7 +715,7 @@ ft_status ft_abs_mse_backward(ft_plan p, const float* d_map, const float* d_targ
         return ft_backward(p, gmap, d_grad_img, batch, stream);
     }
     const int nblk = col_r2c_loss_blocks(p->fy, p->S);
-    ft_status s = ensure(&p->d_ws, &p->ws_bytes, off + (size_t)batch * nblk * sizeof(float), "cudaMalloc(workspace)");
+    ft_status s = ensure(p, &p->d_ws, &p->ws_bytes, off + (size_t)batch * nblk * sizeof(float), "cudaMalloc(workspace)");
     if (s != FT_OK) return s;
     float2* ws = (float2*)p->d_ws;
     float* partial = (float*)((char*)p->d_ws + off);
@@ -716,7 +743,7 @@ ft_status ft_peaks(ft_plan p, const float* d_map, int batch, int top_k, float th
     const bool sparse = peaks_use_tile_max(p, batch, top_k);
     const size_t tpi = (size_t)((p->Hp + tr - 1) / tr) * ((p->S + tc - 1) / tc);     // tiles per map
     const size_t off = aux_off(p, batch);
-    ft_status s = ensure(&p->d_ws, &p->ws_bytes, off + peaks_scratch_bytes(p, batch, top_k), "cudaMalloc(workspace)");
+    ft_status s = ensure(p, &p->d_ws, &p->ws_bytes, off + peaks_scratch_bytes(p, batch, top_k), "cudaMalloc(workspace)");
     if (s != FT_OK) return s;
     unsigned* tmax = (unsigned*)((char*)p->d_ws + off);
     unsigned long long* kbuf = (unsigned long long*)((char*)p->d_ws + off);
@@ -766,7 +793,7 @@ ft_status ft_detect(ft_plan p, const float* d_img, float* d_map, int batch, int 
     }
     // the tile maxima [batch][bands][column blocks] live in the aux region
     const size_t off = aux_off(p, batch);
-    ft_status s = ensure(&p->d_ws, &p->ws_bytes, off + tmax_bytes(p, batch, top_k), "cudaMalloc(workspace)");
+    ft_status s = ensure(p, &p->d_ws, &p->ws_bytes, off + tmax_bytes(p, batch, top_k), "cudaMalloc(workspace)");
     if (s != FT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     float2* ws = (float2*)p->d_ws;
@@ -790,7 +817,7 @@ ft_status ft_abs_mse_grad(ft_plan p, const float* d_map, const float* d_target, 
     if (batch == 0) return FT_OK;
     if (!d_map || !d_target || !d_loss) return FT_ERR_INVALID_ARG;
     const size_t off = aux_off(p, batch);
-    ft_status s = ensure(&p->d_ws, &p->ws_bytes, off + loss_partial_bytes(batch), "cudaMalloc(workspace)");
+    ft_status s = ensure(p, &p->d_ws, &p->ws_bytes, off + loss_partial_bytes(batch), "cudaMalloc(workspace)");
     if (s != FT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     FT_LAUNCH(p, FT_KERNEL_LOSS, st,
@@ -892,9 +919,9 @@ ft_status ft_detect_host(ft_plan p, const float* h_img, int batch, int top_k, fl
     const size_t pk_b = (size_t)batch * top_k * sizeof(ft_peak);
     const size_t cnt_off = (pk_b + 255) & ~(size_t)255;
     ft_status s;
-    if ((s = ensure((void**)&p->d_img_host, &p->img_host_bytes, img_b, "cudaMalloc(image)")) != FT_OK) return s;
-    if ((s = ensure((void**)&p->d_map_host, &p->map_host_bytes, map_b, "cudaMalloc(map)")) != FT_OK) return s;
-    if ((s = ensure((void**)&p->d_peaks_host, &p->peaks_host_bytes, cnt_off + batch * sizeof(int32_t),
+    if ((s = ensure(p, (void**)&p->d_img_host, &p->img_host_bytes, img_b, "cudaMalloc(image)")) != FT_OK) return s;
+    if ((s = ensure(p, (void**)&p->d_map_host, &p->map_host_bytes, map_b, "cudaMalloc(map)")) != FT_OK) return s;
+    if ((s = ensure(p, (void**)&p->d_peaks_host, &p->peaks_host_bytes, cnt_off + batch * sizeof(int32_t),
                     "cudaMalloc(peaks)")) != FT_OK)
         return s;
     p->d_count_host = (int32_t*)((char*)p->d_peaks_host + cnt_off);
@@ -916,7 +943,7 @@ ft_status ft_detect_host(ft_plan p, const float* h_img, int batch, int top_k, fl
     if (tile_max_bytes(p, chunk) > peak_b) peak_b = tile_max_bytes(p, chunk);
     if (peaks_key_bytes(p->Hp, p->S, chunk, top_k) > peak_b) peak_b = peaks_key_bytes(p->Hp, p->S, chunk, top_k);
     const size_t need = aux_off(p, chunk) + peak_b;
-    if ((s = ensure(&p->d_ws, &p->ws_bytes, need, "cudaMalloc(workspace)")) != FT_OK) return s;
+    if ((s = ensure(p, &p->d_ws, &p->ws_bytes, need, "cudaMalloc(workspace)")) != FT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     FT_CUDA(cudaEventRecord(p->start_event, st), "event");
     FT_CUDA(cudaStreamWaitEvent(p->copy_stream, p->start_event, 0), "copy stream wait");

@@ -17,8 +17,6 @@
 
 #include "ft_internal.cuh"
 
-// a wait that has not completed after this many SM cycles (about 2 s) gives up
-#define FT_WAIT_CYCLES 4000000000ll
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -82,12 +80,16 @@ __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// bounded wait for the completion of phase `parity`; false after ~2 s
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+// bounded wait for the completion of phase `parity`: false once `limit` SM
+// cycles have passed (FT_WAIT_CYCLES, about 2 s, by default).  The limit is
+// checked before every try, so a limit of 0 gives up at once (the plan's test
+// setting that exercises the timeout path).
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit = FT_WAIT_CYCLES) {
     const long long t0 = clock64();
-    while (!mbar_try(mbar, parity))
-        if (clock64() - t0 > FT_WAIT_CYCLES) return false;
-    return true;
+    for (;;) {
+        if (clock64() - t0 >= limit) return false;
+        if (mbar_try(mbar, parity)) return true;
+    }
 }
 
 // 16 consecutive 32-bit columns starting at `taddr` for this warp's 32 lanes

@@ -39,7 +39,9 @@ EXPORTED = (
     "ft_batch_group_info", "ft_batch_group_tuned_ms", "ft_batch_run", "ft_tc_dft64",
     "ft_plan_set_precision", "ft_plan_get_precision", "ft_plan_tc_errors", "ft_verify",
     "ft_abs_mse_backward", "ft_detect", "ft_detect_launches",
+    "ft_plan_set_wait_cycles", "ft_plan_get_wait_cycles", "ft_plan_inject_alloc_failures",
 )
+FT_WAIT_CYCLES_DEFAULT = 4000000000
 FT_PRECISION_FP32 = 0
 FT_PRECISION_BF16X3 = 1
 FT_PRECISION_FP16X3 = 2
@@ -131,6 +133,12 @@ def lib() -> ctypes.CDLL:
     L.ft_abs_mse_backward.restype = ci
     L.ft_detect.argtypes = [vp, vp, vp, ci, ci, cf, vp, vp, vp]
     L.ft_detect.restype = ci
+    L.ft_plan_set_wait_cycles.argtypes = [vp, ctypes.c_int64]
+    L.ft_plan_set_wait_cycles.restype = ci
+    L.ft_plan_get_wait_cycles.argtypes = [vp]
+    L.ft_plan_get_wait_cycles.restype = ctypes.c_int64
+    L.ft_plan_inject_alloc_failures.argtypes = [vp, ci]
+    L.ft_plan_inject_alloc_failures.restype = ci
     L.ft_detect_launches.argtypes = [vp, ci, ci]
     L.ft_detect_launches.restype = ci
     for name in ("ft_plan_variant_count", "ft_plan_set_variant", "ft_plan_get_variant", "ft_batch_create",
@@ -469,10 +477,28 @@ def ft_plan_get_precision(plan: Plan) -> int:
 
 
 def ft_plan_tc_errors(plan: Plan) -> int:
-    """Waits for the device, returns and clears the tensor-core error flags."""
+    """Waits for the device, returns and clears the tensor-core error flags;
+    raises FunnelError with status FT_ERR_TIMEOUT when a wait timed out."""
     v = ctypes.c_uint32(0)
-    _check(lib().ft_plan_tc_errors(plan.handle, ctypes.byref(v)), "ft_plan_tc_errors")
+    st = lib().ft_plan_tc_errors(plan.handle, ctypes.byref(v))
+    if st == FT_ERR_TIMEOUT:
+        raise FunnelError(st, "ft_plan_tc_errors", f"flags {int(v.value):#x}: {ft_last_error()}")
+    _check(st, "ft_plan_tc_errors")
     return int(v.value)
+
+
+def ft_plan_set_wait_cycles(plan: Plan, cycles: int) -> None:
+    """Bound of the plan's tensor-core waits in SM cycles (0: give up at once)."""
+    _check(lib().ft_plan_set_wait_cycles(plan.handle, int(cycles)), "ft_plan_set_wait_cycles")
+
+
+def ft_plan_get_wait_cycles(plan: Plan) -> int:
+    return int(lib().ft_plan_get_wait_cycles(plan.handle))
+
+
+def ft_plan_inject_alloc_failures(plan: Plan, count: int) -> None:
+    """The plan's next ``count`` device allocations fail with FT_ERR_OOM."""
+    _check(lib().ft_plan_inject_alloc_failures(plan.handle, int(count)), "ft_plan_inject_alloc_failures")
 
 
 class Batch:
