@@ -333,8 +333,11 @@ def varlen_images(pool, shapes):
 
 
 def time_varlen(f, imgs, shapes, steps, dev):
-    """512 mixed-size images (H, W from {128 ... 2048}), forward + top-32 peaks in
-    one captured graph after autotuning; returns the JSON record."""
+    """512 mixed-size images (H, W from {128 ... 2048}), forward + top-32 peaks:
+    the grouped kernels (one launch per stage over every image, work queues)
+    after autotuning, in one captured graph; returns the JSON record with the
+    tuner's table and per-size throughput (each shape alone, as a batch of its
+    own with the chosen configuration)."""
     import torch
     cache = os.path.join(ROOT, "paper_1904_09409_gb300", "tune_cache.json")
     b = f.Batch(shapes, tune_cache=cache)
@@ -343,37 +346,56 @@ def time_varlen(f, imgs, shapes, steps, dev):
     out = torch.empty(b.n * TOP_K * f.PEAK_DTYPE.itemsize, dtype=torch.uint8, device=dev)
     cnt = torch.empty(b.n, dtype=torch.int32, device=dev)
     s = torch.cuda.Stream(dev)
+
+    def timed(batch, xb, mb, ob, cb, n):
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                batch.run(xb, mb, TOP_K, out=ob, count=cb, stream=s, graph=True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(n):
+                batch.run(xb, mb, TOP_K, out=ob, count=cb, stream=s, graph=True)
+            e1.record(s)
+            s.synchronize()
+        return e0.elapsed_time(e1) / n
+
     with torch.cuda.stream(s):
         t0 = time.perf_counter()
         b.run(x, m, TOP_K, out=out, count=cnt, stream=s, tune=True)
         s.synchronize()
         tune_s = time.perf_counter() - t0
-        for _ in range(3):
-            b.run(x, m, TOP_K, out=out, count=cnt, stream=s, graph=True)
-        s.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(s)
-        for _ in range(steps):
-            b.run(x, m, TOP_K, out=out, count=cnt, stream=s, graph=True)
-        e1.record(s)
-        s.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    groups = b.groups()
+    ms = timed(b, x, m, out, cnt, steps)
+    cfg = b.config()
+    chosen = (cfg["r2c_threads"], cfg["rows_threads"], cfg["c2r_threads"])
+    tune_table = {f"{a}/{r}/{c}": round(v, 4) for (a, r, c), v in b.tune_ms().items()}
     px = sum(h * w for h, w in shapes)
-    per = {f"{g['H']}x{g['W']}": round(g["count"] * g["H"] * g["W"] / (g["tuned_ms"] / 1e3) / 1e6, 1)
-           for g in groups if g["tuned_ms"] > 0}
-    variants = {}
+    # per size: the images of one shape as a batch of their own, same configuration
+    per = {}
+    groups = b.groups()
     for g in groups:
-        variants[str(g["variant"])] = variants.get(str(g["variant"]), 0) + 1
+        h, w, start, count = g["H"], g["W"], g["start"], g["count"]
+        idx = [int(i) for i in b.order[start:start + count]]
+        with f.Batch([(h, w)] * count) as bg:
+            bg.set_config(*chosen)
+            xg = torch.from_numpy(bg.pack([imgs[i] for i in idx])).to(dev)
+            mg = torch.empty(bg.map_total, dtype=torch.float32, device=dev)
+            og = torch.empty(count * TOP_K * f.PEAK_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+            cg = torch.empty(count, dtype=torch.int32, device=dev)
+            tg = timed(bg, xg, mg, og, cg, 10)
+        per[f"{h}x{w}"] = round(count * h * w / (tg / 1e3) / 1e6, 1)
     b.close()
     return {"images_per_s": len(shapes) / (ms / 1e3), "value": px / (ms / 1e3) / 1e6, "unit": UNIT,
             "ms_per_step": ms, "steps": steps, "images": len(shapes), "megapixels": px / 1e6,
-            "shape_groups": len(groups), "tune_s": tune_s, "variants_chosen": variants,
+            "shape_groups": len(groups), "launches_per_step": cfg["launches"],
+            "grouped_images": cfg["grouped_images"], "tune_s": tune_s,
+            "threads_chosen": {"r2c": chosen[0], "rows": chosen[1], "c2r": chosen[2]},
+            "default_threads": "512/128/256", "tune_ms": tune_table,
             "per_size_mpx_s": per,
             "workload": "512 images, H and W i.i.d. from {128,192,256,384,512,768,1024,1536,2048}, content as "
-                        "the 1024^2 batch, maps H x W, top-32; forward + peaks of all shape groups in one "
-                        "CUDA graph launch (8 forked streams), variants chosen by the autotuner; per-size "
-                        "figures are the tuned group timed alone"}
+                        "the 1024^2 batch, maps H x W, top-32; forward + peaks of every image in the grouped "
+                        "kernels (one persistent launch per stage, device work queues), one CUDA graph launch, "
+                        "threads per block chosen by the autotuner (tune_ms: r2c/rows/c2r -> ms); per-size "
+                        "figures are each shape's images alone as a batch of their own"}
 
 
 def host_cores() -> int:

@@ -233,26 +233,40 @@ int ft_plan_get_variant(ft_plan plan);
 /* ------------------------------------------------------------------------
  * Mixed-size batches (the paper's Sec. I remark that rows and columns are
  * independent, taken across images of uneven sizes).  A batch of n images of
- * sizes H[i] x W[i] (maps n_intercept = H[i], n_slope = W[i]) groups equal shapes
- * and keeps one plan per shape.  It fixes a packed layout: the caller stores
- * the images back to back in the order ft_batch_layout reports (order[j] = the
- * caller's index of packed image j, img_off[j] / map_off[j] = its element
- * offset in the packed image / map buffers, totals = {image elements, map
- * elements}); peaks are written as [n][top_k] rows and counts as [n] in the same
- * packed order.  Equal shapes are contiguous, largest first.
+ * sizes H[i] x W[i] (maps n_intercept = H[i], n_slope = W[i]) fixes a packed
+ * layout: the caller stores the images back to back in the order
+ * ft_batch_layout reports (order[j] = the caller's index of packed image j,
+ * img_off[j] / map_off[j] = its element offset in the packed image / map
+ * buffers, totals = {image elements, map elements}); peaks are written as
+ * [n][top_k] rows and counts as [n] in the same packed order.  Equal shapes are
+ * contiguous, largest first.
  *
- * ft_batch_run enqueues every group's ft_detect (ft_forward alone when top_k = 0)
- * on up to 8 side streams forked from and joined back into `stream`.
- *   FT_BATCH_GRAPH: capture that sequence once into a CUDA graph (after an
+ * Images whose sides both have a fixed-length schedule up to 2048 (128, 192,
+ * 256, 384, 512, 768, 1024, 1536, 2048), with the linear or cubic interpolator,
+ * run in the grouped kernels: one persistent launch per stage over all of them
+ * (step 1; steps 2-3; step 4 with the maxima of |P| per 256-cell tile; the peak
+ * pass from those maxima), each block taking (image, block) items from a device
+ * work queue, largest images first, and running the fixed-length code of the
+ * item's length; 4 launches (3 with top_k = 0) whatever the number of shapes.
+ * Every other shape group keeps a plan of its own (one per shape) whose
+ * ft_detect (ft_forward when top_k = 0) runs on one of up to 8 side streams
+ * forked from and joined back into `stream`.  Results are those of per-image
+ * plans (the same FFT arithmetic, bit for bit; the same peak lists).
+ *   FT_BATCH_GRAPH: capture the whole sequence once into a CUDA graph (after an
  *     uncaptured run that allocates every workspace and synchronises `stream`)
  *     and replay it while all arguments stay the same; `stream` must not be the
  *     legacy default stream.
- *   FT_BATCH_TUNE: before running, time every kernel variant of every group's
- *     plan (ft_plan_set_variant) on the caller's buffers (synchronous) and keep
- *     the fastest; with a tune_cache path the choices are merged into that JSON
- *     file (keys "GPU name|HxW|interp") and ft_batch_create applies cached choices.
- * The batch owns its plans, streams and graph; one batch may be used by one host
- * thread at a time. */
+ *   FT_BATCH_TUNE: before running, time on the caller's buffers (synchronous)
+ *     every combination of the grouped kernels' threads per block (step 1: 256
+ *     or 512; steps 2-3: 128 or 256; step 4: 256 or 512 -- which fix the
+ *     transforms per block of every length and the tile shape of the peak pass)
+ *     and every kernel variant of the other groups' plans (ft_plan_set_variant),
+ *     and keep the fastest; with a tune_cache path the choices are merged into
+ *     that JSON file (keys "GPU name|HxW|interp" for the plans, "GPU
+ *     name|batch|interp|shape digest" for the grouped kernels) and
+ *     ft_batch_create applies cached choices.
+ * The batch owns its plans, workspaces, streams and graph; one batch may be
+ * used by one host thread at a time. */
 typedef struct ft_batch_s* ft_batch;
 #define FT_BATCH_GRAPH 1
 #define FT_BATCH_TUNE 2
@@ -262,10 +276,26 @@ ft_status ft_batch_destroy(ft_batch batch);
 ft_status ft_batch_layout(ft_batch batch, int32_t* order, int64_t* img_off, int64_t* map_off,
                           int64_t* totals);
 int ft_batch_group_count(ft_batch batch);
-/* info = {H, W, first packed position, count, variant} of group g */
+/* info = {H, W, first packed position, count, variant} of group g; variant is
+ * -1 for groups in the grouped kernels */
 ft_status ft_batch_group_info(ft_batch batch, int g, int32_t* info);
-/* mean ms of one tuned forward (+ peaks) of group g alone, -1 before tuning */
+/* mean ms of one tuned forward (+ peaks) of group g alone, -1 before tuning and
+ * for groups in the grouped kernels */
 float ft_batch_group_tuned_ms(ft_batch batch, int g);
+/* info[6] = {images in the grouped kernels, shape groups on plans of their own,
+ * threads per block of step 1, of steps 2-3, of step 4 (the grouped kernels),
+ * kernel launches of one ft_batch_run with top_k > 0} */
+ft_status ft_batch_config(ft_batch batch, int32_t* info);
+/* Threads per block of the grouped kernels (256 or 512; 128 or 256; 256 or 512;
+ * FT_ERR_INVALID_ARG otherwise).  Changes later runs (the graph is recaptured). */
+ft_status ft_batch_set_config(ft_batch batch, int r2c_threads, int rows_threads, int c2r_threads);
+/* The autotuner's measurements of the grouped kernels: ms[c] (c < n, at most
+ * 8) = mean ms of one run with step 1 threads {256, 512}[c >> 2 & 1], steps
+ * 2-3 {128, 256}[c >> 1 & 1], step 4 {256, 512}[c & 1]; -1 before tuning.
+ * Returns 8. */
+int ft_batch_tune_ms(ft_batch batch, float* ms, int n);
+/* Kernel launches of one ft_batch_run with this top_k (0 for an invalid one). */
+int ft_batch_launches(ft_batch batch, int top_k);
 ft_status ft_batch_run(ft_batch batch, const float* d_imgs, float* d_maps, int top_k, float threshold,
                        ft_peak* d_out, int32_t* d_count, void* stream, int flags);
 

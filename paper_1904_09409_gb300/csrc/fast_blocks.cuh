@@ -1,0 +1,322 @@
+// One block's work of the fixed-length column and row kernels (see k_cols.cu and
+// k_rows.cu for what each step computes), built on the register-resident FFT of
+// fft_fast.cuh.  The per-plan kernels of k_fast.cu run one of these per CUDA
+// block over a uniform batch; the mixed-size batch kernels of k_batch.cu run
+// them from a work queue over images of different lengths.  B, the transforms
+// per block, is a template parameter: the block has fs_T(N) * B threads.
+//  * the column R2C reads its first pass directly from global memory; the
+//    other two stage their inputs into shared memory with 16-byte cp.async
+//    copies, all in flight at once (C2R: the Hermitian half, each row read once
+//    for both n and N - n; rows: the B spectrum rows feeding the NVMT gather);
+//    the last pass writes global memory directly where the output order allows;
+//  * the NVMT sample x' H' / (2 l) of successive elements of a thread is stepped
+//    exactly by adding the precomputed quotient and remainder of
+//    (N / R0) H' / (2 l), so the inner loop has no integer division;
+//  * the interpolation fraction is remainder * (1 / (2 l)) in FP32 (within one
+//    rounding of the exact fraction).
+#pragma once
+
+#include "fft_fast.cuh"
+
+// The last pass of the column R2C and the split of each complex transform (two
+// real columns a + i b) into the two half spectra:
+//     A[l] = (Z[l] + conj Z[N-l]) / 2,  B[l] = (Z[l] - conj Z[N-l]) / (2 i),
+// scaled by end_scale (l = 0, N/2) or mid_scale, written as one float4 per row.
+template <int N, int B>
+__device__ __forceinline__ void r2c_finish(float2 (&v)[fs_E(N)], float2* sm, int t, int f, const float2* stw,
+                                           bool colok, float2* dst, int out_pitch, float end_scale,
+                                           float mid_scale) {
+    constexpr int E = fs_E(N), T = N / E;
+    constexpr int RL = fs_radix(N, fs_nst(N) - 1), GL = E / RL;
+    using F = FastFft<N, -1, B>;
+    F::template run<0>(v, sm, t, f, stw);
+    // Sample t + T j is the thread's element (j mod GL, j / GL).  Thread t != 0
+    // writes l = t + T j (j < E/2) and needs Z[N - l] = Z[(T - t) + T (E - 1 - j)],
+    // element E - 1 - j >= E/2 of thread T - t; thread 0 writes l = T j
+    // (j <= E/2) and needs Z[N - l], its own element E - j (element 0 for l = 0).
+    // So only elements j >= E/2 go through shared memory.
+#pragma unroll
+    for (int m = 0; m < GL; ++m)
+#pragma unroll
+        for (int q = 0; q < RL; ++q)
+            if (m + GL * q >= E / 2) sm[spos(F::out_pos(t, m, q)) * B + f] = v[m * RL + q];
+    __syncthreads();
+    if (!colok) return;
+    auto el = [&](int j) -> float2 { return v[(j % GL) * RL + j / GL]; };
+    auto split_z = [&](int l, float2 zl, float2 zm, float s) {
+        float4 o;
+        o.x = 0.5f * s * (zl.x + zm.x);
+        o.y = 0.5f * s * (zl.y - zm.y);
+        o.z = 0.5f * s * (zl.y + zm.y);
+        o.w = -0.5f * s * (zl.x - zm.x);
+        *reinterpret_cast<float4*>(dst + (size_t)l * out_pitch) = o;
+    };
+    // only t = 0 meets the end bins 0 and N/2 (N/2 is a multiple of T)
+    if (t != 0) {
+#pragma unroll
+        for (int j = 0; j < E / 2; ++j)
+            split_z(t + T * j, el(j), sm[spos(N - t - T * j) * B + f], mid_scale);
+    } else {
+        split_z(0, el(0), el(0), end_scale);
+#pragma unroll
+        for (int j = 1; j < E / 2; ++j) split_z(T * j, el(j), el(E - j), mid_scale);
+        split_z(N / 2, el(E / 2), el(E / 2), end_scale);
+    }
+}
+
+// Step 1 (and the transpose of step 4) for column block bx of one image: real
+// columns bx 2B + 2f, + 1 of `in` (rows_in rows, pitch in_pitch floats, first
+// row at expanded row row0, zeros elsewhere) -> half spectra out[l][c] (pitch
+// out_pitch complex).  The first pass reads global memory directly (8-byte
+// loads of the thread's column pair): staging the image tile through shared
+// memory first measured slower on GB300 (67 vs 60 us for 32 images of 1024^2).
+template <int N, int B>
+__device__ __forceinline__ void r2c_block(const float* __restrict__ in, int rows_in, int ncols, int in_pitch,
+                                          int row0, const float2* __restrict__ stw, float2* __restrict__ out,
+                                          int out_pitch, float end_scale, float mid_scale, int bx, float2* sm) {
+    constexpr int E = fs_E(N);
+    constexpr int R0 = fs_radix(N, 0), G0 = E / R0;
+    using F = FastFft<N, -1, B>;
+    const int f = threadIdx.x % B;
+    const int t = threadIdx.x / B;
+    const int c = bx * 2 * B + 2 * f;
+    const bool colok = c < ncols;
+    const float* src = in + c;
+
+    float2 v[E];
+    if (colok && row0 == 0 && rows_in == N) {          // every row is an image row
+#pragma unroll
+        for (int m = 0; m < G0; ++m)
+#pragma unroll
+            for (int q = 0; q < R0; ++q)
+                v[m * R0 + q] = __ldg(reinterpret_cast<const float2*>(
+                    src + (size_t)F::template in_pos<0>(t, m, q) * in_pitch));
+    } else {
+#pragma unroll
+        for (int m = 0; m < G0; ++m)
+#pragma unroll
+            for (int q = 0; q < R0; ++q) {
+                const int row = F::template in_pos<0>(t, m, q) - row0;
+                float2 x = make_float2(0.f, 0.f);
+                if (colok && row >= 0 && row < rows_in)
+                    x = __ldg(reinterpret_cast<const float2*>(src + (size_t)row * in_pitch));
+                v[m * R0 + q] = x;
+            }
+    }
+    r2c_finish<N, B>(v, sm, t, f, stw, colok, out + c, out_pitch, end_scale, mid_scale);
+}
+
+// Step 4 (and the transpose of step 1) for column block bx of one image: the
+// Hermitian halves in[l][c] (pitch in_pitch complex, l = 0 .. N/2) of columns
+// bx 2B + 2f, + 1 -> rows row0 .. row0 + rows_out - 1 of the length-N real
+// results, times out_scale, at out[t - row0][c] (pitch out_pitch floats).
+// tmax (may be NULL; only with row0 = 0 and rows_out = N): the maximum of |out|
+// of every tile of 128 / B rows x 2B columns, at tmax[tile row * nbx + bx]
+// (nbx = column blocks of the image) as float bits.
+template <int N, int B>
+__device__ __forceinline__ void c2r_block(const float2* __restrict__ in, int ncols, int in_pitch,
+                                          const float2* __restrict__ stw, float mid_scale, float* __restrict__ out,
+                                          int row0, int rows_out, int out_pitch, float out_scale,
+                                          unsigned* __restrict__ tmax, int nbx, int bx, float2* sm) {
+    constexpr int E = fs_E(N);
+    constexpr int R0 = fs_radix(N, 0), G0 = E / R0;
+    constexpr int RL = fs_radix(N, fs_nst(N) - 1), GL = E / RL;
+    using F = FastFft<N, +1, B>;
+    const int f = threadIdx.x % B;
+    const int t = threadIdx.x / B;
+    const int c = bx * 2 * B + 2 * f;
+    const bool colok = c < ncols;
+
+    // stage the Hermitian half (rows 0 .. N/2, 2B complex each) with 16-byte async
+    // copies; every row is read once and serves both n and N - n.  Thread (t, f)
+    // copies the column pair f of rows t, t + T, ...
+    float2* stg = sm;                                  // [N/2 + 1][2B]
+    {
+        const float2* src = in + c + (size_t)t * in_pitch;
+        float2* dst = stg + t * 2 * B + 2 * f;
+        for (int r = t; r <= N / 2; r += fs_T(N), src += (size_t)fs_T(N) * in_pitch, dst += fs_T(N) * 2 * B) {
+            if (colok)
+                cp_async16(dst, src);
+            else
+                *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+    }
+    // sample n = t + T (m + G0 q) comes from row n when m + G0 q < E/2 and from
+    // row N - n otherwise (the two agree at n = N/2); the end bins 0 and N/2,
+    // which only thread t = 0 holds, enter through their real parts
+    float2 v[E];
+#pragma unroll
+    for (int m = 0; m < G0; ++m)
+#pragma unroll
+        for (int q = 0; q < R0; ++q) {
+            const int n = F::template in_pos<0>(t, m, q);
+            const bool up = m + G0 * q < E / 2;
+            float4 g = *reinterpret_cast<const float4*>(stg + (up ? n : N - n) * 2 * B + 2 * f);
+            g.x *= mid_scale; g.y *= mid_scale; g.z *= mid_scale; g.w *= mid_scale;
+            v[m * R0 + q] = up ? make_float2(g.x - g.w, g.y + g.z)      // A + i B
+                               : make_float2(g.x + g.w, g.z - g.y);     // conj A + i conj B
+        }
+    if (t == 0) {
+        constexpr int mh = (E / 2) % G0, qh = (E / 2) / G0;          // the element of n = N/2
+        const float4 g0 = *reinterpret_cast<const float4*>(stg + 2 * f);
+        const float4 gh = *reinterpret_cast<const float4*>(stg + (N / 2) * 2 * B + 2 * f);
+        v[0] = make_float2(g0.x, g0.z);                               // Re A + i Re B
+        v[mh * R0 + qh] = make_float2(gh.x, gh.z);
+    }
+    __syncthreads();
+    F::template run<0>(v, sm, t, f, stw);
+    if (tmax) {
+        // Tile maxima of |map| for the peak pass: thread t holds rows t + T j,
+        // j = m + GL q, of its column pair.  A tile is RS = 128 / B consecutive
+        // rows of one band (rows T j + RS u .. T j + RS u + RS - 1, u < T / RS) of
+        // the block's 2B columns, 256 cells held by the RS B consecutive threads
+        // t = RS u .. RS u + RS - 1; its tile row is RS-row index T j / RS + u.
+        // Each thread puts max(|re|, |im|) of its element of band j (the stored,
+        // scaled values; NaN counts as 0, like a cell that is never a peak) at
+        // bm[j][thread] in the exchange buffer, which the FFT no longer reads;
+        // then every warp reduces tiles w, w + warps, ...: 4 conflict-free words
+        // per lane and one redux.sync.
+        constexpr int NT = fs_T(N) * B;                // threads of the block
+        constexpr int RS = 128 / B, TPB = fs_T(N) / RS;   // tile rows, tiles per band
+        static_assert(RS * B == 128 && TPB * RS == fs_T(N), "a tile is 128 threads' values");
+        static_assert(E * NT <= FastFft<N, +1, B>::SLOTS * 2, "band maxima fit the exchange buffer");
+        unsigned* bm = reinterpret_cast<unsigned*>(sm);
+#pragma unroll
+        for (int m = 0; m < GL; ++m)
+#pragma unroll
+            for (int q = 0; q < RL; ++q) {
+                const float a = fabsf(v[m * RL + q].x * out_scale), b = fabsf(v[m * RL + q].y * out_scale);
+                bm[(m + GL * q) * NT + threadIdx.x] = colok ? __float_as_uint(fmaxf(fmaxf(a, b), 0.f)) : 0u;
+            }
+        __syncthreads();
+        const int lane = threadIdx.x & 31;
+        for (int w = threadIdx.x >> 5; w < E * TPB; w += NT / 32) {
+            const unsigned* src = bm + (w / TPB) * NT + (w % TPB) * 128 + lane;
+            unsigned x = max(max(src[0], src[32]), max(src[64], src[96]));
+            x = __reduce_max_sync(0xffffffffu, x);
+            if (lane == 0) tmax[(size_t)w * nbx + bx] = x;
+        }
+    }
+    if (!colok) return;
+    // row n of the result goes to output row n - row0 when that is in range
+    float* dst = out + c;
+#pragma unroll
+    for (int m = 0; m < GL; ++m)
+#pragma unroll
+        for (int q = 0; q < RL; ++q) {
+            const int rr = F::out_pos(t, m, q) - row0;
+            if ((unsigned)rr < (unsigned)rows_out)
+                *reinterpret_cast<float2*>(dst + (size_t)rr * out_pitch) =
+                    make_float2(v[m * RL + q].x * out_scale, v[m * RL + q].y * out_scale);
+        }
+}
+
+// row pitch (complex) of the staged spectrum rows: W samples between two zero
+// samples on each side (so a clamped tap index needs no bounds test); W + 4
+// keeps 16-byte alignment for cp.async and shifts successive rows by 8 banks
+__host__ __device__ constexpr int srow_pitch(int W) { return W + 4; }
+
+// Steps 2-3 in place for rows bx B .. bx B + B - 1 of one image's half spectrum
+// base[L][N] (W columns of image data per row before, N = n_slope values of G
+// after): the NVMT gather with the exact positions x' H' / (2 l), then the
+// exp(+j) transform along x'.  Row 0 becomes zero.  Shared memory: the larger
+// of the FFT's exchange buffer and B staged rows of srow_pitch(W) complex.
+template <int N, int INTERP, int B>
+__device__ __forceinline__ void rows_block(float2* __restrict__ base, int W, int Hp, int L,
+                                           const float2* __restrict__ stw, int bx, float2* sm) {
+    constexpr int E = fs_E(N), T = N / E;
+    constexpr int R0 = fs_radix(N, 0), G0 = E / R0;
+    constexpr int RL = fs_radix(N, fs_nst(N) - 1), GL = E / RL;
+    constexpr int STEPX = N / R0;                      // x' distance between a thread's elements
+    using F = FastFft<N, +1, B>;
+    // [B][W + 4] input rows (sample x at 2 + x, 16-byte aligned, two zeros on
+    // each side) in the FFT's own exchange buffer: they are read only by the
+    // gather, which ends before the first exchange
+    float2* srow = sm;
+    const int WP = srow_pitch(W);
+    const int f = threadIdx.x % B;
+    const int t = threadIdx.x / B;
+    const int l0 = bx * B;
+    const int l = l0 + f;
+
+    // stage the block's B spectrum rows (W complex each) with 16-byte async copies
+    const int chunks = W >> 1;                         // two complex per 16 bytes
+    if (threadIdx.x < 2 * B) {
+        const int r = threadIdx.x >> 1;
+        *reinterpret_cast<float4*>(srow + r * WP + ((threadIdx.x & 1) ? W + 2 : 0)) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+        float2* dst = srow + r * WP + 2;
+        const float2* src = base + (size_t)(l0 + r) * N;
+        if (l0 + r < L) {
+            for (int c = threadIdx.x; c < chunks; c += fs_T(N) * B) cp_async16(dst + 2 * c, src + 2 * c);
+        } else {
+            for (int c = threadIdx.x; c < chunks; c += fs_T(N) * B)
+                *reinterpret_cast<float4*>(dst + 2 * c) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+
+    float2 v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = make_float2(0.f, 0.f);
+    if (l >= 1 && l < L) {
+        const float2* myrow = srow + f * WP + 2;
+        const int den = 2 * l;
+        const float inv = 1.f / (float)den;
+        const int step = STEPX * Hp;
+        const int sA = step / den, sB = step - sA * den;
+        const int halfW = W >> 1;
+        const float2 zero = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int m = 0; m < G0; ++m) {
+            const int i = t + m * T;
+            const int num = (i - N / 2) * Hp;
+            int qf = floor_div(num, den);
+            int rem = num - qf * den;
+#pragma unroll
+            for (int q = 0; q < R0; ++q) {
+                const float fr = (float)rem * inv;
+                const int c0 = qf + halfW;
+                float2 acc;
+                if constexpr (INTERP == FT_INTERP_LINEAR) {
+                    // taps c0, c0 + 1; outside 0 .. W-1 the padding's zeros
+                    const int cc = min(max(c0, -2), W);
+                    const float2 a0 = myrow[cc], a1 = myrow[cc + 1];
+                    acc = make_float2(fmaf(fr, a1.x - a0.x, a0.x), fmaf(fr, a1.y - a0.y, a0.y));
+                } else {
+                    acc = zero;
+#pragma unroll
+                    for (int d = -1; d <= 2; ++d) {
+                        const float2 a = (unsigned)(c0 + d) < (unsigned)W ? myrow[c0 + d] : zero;
+                        const float w = keys_w(fr - (float)d);
+                        acc.x = fmaf(w, a.x, acc.x);
+                        acc.y = fmaf(w, a.y, acc.y);
+                    }
+                }
+                if ((i + q * STEPX) & 1) acc = make_float2(-acc.x, -acc.y);
+                v[m * R0 + q] = acc;
+                rem += sB;
+                qf += sA;
+                if (rem >= den) { rem -= den; qf += 1; }
+            }
+        }
+    }
+    __syncthreads();                                   // the staged rows are dead from here
+    F::template run<0>(v, sm, t, f, stw);
+    if (l >= L) return;
+    float2* row = base + (size_t)l * N;
+#pragma unroll
+    for (int m = 0; m < GL; ++m)
+#pragma unroll
+        for (int q = 0; q < RL; ++q) {
+            const int s = F::out_pos(t, m, q);
+            float2 val = v[m * RL + q];
+            if ((s + N / 2) & 1) val = make_float2(-val.x, -val.y);
+            row[s] = val;
+        }
+}

@@ -337,6 +337,45 @@ cudaError_t launch_col_r2c_tc4096(const float* img_cm, int H, int W, int row0, f
 cudaError_t launch_col_c2r_tc4096(const float2* ws, int L, int S, float* map_cm, int prec, unsigned* err,
                                   long long wait, int batch, cudaStream_t st);
 
+// ---------------------------------------------- mixed-size batches (k_batch.cu)
+// One image of a mixed-size batch in the grouped kernels: map n_intercept = H,
+// n_slope = W; offsets in elements of the packed images / maps, complex
+// elements of the batch's spectrum workspace and words of its tile maxima.
+struct BatchImg {
+    long long img_off, map_off, ws_off, tm_off;
+    int H, W;
+    int pos;                // packed position (row of the peak records and counts)
+    const float2* stw_y;    // per-pass twiddles of length H (steps 1 and 4)
+    const float2* stw_x;    // per-pass twiddles of length W (step 3)
+};
+// lengths the grouped kernels take (every fixed-length schedule up to 2048)
+__host__ __device__ constexpr bool batch_len_ok(int n) {
+    return n == 128 || n == 192 || n == 256 || n == 384 || n == 512 || n == 768 || n == 1024 || n == 1536 ||
+           n == 2048;
+}
+// blocks of one image per stage for the given threads per block (the stage's
+// tuning knob); rows: NVMT + row FFT blocks; cols: column blocks of step 1 / 4
+int batch_r2c_blocks(int H, int W, int threads);
+int batch_rows_blocks(int H, int W, int threads);
+int batch_c2r_blocks(int H, int W, int threads);
+// tile shape of step 4's maxima: rows x cols cells, bands x column blocks tiles
+void batch_tile_shape(int H, int W, int threads, int* rows, int* cols, int* bands, int* nbx);
+bool batch_threads_ok(int stage, int threads);   // stage 0 r2c, 1 rows, 2 c2r
+// The four stage kernels, each a persistent loop over a device work queue of
+// `items` (image, block) pairs (*queue counts taken items and must be 0 at the
+// launch; the peak stage takes one image per item).  grid = 0 picks the
+// resident-block count of the device.
+cudaError_t launch_batch_r2c(const BatchImg* imgs, const int2* items, int nitems, unsigned* queue, const float* in,
+                             float2* ws, int threads, int maxH, cudaStream_t st);
+cudaError_t launch_batch_rows(const BatchImg* imgs, const int2* items, int nitems, unsigned* queue, float2* ws,
+                              int interp, int threads, int maxW, cudaStream_t st);
+cudaError_t launch_batch_c2r(const BatchImg* imgs, const int2* items, int nitems, unsigned* queue, const float2* ws,
+                             float* maps, unsigned* tmax, int threads, int maxH, cudaStream_t st);
+cudaError_t launch_batch_peaks(const BatchImg* imgs, int nimg, unsigned* queue, const float* maps, const unsigned* tmax,
+                               int c2r_threads, int top_k, float threshold, ft_peak* out, int32_t* count,
+                               size_t smem, cudaStream_t st);
+size_t batch_peaks_smem(const BatchImg* host_imgs, int nimg, int c2r_threads, int top_k);
+
 // line verification of Sec. 4.5 (k_verify.cu): image element (v, u) of the
 // transform's frame at img[v * stride_v + u * stride_u] (image b at b * img_stride)
 cudaError_t launch_verify(const float* img, int H, int W, int stride_v, int stride_u, size_t img_stride, int S,

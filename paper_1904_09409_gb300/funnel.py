@@ -40,6 +40,7 @@ EXPORTED = (
     "ft_plan_set_precision", "ft_plan_get_precision", "ft_plan_tc_errors", "ft_verify",
     "ft_abs_mse_backward", "ft_detect", "ft_detect_launches",
     "ft_plan_set_wait_cycles", "ft_plan_get_wait_cycles", "ft_plan_inject_alloc_failures",
+    "ft_batch_config", "ft_batch_set_config", "ft_batch_tune_ms", "ft_batch_launches",
 )
 FT_WAIT_CYCLES_DEFAULT = 4000000000
 FT_PRECISION_FP32 = 0
@@ -139,6 +140,14 @@ def lib() -> ctypes.CDLL:
     L.ft_plan_get_wait_cycles.restype = ctypes.c_int64
     L.ft_plan_inject_alloc_failures.argtypes = [vp, ci]
     L.ft_plan_inject_alloc_failures.restype = ci
+    L.ft_batch_config.argtypes = [vp, vp]
+    L.ft_batch_config.restype = ci
+    L.ft_batch_set_config.argtypes = [vp, ci, ci, ci]
+    L.ft_batch_set_config.restype = ci
+    L.ft_batch_tune_ms.argtypes = [vp, vp, ci]
+    L.ft_batch_tune_ms.restype = ci
+    L.ft_batch_launches.argtypes = [vp, ci]
+    L.ft_batch_launches.restype = ci
     L.ft_detect_launches.argtypes = [vp, ci, ci]
     L.ft_detect_launches.restype = ci
     for name in ("ft_plan_variant_count", "ft_plan_set_variant", "ft_plan_get_variant", "ft_batch_create",
@@ -536,6 +545,26 @@ class Batch:
                             variant=int(info[4]),
                             tuned_ms=float(lib().ft_batch_group_tuned_ms(self.handle, g))))
         return out
+
+    def config(self):
+        """The grouped kernels' configuration (ft_batch_config)."""
+        info = np.zeros(6, np.int32)
+        _check(lib().ft_batch_config(self.handle, info.ctypes.data), "ft_batch_config")
+        return dict(grouped_images=int(info[0]), plan_groups=int(info[1]), r2c_threads=int(info[2]),
+                    rows_threads=int(info[3]), c2r_threads=int(info[4]), launches=int(info[5]))
+
+    def set_config(self, r2c_threads: int, rows_threads: int, c2r_threads: int) -> None:
+        _check(lib().ft_batch_set_config(self.handle, int(r2c_threads), int(rows_threads), int(c2r_threads)),
+               "ft_batch_set_config")
+
+    def tune_ms(self):
+        """{(r2c, rows, c2r threads): mean ms} measured by the autotuner (-1 before)."""
+        ms = np.full(8, -1.0, np.float32)
+        lib().ft_batch_tune_ms(self.handle, ms.ctypes.data, 8)
+        return {((256, 512)[c >> 2 & 1], (128, 256)[c >> 1 & 1], (256, 512)[c & 1]): float(ms[c]) for c in range(8)}
+
+    def launches(self, top_k: int = 1) -> int:
+        return int(lib().ft_batch_launches(self.handle, int(top_k)))
 
     def pack(self, images):
         """List of (H, W) arrays in caller order -> packed float32 numpy buffer."""

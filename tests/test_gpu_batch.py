@@ -1,8 +1,11 @@
-"""Mixed-size batches (ft_batch_*): packed layout, one graph launch, autotuner.
+"""Mixed-size batches (ft_batch_*): packed layout, grouped kernels (one launch
+per stage over every shape with a fixed-length schedule up to 2048), per-shape
+plans for the other shapes, one graph launch, autotuner.
 
-Without tuning every group uses the same kernels as a single-shape plan, so the
-batch must reproduce per-image ft_forward / ft_peaks bit for bit; tuned variants
-are checked against the FP64 oracle instead."""
+The grouped kernels run the same FFT arithmetic per transform as a single-shape
+plan (only the transforms per block differ), so the batch must reproduce
+per-image ft_forward / ft_peaks bit for bit, in every configuration of the
+autotuner; tuned plan variants are checked against the FP64 oracle instead."""
 import json
 
 import numpy as np
@@ -102,15 +105,54 @@ def test_autotuner_and_cache(torch, tmp_path):
     with f.Batch(SHAPES, tune_cache=cache) as b:
         maps, _, _ = run_batch(torch, b, imgs, tune=True)
         tuned = {(g["H"], g["W"]): g["variant"] for g in b.groups()}
-        assert all(0 <= v <= 4 for v in tuned.values())
-        assert all(g["tuned_ms"] > 0 for g in b.groups())
+        plan_groups = [g for g in b.groups() if g["variant"] >= 0]
+        assert all(0 <= g["variant"] <= 4 and g["tuned_ms"] > 0 for g in plan_groups)
+        # the grouped kernels: 8 configurations timed, the fastest kept
+        ms = b.tune_ms()
+        assert len(ms) == 8 and all(v > 0 for v in ms.values())
+        cfg = b.config()
+        chosen = (cfg["r2c_threads"], cfg["rows_threads"], cfg["c2r_threads"])
+        assert ms[chosen] == min(ms.values())
     for i in range(len(SHAPES)):
         h, w = SHAPES[i]
         assert _gpu.rel_l2(maps[i], oracle.funnel_ref(imgs[i], w, h)) <= 1e-5
     entries = json.load(open(cache))
-    assert len(entries) == len(tuned)
+    assert len(entries) == len(plan_groups) + 1             # one entry for the grouped kernels
     with f.Batch(SHAPES, tune_cache=cache) as b2:          # choices come back from the cache
         assert {(g["H"], g["W"]): g["variant"] for g in b2.groups()} == tuned
+        c2 = b2.config()
+        assert (c2["r2c_threads"], c2["rows_threads"], c2["c2r_threads"]) == chosen
+
+
+SIZES = (128, 192, 256, 384, 512, 768, 1024, 1536, 2048)
+
+
+def test_grouped_kernels_every_configuration_bit_exact(torch):
+    """Shapes drawn from the mixed-size workload's sizes (both sides from
+    {128 ... 2048}, so every image runs in the grouped kernels: 4 launches)
+    plus two shapes on plans of their own: in each of the 8 configurations the
+    maps and peak lists equal those of per-image plans bit for bit."""
+    from paper_1904_09409_gb300 import funnel as f
+    rng = np.random.default_rng(77)
+    shapes = [(int(rng.choice(SIZES[:7])), int(rng.choice(SIZES[:7]))) for _ in range(18)]
+    shapes += [(2048, 256), (192, 1536), (128, 128), (64, 64), (48, 72)]
+    imgs = [synth.varlen_image(700 + i, h, w).img for i, (h, w) in enumerate(shapes)]
+    ref_maps, ref_peaks = individual(imgs)
+    with f.Batch(shapes) as b:
+        cfg = b.config()
+        assert cfg["grouped_images"] == len(shapes) - 2 and cfg["plan_groups"] == 2
+        for c in range(8):
+            r2c, rows, c2r = (256, 512)[c >> 2 & 1], (128, 256)[c >> 1 & 1], (256, 512)[c & 1]
+            b.set_config(r2c, rows, c2r)
+            maps, peaks, _ = run_batch(torch, b, imgs)
+            for i in range(len(shapes)):
+                assert np.array_equal(maps[i], ref_maps[i]), (c, shapes[i])
+                assert np.array_equal(peaks[i], ref_peaks[i]), (c, shapes[i])
+        with pytest.raises(f.FunnelError):
+            b.set_config(384, 128, 256)
+    with f.Batch([s for s in shapes if s[0] >= 128 and s[1] >= 128]) as b:
+        assert b.config()["plan_groups"] == 0
+        assert b.launches(TOP_K) == 4 and b.launches(0) == 3
 
 
 LARGE_SHAPES = [(2048, 2048), (1536, 1536), (2048, 1536), (1536, 2048), (128, 2048), (2048, 128),
