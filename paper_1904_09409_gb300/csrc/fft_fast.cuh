@@ -181,6 +181,17 @@ struct FastFft {
             for (int q = 0; q < R; ++q) v[m * R + q] = sm[spos(in_pos<s>(t, m, q)) * B + f];
     }
 
+    // The barriers of run<s> for the threads of a block that hold no transform of
+    // this length (a block whose stages use transforms of different lengths).
+    template <int s>
+    __device__ __forceinline__ static void idle() {
+        if constexpr (s + 1 < NS) {
+            __syncthreads();
+            __syncthreads();
+            idle<s + 1>();
+        }
+    }
+
     // Passes s .. NS-1.  On entry v holds the inputs of pass s in (m, q) order;
     // on return it holds the outputs of the last pass, element (m, q) being the
     // sample out_pos(t, m, q).  Every thread of the block must call it; it leaves

@@ -317,6 +317,14 @@ cudaError_t launch_nvmt_rows_fourier(float2* ws, int W, int S, int Hp, int L, co
                                      const FftLen& fm, const FftLen& fs, const float2* chirp_u,
                                      const float2* chirp_x, const float2* hc, int batch, cudaStream_t st);
 
+// the same on the register-resident FFT (k_fourier_fast.cu) where W = S, M = 2W
+// and all three lengths have a schedule (fw, fm, fs with per-pass twiddles);
+// cudaErrorNotSupported otherwise
+bool fourier_fast_ok(int W, int M, int S);
+cudaError_t launch_nvmt_rows_fourier_fast(bool adjoint, float2* ws, int W, int S, int Hp, int L, const FftLen& fw,
+                                          const FftLen& fm, const FftLen& fs, const float2* chirp_u,
+                                          const float2* chirp_x, const float2* hc, int batch, cudaStream_t st);
+
 // batched 64-point DFT as a split-precision tensor-core GEMM (k_tc.cu);
 // fmt 1 = BF16 hi+lo, 0 = FP16 hi+lo; err gets bit 0 set if a wait timed out
 cudaError_t launch_tc_dft64(const float2* x, float2* y, int nvec, int sign, int fmt, unsigned* err,

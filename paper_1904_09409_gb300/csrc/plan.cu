@@ -226,9 +226,18 @@ static cudaError_t col_c2r(ft_plan p, const float2* in, int ncols, float mid, fl
                           out_pitch, out_img, os, batch, st);
 }
 
+// the band-limited interpolator on the register-resident FFT (fixed-length
+// kernels in use, W = S, M = 2W, all three lengths with a schedule)
+static bool fourier_fast(ft_plan p) {
+    return p->use_fast_x && p->fw.stw && p->fm.stw && fourier_fast_ok(p->W, p->fm.N, p->S);
+}
+
 static cudaError_t nvmt_rows(ft_plan p, float2* ws, int batch, cudaStream_t st) {
     if (p->interp == FT_INTERP_FOURIER) {
         const size_t nu = (size_t)p->L * (p->W + 1), nx = (size_t)p->L * p->S;
+        if (fourier_fast(p))
+            return launch_nvmt_rows_fourier_fast(false, ws, p->W, p->S, p->Hp, p->L, p->fw, p->fm, p->fx, p->d_chirp,
+                                                 p->d_chirp + nu, p->d_chirp + nu + nx, batch, st);
         return launch_nvmt_rows_fourier(ws, p->W, p->S, p->Hp, p->L, p->fw, p->fm, p->fx, p->d_chirp,
                                         p->d_chirp + nu, p->d_chirp + nu + nx, batch, st);
     }
@@ -242,6 +251,9 @@ static cudaError_t nvmt_rows(ft_plan p, float2* ws, int batch, cudaStream_t st) 
 static cudaError_t nvmt_rows_adj(ft_plan p, float2* ws, int batch, cudaStream_t st) {
     if (p->interp == FT_INTERP_FOURIER) {
         const size_t nu = (size_t)p->L * (p->W + 1), nx = (size_t)p->L * p->S;
+        if (fourier_fast(p))
+            return launch_nvmt_rows_fourier_fast(true, ws, p->W, p->S, p->Hp, p->L, p->fw, p->fm, p->fx, p->d_chirp,
+                                                 p->d_chirp + nu, p->d_chirp + nu + nx, batch, st);
         return launch_nvmt_rows_fourier_adj(ws, p->W, p->S, p->Hp, p->L, p->fw, p->fm, p->fx, p->d_chirp,
                                             p->d_chirp + nu, p->d_chirp + nu + nx, batch, st);
     }
@@ -312,7 +324,10 @@ ft_status ft_plan_create_space(ft_plan* out, int img_H, int img_W, int n_slope, 
     const bool generic = force && force[0] == '1';
     const bool fast_y = fs_has(fy.N), fast_x = fs_has(fx.N);
     const size_t sy = fast_y ? fs_twsize(fy.N) : 0, sx = fast_x ? fs_twsize(fx.N) : 0;
-    std::vector<float2> tw((size_t)fy.N + fx.N + sy + sx + fw.N + fm.N);
+    // per-pass tables of the band-limited interpolator's lengths W and M
+    const bool fast_w = fw.N && fs_has(fw.N), fast_m = fm.N && fs_has(fm.N);
+    const size_t sw = fast_w ? fs_twsize(fw.N) : 0, smm = fast_m ? fs_twsize(fm.N) : 0;
+    std::vector<float2> tw((size_t)fy.N + fx.N + sy + sx + fw.N + fm.N + sw + smm);
     twiddles(fy.N, tw.data());
     twiddles(fx.N, tw.data() + fy.N);
     if (fast_y) stage_twiddles(fy.N, tw.data(), tw.data() + fy.N + fx.N);
@@ -320,6 +335,9 @@ ft_status ft_plan_create_space(ft_plan* out, int img_H, int img_W, int n_slope, 
     const size_t wo = (size_t)fy.N + fx.N + sy + sx;
     if (fw.N) twiddles(fw.N, tw.data() + wo);
     if (fm.N) twiddles(fm.N, tw.data() + wo + fw.N);
+    const size_t so = wo + fw.N + fm.N;
+    if (fast_w) stage_twiddles(fw.N, tw.data() + wo, tw.data() + so);
+    if (fast_m) stage_twiddles(fm.N, tw.data() + wo + fw.N, tw.data() + so + sw);
     e = cudaMalloc(&p->d_tw, tw.size() * sizeof(float2));
     if (e != cudaSuccess) {
         delete p;
@@ -341,7 +359,8 @@ ft_status ft_plan_create_space(ft_plan* out, int img_H, int img_W, int n_slope, 
         p->fm = fm;
         p->fw.tw = p->d_tw + wo;
         p->fm.tw = p->d_tw + wo + fw.N;
-        p->fw.stw = p->fm.stw = nullptr;
+        p->fw.stw = fast_w ? p->d_tw + so : nullptr;
+        p->fm.stw = fast_m ? p->d_tw + so + sw : nullptr;
         const ft_status cs = build_chirps(p);
         if (cs != FT_OK) {
             ft_plan_destroy(p);

@@ -433,8 +433,11 @@ def test_detect_host_pipeline_matches_device_calls(torch):
 
 
 # ------------------------------------------ band-limited (chirp-z) interpolator
+# (W = S with M = 2W and fixed-length schedules for W and M run the register-resident
+# kernel: 128 x 128, 192 x 192, 100 x 128 with H' = 256; the others the generic one)
 @pytest.mark.parametrize("H,W,S,Hp", [(32, 32, 32, 32), (48, 48, 64, 72), (64, 64, 128, 96),
-                                      (128, 128, 128, 128), (96, 64, 64, 144)])
+                                      (128, 128, 128, 128), (96, 64, 64, 144), (192, 192, 192, 192),
+                                      (100, 128, 128, 256)])
 def test_fourier_interp_matches_oracle(torch, H, W, S, Hp):
     """Sec. IV's chirp-z NVMT: the oracle evaluates the trigonometric interpolant
     of every row directly (dense Dirichlet kernel); the GPU uses a Bluestein
@@ -447,7 +450,8 @@ def test_fourier_interp_matches_oracle(torch, H, W, S, Hp):
         assert _gpu.rel_l2(got[i], ref) <= TOL_MAP, _gpu.rel_l2(got[i], ref)
 
 
-@pytest.mark.parametrize("H,W,S,Hp", [(32, 32, 32, 32), (48, 48, 64, 72), (64, 64, 128, 96), (256, 256, 256, 256)])
+@pytest.mark.parametrize("H,W,S,Hp", [(32, 32, 32, 32), (48, 48, 64, 72), (64, 64, 128, 96), (256, 256, 256, 256),
+                                      (192, 192, 192, 192), (100, 128, 128, 256)])
 def test_fourier_interp_adjoint_matches_oracle(torch, H, W, S, Hp):
     """ft_backward with the band-limited interpolator: the oracle's transpose
     (dense Dirichlet kernel scattered back) and the dot-product identity."""
@@ -463,6 +467,31 @@ def test_fourier_interp_adjoint_matches_oracle(torch, H, W, S, Hp):
         lhs = float(np.sum(px[i].astype(np.float64) * g[i]))
         rhs = float(np.sum(x[i].astype(np.float64) * gi[i]))
         assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(px[i]) * np.linalg.norm(g[i])
+
+
+@pytest.mark.parametrize("side,n", [(1024, 3), (2048, 1), (768, 5)])
+def test_fourier_interp_register_kernel_at_benchmark_size(torch, monkeypatch, side, n):
+    """At the benchmark's sizes the dense oracle is out of reach (W/2 cosines per
+    kernel entry), so the register-resident chirp-z kernel is checked against
+    properties that hold at any size: it equals the generic kernel (pinned to
+    the oracle above) to FP32 rounding, and ft_backward is its transpose
+    (the dot-product identity <A x, y> = <x, A^T y>)."""
+    rng = np.random.default_rng(side)
+    x = inputs(side, side, n, seed=side)
+    g = rng.standard_normal((n, side, side)).astype(np.float32)
+    with make_plan(side, side, side, side, "fourier") as plan:
+        fast = _gpu.forward(plan, x)
+        gi = _gpu.backward(plan, g)
+    monkeypatch.setenv("FT_FORCE_GENERIC", "1")
+    with make_plan(side, side, side, side, "fourier") as plan:
+        gen = _gpu.forward(plan, x)
+        gi_gen = _gpu.backward(plan, g)
+    for i in range(n):
+        assert _gpu.rel_l2(fast[i], gen[i].astype(np.float64)) <= 2e-6, i
+        assert _gpu.rel_l2(gi[i], gi_gen[i].astype(np.float64)) <= 2e-6, i
+        lhs = float(np.sum(fast[i].astype(np.float64) * g[i]))
+        rhs = float(np.sum(x[i].astype(np.float64) * gi[i]))
+        assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(fast[i]) * np.linalg.norm(g[i])
 
 
 # ------------------------------------------------------- line verification
