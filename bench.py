@@ -398,6 +398,55 @@ def time_varlen(f, imgs, shapes, steps, dev):
                         "figures are each shape's images alone as a batch of their own"}
 
 
+def fourier_rows_flops(H, W, S, Hp):
+    """FP32 FLOPs of steps 2-3 with the band-limited interpolator per image: per
+    kept row (l >= 1) complex FFTs of lengths W, M (twice) and S at 5 N log2 N,
+    the pre-chirp and its weights on W + 1 entries (8 each), the chirp spectrum
+    product on M (6) and the post-chirp with its weights on S (8)."""
+    import math
+    M = W + S
+    while True:                                    # the smallest 2^a 3^b >= W + S
+        m = M
+        for p in (2, 3):
+            while m % p == 0:
+                m //= p
+        if m == 1:
+            break
+        M += 1
+    per_row = (5 * W * math.log2(W) + 2 * 5 * M * math.log2(M) + 5 * S * math.log2(S)
+               + 8 * (W + 1) + 6 * M + 8 * S)
+    return per_row * (Hp // 2)
+
+
+def fma_peak(f, stream, dev):
+    """Measured FP32 FMA throughput of this GPU (ft_fma_probe, 8 blocks of 256
+    threads per multiprocessor, best of 5) next to the nominal figure
+    SMs x 128 lanes x 2 x max SM clock."""
+    import torch
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    blocks, iters = sms * 8, 8192
+    out = torch.empty(blocks * 256, dtype=torch.float32, device=dev)
+    f.ft_fma_probe(out, blocks, iters, stream=stream)
+    best = None
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        flops = f.ft_fma_probe(out, blocks, iters, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        t = flops / (a.elapsed_time(b) / 1e3) / 1e12
+        best = t if best is None or t > best else best
+    try:
+        max_mhz = float(subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits",
+                                        "-i", str(dev.index or 0)], capture_output=True, text=True,
+                                       timeout=20).stdout.split()[0])
+    except Exception:
+        max_mhz = 2070.0
+    return {"measured_tflops": best, "nominal_tflops": sms * 128 * 2 * max_mhz * 1e6 / 1e12, "sms": sms,
+            "sm_max_mhz": max_mhz, "probe": f"{blocks} blocks x 256 threads x {iters} rounds x 8 FMA chains"}
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -631,15 +680,27 @@ def run_extras(f, args, plan, imgs, lines, x, stream, dev, rank, ws, vl_imgs, vl
     for _ in range(3):
         f.ft_detect(fplan, x, mf, TOP_K, out=pk, count=cn, stream=stream)
     fo_steps = max(3, min(args.steps, 50))
+    f.ft_profile_read(fplan)
     q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     q0.record(stream)
-    for _ in range(fo_steps):
+    for i in range(fo_steps):
+        f.ft_profile_enable(fplan, i % PROF_EVERY == 0)
         f.ft_detect(fplan, x, mf, TOP_K, out=pk, count=cn, stream=stream)
     q1.record(stream)
     torch.cuda.synchronize(dev)
     fo_ms = replicas.max_over_ranks(q0.elapsed_time(q1) / fo_steps, dev)
+    fo_prof = {k: 1e3 * v[0] / v[1] for k, v in f.ft_profile_read(fplan).items()}
     fplan.close()
     del mf
+    fma = fma_peak(f, stream, dev)
+    fo_flops = fourier_rows_flops(SIDE, SIDE, SIDE, SIDE) * BATCH
+    fo_rows_us = fo_prof.get("k_nvmt_rows")
+    fo_alu = None
+    if fo_rows_us:
+        t = fo_flops / (fo_rows_us / 1e6) / 1e12
+        fo_alu = {"kernel": "k_nvmt_rows (chirp-z)", "bound": "alu", "flops_per_launch": fo_flops,
+                  "achieved": t, "peak": fma["measured_tflops"], "unit": "TFLOP/s",
+                  "frac": t / fma["measured_tflops"], "peak_source": "measured (FMA probe in this run)"}
 
     # Sec. 4.5 line verification of the step's top-32 peaks (band of 5 pixels)
     pk_b = torch.empty(BATCH * TOP_K * f.PEAK_DTYPE.itemsize, dtype=torch.uint8, device=dev)
@@ -685,8 +746,9 @@ def run_extras(f, args, plan, imgs, lines, x, stream, dev, rank, ws, vl_imgs, vl
         "varlen": varlen,
         "verify": verify,
         "precision_4096": precision,
+        "fp32_fma_peak": fma,
         "fourier_interp": {"value": px_step / (fo_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": fo_ms,
-                           "steps": fo_steps,
+                           "steps": fo_steps, "kernels_us": fo_prof, "roofline": fo_alu,
                            "workload": "the same 64 x 1024^2 step (ft_detect, top-32 peaks) with the band-limited "
                                        "(chirp-z, Sec. IV) interpolator instead of the linear one"},
         "fwd_bwd": {"value": px_step / (fb_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": fb_ms,

@@ -425,6 +425,13 @@ ft_status ft_profile_enable(ft_plan plan, int enable);
 ft_status ft_profile_read(ft_plan plan, double* total_ms, int32_t* launches, int n);
 const char* ft_kernel_name(int id);
 
+/* FP32 FMA throughput probe (a measurement aid for the ALU roofline; no part
+ * of the transform): `blocks` blocks of 256 threads, each thread running 8
+ * independent FMA chains for `iters` rounds, one float per thread written to
+ * d_out (device, blocks x 256 floats).  FLOPs of one call:
+ * blocks x 256 x iters x 16.  Time it with CUDA events on `stream`. */
+ft_status ft_fma_probe(float* d_out, int blocks, int iters, void* stream);
+
 /* Static text for a status; never NULL. */
 const char* ft_status_string(ft_status status);
 

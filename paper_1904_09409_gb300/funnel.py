@@ -40,7 +40,7 @@ EXPORTED = (
     "ft_plan_set_precision", "ft_plan_get_precision", "ft_plan_tc_errors", "ft_verify",
     "ft_abs_mse_backward", "ft_detect", "ft_detect_launches",
     "ft_plan_set_wait_cycles", "ft_plan_get_wait_cycles", "ft_plan_inject_alloc_failures",
-    "ft_batch_config", "ft_batch_set_config", "ft_batch_tune_ms", "ft_batch_launches",
+    "ft_batch_config", "ft_batch_set_config", "ft_batch_tune_ms", "ft_batch_launches", "ft_fma_probe",
 )
 FT_WAIT_CYCLES_DEFAULT = 4000000000
 FT_PRECISION_FP32 = 0
@@ -148,6 +148,8 @@ def lib() -> ctypes.CDLL:
     L.ft_batch_tune_ms.restype = ci
     L.ft_batch_launches.argtypes = [vp, ci]
     L.ft_batch_launches.restype = ci
+    L.ft_fma_probe.argtypes = [vp, ci, ci, vp]
+    L.ft_fma_probe.restype = ci
     L.ft_detect_launches.argtypes = [vp, ci, ci]
     L.ft_detect_launches.restype = ci
     for name in ("ft_plan_variant_count", "ft_plan_set_variant", "ft_plan_get_variant", "ft_batch_create",
@@ -447,6 +449,13 @@ def ft_kernel_name(kernel_id: int) -> str:
 
 def ft_status_string(status: int) -> str:
     return lib().ft_status_string(int(status)).decode()
+
+
+def ft_fma_probe(out, blocks: int, iters: int, stream=None) -> int:
+    """FP32 FMA probe: returns the FLOPs of the call (time it with CUDA events)."""
+    op = _dev_ptr(out, "float32", blocks * 256, "out")
+    _check(lib().ft_fma_probe(op, int(blocks), int(iters), _stream_ptr(stream)), "ft_fma_probe")
+    return blocks * 256 * iters * 16
 
 
 def ft_last_error() -> str:
