@@ -369,20 +369,24 @@ def time_varlen(f, imgs, shapes, steps, dev):
     chosen = (cfg["r2c_threads"], cfg["rows_threads"], cfg["c2r_threads"])
     tune_table = {f"{a}/{r}/{c}": round(v, 4) for (a, r, c), v in b.tune_ms().items()}
     px = sum(h * w for h, w in shapes)
-    # per size: the images of one shape as a batch of their own, same configuration
+    # per size: the workload's images of one shape, repeated to at least 16
+    # megapixels, as a batch of their own with the same configuration (a launch
+    # of a shape's few images alone would measure launch latency, not the kernels)
     per = {}
     groups = b.groups()
     for g in groups:
         h, w, start, count = g["H"], g["W"], g["start"], g["count"]
         idx = [int(i) for i in b.order[start:start + count]]
-        with f.Batch([(h, w)] * count) as bg:
+        reps = max(count, -(-16 * 2 ** 20 // (h * w)))
+        sel = [imgs[idx[r % count]] for r in range(reps)]
+        with f.Batch([(h, w)] * reps) as bg:
             bg.set_config(*chosen)
-            xg = torch.from_numpy(bg.pack([imgs[i] for i in idx])).to(dev)
+            xg = torch.from_numpy(bg.pack(sel)).to(dev)
             mg = torch.empty(bg.map_total, dtype=torch.float32, device=dev)
-            og = torch.empty(count * TOP_K * f.PEAK_DTYPE.itemsize, dtype=torch.uint8, device=dev)
-            cg = torch.empty(count, dtype=torch.int32, device=dev)
+            og = torch.empty(reps * TOP_K * f.PEAK_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+            cg = torch.empty(reps, dtype=torch.int32, device=dev)
             tg = timed(bg, xg, mg, og, cg, 10)
-        per[f"{h}x{w}"] = round(count * h * w / (tg / 1e3) / 1e6, 1)
+        per[f"{h}x{w}"] = round(reps * h * w / (tg / 1e3) / 1e6, 1)
     b.close()
     return {"images_per_s": len(shapes) / (ms / 1e3), "value": px / (ms / 1e3) / 1e6, "unit": UNIT,
             "ms_per_step": ms, "steps": steps, "images": len(shapes), "megapixels": px / 1e6,
@@ -395,7 +399,7 @@ def time_varlen(f, imgs, shapes, steps, dev):
                         "the 1024^2 batch, maps H x W, top-32; forward + peaks of every image in the grouped "
                         "kernels (one persistent launch per stage, device work queues), one CUDA graph launch, "
                         "threads per block chosen by the autotuner (tune_ms: r2c/rows/c2r -> ms); per-size "
-                        "figures are each shape's images alone as a batch of their own"}
+                        "figures are each shape's images, repeated to >= 16 Mpx, as a batch of their own"}
 
 
 def fourier_rows_flops(H, W, S, Hp):

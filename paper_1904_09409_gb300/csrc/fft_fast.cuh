@@ -229,13 +229,13 @@ cudaError_t launch_col_r2c_loss_fast(const float* map, const float* target, int 
 cudaError_t launch_col_c2r_fast(const float2* in, int ncols, int in_pitch, size_t in_img,
                                 const FftLen& f, float mid_scale, float* out, int row0, int rows_out,
                                 int out_pitch, size_t out_img, float out_scale, int batch,
-                                cudaStream_t st, unsigned* tmax = nullptr);
+                                cudaStream_t st, unsigned* tmax = nullptr, bool pdl = false);
 // tiles of the tile maxima of launch_col_c2r_fast for length N: rows x cols
 // cells, bands = N / rows tiles per column block; false without a schedule.
 // A tile is 256 cells: 128 / B rows of one column block of 2B columns.
 __host__ __device__ constexpr int c2r_tile_rows(int N) { return 128 / fs_Bc2r(N); }
 bool c2r_tile_shape(int N, int* rows, int* cols, int* bands);
 cudaError_t launch_nvmt_rows_fast(float2* ws, int W, int Hp, int L, int interp, const FftLen& fx,
-                                  int batch, cudaStream_t st);
+                                  int batch, cudaStream_t st, bool pdl = false);
 cudaError_t launch_nvmt_rows_adjoint_fast(float2* ws, int W, int Hp, int L, int interp,
                                           const FftLen& fx, int batch, cudaStream_t st);

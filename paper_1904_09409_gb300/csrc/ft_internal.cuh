@@ -47,6 +47,34 @@ __device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int t) 
     return SIGN > 0 ? make_float2(w.x, -w.y) : w;
 }
 
+// ------------------------------------------- programmatic dependent launch
+// A kernel of the forward chain (steps 2-3, step 4, the peak pass) may be
+// launched while its predecessor on the stream is still running (its blocks are
+// placed as the predecessor's last blocks retire); pdl_wait() blocks until the
+// predecessor has completed and its writes are visible, and is a no-op for a
+// kernel launched without the attribute.  pdl_trigger() lets the successor be
+// launched early (the predecessor's blocks call it when they start).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// launch kernel k (grid g, block b, sm bytes of dynamic shared memory) on st,
+// with programmatic stream serialisation when pdl is set
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_maybe_pdl(void (*k)(KArgs...), dim3 g, dim3 b, size_t sm, cudaStream_t st, bool pdl,
+                                    Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? at : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 // ----------------------------------------------------- NVMT index helpers
 __device__ __forceinline__ int floor_div(int a, int b) {   // b > 0
     int q = a / b;
@@ -218,6 +246,7 @@ struct ft_plan_s {
     int variant;            // see ft_plan_set_variant
     int peak_mode;          // peak pass: 0 = the faster one by the cost model, 1 = from tile maxima, 2 = per-tile keys
     int num_sms;            // multiprocessors of the plan's device
+    int pdl;                // programmatic dependent launch in the forward chain (FT_PDL=0: off)
     int precision;          // ft_precision of step 3 (ft_plan_set_precision)
     unsigned* d_tc_err;     // error flags of the tensor-core kernels (allocated with the first split precision)
     long long tc_wait;      // bound of every tensor-core wait in SM cycles (ft_plan_set_wait_cycles)
@@ -303,7 +332,8 @@ size_t peaks_key_bytes(int Hp, int S, int batch, int top_k);
 // memory fits the current device.
 bool peak_sparse_fits(int tile_rows, int tile_cols, int top_k);
 cudaError_t launch_peak_sparse(const float* map, const unsigned* tmax, int Hp, int S, int tile_rows, int tile_cols,
-                               int batch, int top_k, float threshold, ft_peak* out, int32_t* count, cudaStream_t st);
+                               int batch, int top_k, float threshold, ft_peak* out, int32_t* count, cudaStream_t st,
+                               bool pdl = false);
 // tile maxima of given maps (map 8-byte aligned) in tiles of tile_max_shape
 void tile_max_shape(int* tile_rows, int* tile_cols);
 cudaError_t launch_tile_max(const float* map, int Hp, int S, int batch, unsigned* tmax, cudaStream_t st);

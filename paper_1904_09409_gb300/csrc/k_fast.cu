@@ -9,6 +9,7 @@ k_col_r2c_fast(const float* __restrict__ in, int rows_in, int ncols, int in_pitc
                int row0, const float2* __restrict__ stw, float2* __restrict__ out, int out_pitch,
                size_t out_img, float end_scale, float mid_scale) {
     extern __shared__ float2 sm[];
+    pdl_trigger();
     r2c_block<N, fs_Bcol(N)>(in + (size_t)blockIdx.y * in_img, rows_in, ncols, in_pitch, row0, stw,
                              out + (size_t)blockIdx.y * out_img, out_pitch, end_scale, mid_scale, blockIdx.x, sm);
 }
@@ -19,6 +20,8 @@ k_col_c2r_fast(const float2* __restrict__ in, int ncols, int in_pitch, size_t in
                const float2* __restrict__ stw, float mid_scale, float* __restrict__ out, int row0,
                int rows_out, int out_pitch, size_t out_img, float out_scale, unsigned* __restrict__ tmax) {
     extern __shared__ float2 sm[];
+    pdl_trigger();
+    pdl_wait();
     constexpr int bands = fs_E(N) * fs_T(N) / c2r_tile_rows(N);
     c2r_block<N, fs_Bc2r(N)>(in + (size_t)blockIdx.y * in_img, ncols, in_pitch, stw, mid_scale,
                              out + (size_t)blockIdx.y * out_img, row0, rows_out, out_pitch, out_scale,
@@ -92,6 +95,8 @@ template <int N, int INTERP>
 __global__ void __launch_bounds__(fs_T(N) * fs_Brow(N), 1024 / (fs_T(N) * fs_Brow(N)))
 k_nvmt_rows_fast(float2* __restrict__ ws, int W, int Hp, int L, const float2* __restrict__ stw) {
     extern __shared__ float2 sm[];
+    pdl_trigger();
+    pdl_wait();
     rows_block<N, INTERP, fs_Brow(N)>(ws + (size_t)blockIdx.y * L * N, W, Hp, L, stw, blockIdx.x, sm);
 }
 
@@ -207,34 +212,33 @@ static cudaError_t go_r2c_loss(const float* map, const float* target, int ncols,
 template <int N>
 static cudaError_t go_c2r(const float2* in, int ncols, int in_pitch, size_t in_img, const float2* stw,
                           float mid, float* out, int row0, int rows_out, int out_pitch, size_t out_img,
-                          float os, unsigned* tmax, int batch, cudaStream_t st) {
+                          float os, unsigned* tmax, int batch, cudaStream_t st, bool pdl) {
     constexpr int B = fs_Bc2r(N);
     const size_t sm = (size_t)FastFft<N, +1, B>::SLOTS * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_col_c2r_fast<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     dim3 grid((ncols + 2 * B - 1) / (2 * B), batch);
-    k_col_c2r_fast<N><<<grid, fs_T(N) * B, sm, st>>>(in, ncols, in_pitch, in_img, stw, mid, out, row0,
-                                                     rows_out, out_pitch, out_img, os, tmax);
-    return cudaGetLastError();
+    return launch_maybe_pdl(k_col_c2r_fast<N>, grid, dim3(fs_T(N) * B), sm, st, pdl, in, ncols, in_pitch, in_img, stw,
+                            mid, out, row0, rows_out, out_pitch, out_img, os, tmax);
 }
 
 template <int N, int INTERP>
-static cudaError_t go_rows_i(float2* ws, int W, int Hp, int L, const float2* stw, int batch, cudaStream_t st) {
+static cudaError_t go_rows_i(float2* ws, int W, int Hp, int L, const float2* stw, int batch, cudaStream_t st,
+                             bool pdl) {
     constexpr int B = fs_Brow(N);
     const size_t slots = FastFft<N, +1, B>::SLOTS, rows = (size_t)srow_pitch(W) * B;
     const size_t sm = (slots > rows ? slots : rows) * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_nvmt_rows_fast<N, INTERP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     dim3 grid((L + B - 1) / B, batch);
-    k_nvmt_rows_fast<N, INTERP><<<grid, fs_T(N) * B, sm, st>>>(ws, W, Hp, L, stw);
-    return cudaGetLastError();
+    return launch_maybe_pdl(k_nvmt_rows_fast<N, INTERP>, grid, dim3(fs_T(N) * B), sm, st, pdl, ws, W, Hp, L, stw);
 }
 
 template <int N>
 static cudaError_t go_rows(float2* ws, int W, int Hp, int L, int interp, const float2* stw, int batch,
-                           cudaStream_t st) {
-    return interp == FT_INTERP_LINEAR ? go_rows_i<N, FT_INTERP_LINEAR>(ws, W, Hp, L, stw, batch, st)
-                                      : go_rows_i<N, FT_INTERP_CUBIC>(ws, W, Hp, L, stw, batch, st);
+                           cudaStream_t st, bool pdl) {
+    return interp == FT_INTERP_LINEAR ? go_rows_i<N, FT_INTERP_LINEAR>(ws, W, Hp, L, stw, batch, st, pdl)
+                                      : go_rows_i<N, FT_INTERP_CUBIC>(ws, W, Hp, L, stw, batch, st, pdl);
 }
 
 template <int N, int INTERP>
@@ -292,11 +296,11 @@ cudaError_t launch_col_r2c_loss_fast(const float* map, const float* target, int 
 cudaError_t launch_col_c2r_fast(const float2* in, int ncols, int in_pitch, size_t in_img,
                                 const FftLen& f, float mid_scale, float* out, int row0, int rows_out,
                                 int out_pitch, size_t out_img, float out_scale, int batch,
-                                cudaStream_t st, unsigned* tmax) {
+                                cudaStream_t st, unsigned* tmax, bool pdl) {
     if (tmax && (row0 != 0 || rows_out != f.N)) return cudaErrorInvalidValue;
     switch (f.N) {
 #define X(n) case n: return go_c2r<n>(in, ncols, in_pitch, in_img, f.stw, mid_scale, out, row0, rows_out, \
-                                      out_pitch, out_img, out_scale, tmax, batch, st);
+                                      out_pitch, out_img, out_scale, tmax, batch, st, pdl);
         FT_FAST_LENGTHS(X)
 #undef X
     }
@@ -313,9 +317,9 @@ bool c2r_tile_shape(int N, int* rows, int* cols, int* bands) {
 }
 
 cudaError_t launch_nvmt_rows_fast(float2* ws, int W, int Hp, int L, int interp, const FftLen& fx,
-                                  int batch, cudaStream_t st) {
+                                  int batch, cudaStream_t st, bool pdl) {
     switch (fx.N) {
-#define X(n) case n: return go_rows<n>(ws, W, Hp, L, interp, fx.stw, batch, st);
+#define X(n) case n: return go_rows<n>(ws, W, Hp, L, interp, fx.stw, batch, st, pdl);
         FT_FAST_LENGTHS(X)
 #undef X
     }

@@ -34,6 +34,7 @@ k_peak_sparse(const float* __restrict__ map, const unsigned* __restrict__ tmax, 
               int nty, int ntx, int K, float thr, ft_peak* __restrict__ out, int32_t* __restrict__ count) {
     extern __shared__ __align__(16) unsigned char spsm[];
     __shared__ SparseShared sh;
+    pdl_wait();
     const int img = blockIdx.x;
     peak_sparse_block(map + (size_t)img * Hp * S, tmax + (size_t)img * nty * ntx, Hp, S, TH, logTW, nty, ntx, K, thr,
                       out + (size_t)img * K, count + img, spsm, sh);
@@ -97,7 +98,8 @@ static int sparse_warps(int rows, int cols, int top_k) {
 bool peak_sparse_fits(int tile_rows, int tile_cols, int top_k) { return sparse_warps(tile_rows, tile_cols, top_k) > 0; }
 
 cudaError_t launch_peak_sparse(const float* map, const unsigned* tmax, int Hp, int S, int tile_rows, int tile_cols,
-                               int batch, int top_k, float threshold, ft_peak* out, int32_t* count, cudaStream_t st) {
+                               int batch, int top_k, float threshold, ft_peak* out, int32_t* count, cudaStream_t st,
+                               bool pdl) {
     const int nw = sparse_warps(tile_rows, tile_cols, top_k);
     if (nw == 0) return cudaErrorInvalidValue;
     int logTW = 0;
@@ -106,7 +108,6 @@ cudaError_t launch_peak_sparse(const float* map, const unsigned* tmax, int Hp, i
     const size_t sm = sparse_smem(tile_rows, tile_cols, top_k, nw, nty * ntx);
     cudaError_t e = cudaFuncSetAttribute(k_peak_sparse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_peak_sparse<<<batch, nw * 32, sm, st>>>(map, tmax, Hp, S, tile_rows, logTW, nty, ntx, top_k, threshold, out,
-                                              count);
-    return cudaGetLastError();
+    return launch_maybe_pdl(k_peak_sparse, dim3(batch), dim3(nw * 32), sm, st, pdl, map, tmax, Hp, S, tile_rows,
+                            logTW, nty, ntx, top_k, threshold, out, count);
 }

@@ -220,7 +220,7 @@ static cudaError_t col_c2r(ft_plan p, const float2* in, int ncols, float mid, fl
     const size_t in_img = (size_t)p->L * p->S;
     if (p->use_fast_y)
         return launch_col_c2r_fast(in, ncols, p->S, in_img, p->fy, mid, out, row0, rows_out, out_pitch,
-                                   out_img, os, batch, st, tmax);
+                                   out_img, os, batch, st, tmax, p->pdl);
     if (tmax) return cudaErrorInvalidValue;
     return launch_col_c2r(in, ncols, p->S, in_img, p->fy, p->col_logB_y, mid, out, row0, rows_out,
                           out_pitch, out_img, os, batch, st);
@@ -244,7 +244,7 @@ static cudaError_t nvmt_rows(ft_plan p, float2* ws, int batch, cudaStream_t st) 
     if (p->precision != FT_PRECISION_FP32 && p->S == 4096)
         return launch_nvmt_rows_tc4096(ws, p->W, p->Hp, p->L, p->interp, p->precision, p->d_tc_err, p->tc_wait,
                                        batch, st);
-    if (p->use_fast_x) return launch_nvmt_rows_fast(ws, p->W, p->Hp, p->L, p->interp, p->fx, batch, st);
+    if (p->use_fast_x) return launch_nvmt_rows_fast(ws, p->W, p->Hp, p->L, p->interp, p->fx, batch, st, p->pdl);
     return launch_nvmt_rows(ws, p->W, p->S, p->Hp, p->L, p->interp, p->fx, p->row_logB_x, batch, st);
 }
 
@@ -381,6 +381,10 @@ ft_status ft_plan_create_space(ft_plan* out, int img_H, int img_W, int n_slope, 
     p->variant = generic ? 1 : 0;
     const char* lanes = getenv("FT_LANES");
     p->lanes = lanes && atoi(lanes) > 1 ? FT_LANES : 1;
+    // programmatic dependent launch of the fixed-length kernels that follow
+    // another kernel (steps 2-3, step 4, the peak pass); FT_PDL=0 turns it off
+    const char* pdl = getenv("FT_PDL");
+    p->pdl = !(pdl && !strcmp(pdl, "0"));
     const char* pm = getenv("FT_PEAKS");
     p->peak_mode = pm && !strcmp(pm, "sparse") ? 1 : (pm && !strcmp(pm, "dense") ? 2 : 0);
     if (cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess || p->num_sms < 1)
@@ -825,7 +829,8 @@ ft_status ft_detect(ft_plan p, const float* d_img, float* d_map, int batch, int 
     }
     if ((s = forward_part(p, src, d_map, ws, nullptr, batch, st, tmax)) != FT_OK) return s;
     FT_LAUNCH(p, FT_KERNEL_PEAK_SPARSE, st,
-              launch_peak_sparse(d_map, tmax, p->Hp, p->S, rows, cols, batch, top_k, threshold, d_out, d_count, st),
+              launch_peak_sparse(d_map, tmax, p->Hp, p->S, rows, cols, batch, top_k, threshold, d_out, d_count, st,
+                                 p->pdl),
               "peak detection (tile maxima)");
     return FT_OK;
 }
