@@ -432,6 +432,18 @@ const char* ft_kernel_name(int id);
  * blocks x 256 x iters x 16.  Time it with CUDA events on `stream`. */
 ft_status ft_fma_probe(float* d_out, int blocks, int iters, void* stream);
 
+/* Bounds-checked debug build (libfunnel_debug.so, compiled with FT_DEBUG): the
+ * device checks every gather / scatter index of the fixed-length transform
+ * kernels and the peak pass; an index out of range is skipped (a load reads 0)
+ * and sets a bit in a flag word: 1 step-1 loads, 2 step-1 stores, 4 step-4
+ * staging, 8 step-4 stores, 16 NVMT taps, 32 FFT exchange slots, 64 NVMT
+ * transpose, 128 peak staging.  ft_debug_flags waits for the device, returns
+ * the bits recorded since the last call in *flags and clears them (0 in the
+ * normal build, where the checks do not exist).  ft_debug_build returns 1 for
+ * the debug build, 0 otherwise. */
+ft_status ft_debug_flags(uint32_t* flags);
+int ft_debug_build(void);
+
 /* Static text for a status; never NULL. */
 const char* ft_status_string(ft_status status);
 

@@ -39,7 +39,8 @@ __device__ __forceinline__ void r2c_finish(float2 (&v)[fs_E(N)], float2* sm, int
     for (int m = 0; m < GL; ++m)
 #pragma unroll
         for (int q = 0; q < RL; ++q)
-            if (m + GL * q >= E / 2) sm[spos(F::out_pos(t, m, q)) * B + f] = v[m * RL + q];
+            if (m + GL * q >= E / 2 && FT_IN(spos(F::out_pos(t, m, q)) * B + f, F::SLOTS, FT_DBG_FFT_SLOT))
+                sm[spos(F::out_pos(t, m, q)) * B + f] = v[m * RL + q];
     __syncthreads();
     if (!colok) return;
     auto el = [&](int j) -> float2 { return v[(j % GL) * RL + j / GL]; };
@@ -49,13 +50,15 @@ __device__ __forceinline__ void r2c_finish(float2 (&v)[fs_E(N)], float2* sm, int
         o.y = 0.5f * s * (zl.y - zm.y);
         o.z = 0.5f * s * (zl.y + zm.y);
         o.w = -0.5f * s * (zl.x - zm.x);
-        *reinterpret_cast<float4*>(dst + (size_t)l * out_pitch) = o;
+        if (FT_IN(l, N / 2 + 1, FT_DBG_R2C_STORE)) *reinterpret_cast<float4*>(dst + (size_t)l * out_pitch) = o;
     };
     // only t = 0 meets the end bins 0 and N/2 (N/2 is a multiple of T)
     if (t != 0) {
 #pragma unroll
-        for (int j = 0; j < E / 2; ++j)
-            split_z(t + T * j, el(j), sm[spos(N - t - T * j) * B + f], mid_scale);
+        for (int j = 0; j < E / 2; ++j) {
+            const int k = spos(N - t - T * j) * B + f;
+            split_z(t + T * j, el(j), FT_IN(k, F::SLOTS, FT_DBG_FFT_SLOT) ? sm[k] : make_float2(0.f, 0.f), mid_scale);
+        }
     } else {
         split_z(0, el(0), el(0), end_scale);
 #pragma unroll
@@ -88,9 +91,12 @@ __device__ __forceinline__ void r2c_block(const float* __restrict__ in, int rows
 #pragma unroll
         for (int m = 0; m < G0; ++m)
 #pragma unroll
-            for (int q = 0; q < R0; ++q)
-                v[m * R0 + q] = __ldg(reinterpret_cast<const float2*>(
-                    src + (size_t)F::template in_pos<0>(t, m, q) * in_pitch));
+            for (int q = 0; q < R0; ++q) {
+                const int row = F::template in_pos<0>(t, m, q);
+                v[m * R0 + q] = FT_IN(row, rows_in, FT_DBG_R2C_LOAD) && FT_IN(c + 1, ncols, FT_DBG_R2C_LOAD)
+                                    ? __ldg(reinterpret_cast<const float2*>(src + (size_t)row * in_pitch))
+                                    : make_float2(0.f, 0.f);
+            }
     } else {
 #pragma unroll
         for (int m = 0; m < G0; ++m)
@@ -98,7 +104,7 @@ __device__ __forceinline__ void r2c_block(const float* __restrict__ in, int rows
             for (int q = 0; q < R0; ++q) {
                 const int row = F::template in_pos<0>(t, m, q) - row0;
                 float2 x = make_float2(0.f, 0.f);
-                if (colok && row >= 0 && row < rows_in)
+                if (colok && row >= 0 && row < rows_in && FT_IN(c + 1, ncols, FT_DBG_R2C_LOAD))
                     x = __ldg(reinterpret_cast<const float2*>(src + (size_t)row * in_pitch));
                 v[m * R0 + q] = x;
             }
@@ -153,7 +159,10 @@ __device__ __forceinline__ void c2r_block(const float2* __restrict__ in, int nco
         for (int q = 0; q < R0; ++q) {
             const int n = F::template in_pos<0>(t, m, q);
             const bool up = m + G0 * q < E / 2;
-            float4 g = *reinterpret_cast<const float4*>(stg + (up ? n : N - n) * 2 * B + 2 * f);
+            const int row = up ? n : N - n;
+            float4 g = FT_IN(row, N / 2 + 1, FT_DBG_C2R_STAGE)
+                           ? *reinterpret_cast<const float4*>(stg + row * 2 * B + 2 * f)
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
             g.x *= mid_scale; g.y *= mid_scale; g.z *= mid_scale; g.w *= mid_scale;
             v[m * R0 + q] = up ? make_float2(g.x - g.w, g.y + g.z)      // A + i B
                                : make_float2(g.x + g.w, g.z - g.y);     // conj A + i conj B
@@ -196,7 +205,7 @@ __device__ __forceinline__ void c2r_block(const float2* __restrict__ in, int nco
             const unsigned* src = bm + (w / TPB) * NT + (w % TPB) * 128 + lane;
             unsigned x = max(max(src[0], src[32]), max(src[64], src[96]));
             x = __reduce_max_sync(0xffffffffu, x);
-            if (lane == 0) tmax[(size_t)w * nbx + bx] = x;
+            if (lane == 0 && FT_IN(bx, nbx, FT_DBG_C2R_STORE)) tmax[(size_t)w * nbx + bx] = x;
         }
     }
     if (!colok) return;
@@ -207,7 +216,7 @@ __device__ __forceinline__ void c2r_block(const float2* __restrict__ in, int nco
 #pragma unroll
         for (int q = 0; q < RL; ++q) {
             const int rr = F::out_pos(t, m, q) - row0;
-            if ((unsigned)rr < (unsigned)rows_out)
+            if ((unsigned)rr < (unsigned)rows_out && FT_IN(c + 1, ncols, FT_DBG_C2R_STORE))
                 *reinterpret_cast<float2*>(dst + (size_t)rr * out_pitch) =
                     make_float2(v[m * RL + q].x * out_scale, v[m * RL + q].y * out_scale);
         }
@@ -286,7 +295,8 @@ __device__ __forceinline__ void rows_block(float2* __restrict__ base, int W, int
                 if constexpr (INTERP == FT_INTERP_LINEAR) {
                     // taps c0, c0 + 1; outside 0 .. W-1 the padding's zeros
                     const int cc = min(max(c0, -2), W);
-                    const float2 a0 = myrow[cc], a1 = myrow[cc + 1];
+                    const bool ok = FT_IN(cc + 3, WP, FT_DBG_NVMT_GATHER) && FT_IN(cc + 2, WP, FT_DBG_NVMT_GATHER);
+                    const float2 a0 = ok ? myrow[cc] : zero, a1 = ok ? myrow[cc + 1] : zero;
                     acc = make_float2(fmaf(fr, a1.x - a0.x, a0.x), fmaf(fr, a1.y - a0.y, a0.y));
                 } else {
                     acc = zero;

@@ -168,7 +168,8 @@ struct FastFft {
             const int k = i % P;
             const int j = (i - k) * R + k;
 #pragma unroll
-            for (int q = 0; q < R; ++q) sm[spos(j + q * P) * B + f] = v[m * R + q];
+            for (int q = 0; q < R; ++q)
+                if (FT_IN(spos(j + q * P) * B + f, SLOTS, FT_DBG_FFT_SLOT)) sm[spos(j + q * P) * B + f] = v[m * R + q];
         }
     }
 
@@ -178,7 +179,10 @@ struct FastFft {
 #pragma unroll
         for (int m = 0; m < G; ++m)
 #pragma unroll
-            for (int q = 0; q < R; ++q) v[m * R + q] = sm[spos(in_pos<s>(t, m, q)) * B + f];
+            for (int q = 0; q < R; ++q) {
+                const int k = spos(in_pos<s>(t, m, q)) * B + f;
+                v[m * R + q] = FT_IN(k, SLOTS, FT_DBG_FFT_SLOT) ? sm[k] : make_float2(0.f, 0.f);
+            }
     }
 
     // The barriers of run<s> for the threads of a block that hold no transform of

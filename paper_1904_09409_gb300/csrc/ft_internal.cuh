@@ -16,6 +16,45 @@
 // (about 2 s) gives up (ft_plan_set_wait_cycles changes it per plan)
 #define FT_WAIT_CYCLES 4000000000ll
 
+// ------------------------------------------------ bounds-checked debug build
+// Compiled with -DFT_DEBUG (libfunnel_debug.so, which the Python binding loads
+// when FT_DEBUG=1), every gather / scatter index of the kernels passes through
+// FT_IN(index, size, code): an index outside [0, size) sets the bit `code` in
+// the translation unit's flag word and the access is skipped (a load reads 0).
+// Nothing traps; ft_debug_flags() reads and clears the words of all units.  In
+// the normal build FT_IN is the constant true and the checks compile away.
+#define FT_DBG_R2C_LOAD 1u        // step 1: image rows / columns read
+#define FT_DBG_R2C_STORE 2u       // step 1: half-spectrum rows written
+#define FT_DBG_C2R_STAGE 4u       // step 4: Hermitian rows staged / gathered
+#define FT_DBG_C2R_STORE 8u       // step 4: map rows, tile maxima written
+#define FT_DBG_NVMT_GATHER 16u    // step 2: interpolation taps of a staged row
+#define FT_DBG_FFT_SLOT 32u       // exchange slots of the register FFT
+#define FT_DBG_NVMT_ADJ 64u       // transpose of step 2: samples gathered back
+#define FT_DBG_PEAK_STAGE 128u    // peak pass: staged tile cells
+#ifdef FT_DEBUG
+static __device__ unsigned g_ft_debug;
+__device__ __forceinline__ bool ft_in_range(long long i, long long n, unsigned code) {
+    if (i >= 0 && i < n) return true;
+    atomicOr(&g_ft_debug, code);
+    return false;
+}
+#define FT_IN(i, n, code) ft_in_range((long long)(i), (long long)(n), (code))
+#define FT_DEBUG_READER(name)                                                 \
+    unsigned name() {                                                         \
+        unsigned v = 0, z = 0;                                                \
+        if (cudaMemcpyFromSymbol(&v, g_ft_debug, sizeof(v)) != cudaSuccess) return 0x80000000u; \
+        cudaMemcpyToSymbol(g_ft_debug, &z, sizeof(z));                        \
+        return v;                                                             \
+    }
+#else
+#define FT_IN(i, n, code) true
+#define FT_DEBUG_READER(name) \
+    unsigned name() { return 0u; }
+#endif
+// the flag words of the units with checks (host; the device must be idle)
+unsigned ft_debug_read_fast();
+unsigned ft_debug_read_peak_sparse();
+
 // One FFT length N = 2^a 3^b: its radix sequence and twiddle table
 // tw[t] = exp(-2 pi i t / N), t in [0, N), rounded to FP32 from FP64 values.
 struct FftLen {

@@ -162,7 +162,7 @@ k_nvmt_rows_adjoint_fast(float2* __restrict__ ws, int W, int Hp, int L, const fl
         if (l >= 1) {
 #pragma unroll
             for (int j = 0; j < ND; ++j) {
-                if (rem[j] > lim && xp[j] >= -N / 2 && xp[j] < N / 2) {
+                if (rem[j] > lim && xp[j] >= -N / 2 && xp[j] < N / 2 && FT_IN(xp[j] + N / 2, N, FT_DBG_NVMT_ADJ)) {
                     const float fr = (float)(Hp - 1 - rem[j]) * inv;
                     const float w = INTERP == FT_INTERP_LINEAR ? (j == 0 ? 1.f - fr : fr) : keys_w(fr - (float)(DLO + j));
                     const float2 g = sm[spos(xp[j] + N / 2) * B + f];
@@ -177,6 +177,8 @@ k_nvmt_rows_adjoint_fast(float2* __restrict__ ws, int W, int Hp, int L, const fl
         row[x] = acc;
     }
 }
+
+FT_DEBUG_READER(ft_debug_read_fast)
 
 // ------------------------------------------------------------------ dispatch
 #define FT_FAST_LENGTHS(X) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(8192) X(192) X(384) X(768) X(1536)

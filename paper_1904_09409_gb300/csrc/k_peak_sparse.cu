@@ -40,6 +40,8 @@ k_peak_sparse(const float* __restrict__ map, const unsigned* __restrict__ tmax, 
                       out + (size_t)img * K, count + img, spsm, sh);
 }
 
+FT_DEBUG_READER(ft_debug_read_peak_sparse)
+
 // Tile maxima of given maps: one warp per tile of PT_ROWS x PT_COLS cells (the
 // last row / column of tiles ragged), lane l reading columns 2 (l mod 8) + 0, 1
 // of rows l / 8 + 4 j (8-byte loads, 64 bytes per row, all 4 in flight); NaN

@@ -95,12 +95,15 @@ __device__ __forceinline__ void peak_sparse_block(const float* __restrict__ m, c
                         const int r = rb + u * spp;
                         int t = t0 - 1 + r;
                         t = t < 0 ? t + Hp : (t >= Hp ? t - Hp : t);
-                        x[u] = (cok && r < th + 2) ? fabsf(__ldg(m + (size_t)t * S + sc)) : 0.f;
+                        x[u] = (cok && r < th + 2 && FT_IN(t, Hp, FT_DBG_PEAK_STAGE) && FT_IN(sc, S, FT_DBG_PEAK_STAGE))
+                                   ? fabsf(__ldg(m + (size_t)t * S + sc))
+                                   : 0.f;
                     }
 #pragma unroll
                     for (int u = 0; u < 16; ++u) {
                         const int r = rb + u * spp;
-                        if (cok && r < th + 2) stg[r * pitch + c] = x[u];
+                        if (cok && r < th + 2 && FT_IN(r * pitch + c, (TH + 2) * pitch, FT_DBG_PEAK_STAGE))
+                            stg[r * pitch + c] = x[u];
                     }
                 }
             }

@@ -277,6 +277,22 @@ const char* ft_status_string(ft_status s) {
 
 const char* ft_last_error(void) { return g_last_error; }
 
+int ft_debug_build(void) {
+#ifdef FT_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+ft_status ft_debug_flags(uint32_t* flags) {
+    if (!flags) return FT_ERR_INVALID_ARG;
+    *flags = 0;
+    FT_CUDA(cudaDeviceSynchronize(), "ft_debug_flags");
+    *flags = ft_debug_read_fast() | ft_debug_read_peak_sparse();
+    return FT_OK;
+}
+
 ft_status ft_plan_create(ft_plan* out, int H, int W, int n_slope, int n_intercept, int interp) {
     return ft_plan_create_space(out, H, W, n_slope, n_intercept, interp, FT_SPACE_REGULAR);
 }

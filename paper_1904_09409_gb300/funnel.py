@@ -14,7 +14,8 @@ from typing import Optional, Tuple
 import numpy as np
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "libfunnel.so")
+# FT_DEBUG=1 in the environment loads the bounds-checked build (ft_debug_flags)
+LIB_PATH = os.path.join(PKG, "libfunnel_debug.so" if os.environ.get("FT_DEBUG") == "1" else "libfunnel.so")
 
 FT_OK = 0
 FT_ERR_INVALID_ARG = 1
@@ -41,6 +42,7 @@ EXPORTED = (
     "ft_abs_mse_backward", "ft_detect", "ft_detect_launches",
     "ft_plan_set_wait_cycles", "ft_plan_get_wait_cycles", "ft_plan_inject_alloc_failures",
     "ft_batch_config", "ft_batch_set_config", "ft_batch_tune_ms", "ft_batch_launches", "ft_fma_probe",
+    "ft_debug_flags", "ft_debug_build",
 )
 FT_WAIT_CYCLES_DEFAULT = 4000000000
 FT_PRECISION_FP32 = 0
@@ -150,6 +152,10 @@ def lib() -> ctypes.CDLL:
     L.ft_batch_launches.restype = ci
     L.ft_fma_probe.argtypes = [vp, ci, ci, vp]
     L.ft_fma_probe.restype = ci
+    L.ft_debug_flags.argtypes = [ctypes.POINTER(ctypes.c_uint32)]
+    L.ft_debug_flags.restype = ci
+    L.ft_debug_build.argtypes = []
+    L.ft_debug_build.restype = ci
     L.ft_detect_launches.argtypes = [vp, ci, ci]
     L.ft_detect_launches.restype = ci
     for name in ("ft_plan_variant_count", "ft_plan_set_variant", "ft_plan_get_variant", "ft_batch_create",
@@ -456,6 +462,18 @@ def ft_fma_probe(out, blocks: int, iters: int, stream=None) -> int:
     op = _dev_ptr(out, "float32", blocks * 256, "out")
     _check(lib().ft_fma_probe(op, int(blocks), int(iters), _stream_ptr(stream)), "ft_fma_probe")
     return blocks * 256 * iters * 16
+
+
+def ft_debug_flags() -> int:
+    """Index-check failures recorded by the debug build since the last call
+    (FT_DBG_* bits; always 0 in the normal build).  Waits for the device."""
+    v = ctypes.c_uint32(0)
+    _check(lib().ft_debug_flags(ctypes.byref(v)), "ft_debug_flags")
+    return int(v.value)
+
+
+def ft_debug_build() -> bool:
+    return bool(lib().ft_debug_build())
 
 
 def ft_last_error() -> str:
