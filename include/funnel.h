@@ -338,19 +338,22 @@ ft_status ft_tc_dft64(const void* d_x, void* d_y, int nvec, int sign, int precis
 ft_status ft_plan_set_precision(ft_plan plan, int precision);
 int ft_plan_get_precision(ft_plan plan);
 
-/* Error flags of the plan's tensor-core kernels: bit 0 is set when a wait for
- * the tensor cores timed out (after ft_plan_get_wait_cycles SM cycles, about
- * 2 s by default).  A row group whose wait gave up sets the bit, waits for its
- * own issued MMAs with the default bound, frees its tensor memory with the rest
- * of its block and stops, so the rows it had not finished are left incomplete;
- * the CUDA context stays usable.  Waits for all work on the plan's device,
+/* Error flags of the plan's device-side waits, each bounded by
+ * ft_plan_get_wait_cycles SM cycles (about 2 s by default).  Bit 0: a wait for
+ * the tensor cores timed out; the row group that gave up waits for its own
+ * issued MMAs with the default bound, frees its tensor memory with the rest of
+ * its block and stops, so the rows it had not finished are left incomplete.
+ * Bit 1: a wait of the FP32 row kernel (steps 2-3) for the bulk copies that
+ * stage its spectrum rows timed out; the block waits for its copies in flight
+ * with the default bound and returns without writing its rows.  The CUDA
+ * context stays usable either way.  Waits for all work on the plan's device,
  * copies the flags to *flags (host) and clears them; returns FT_ERR_TIMEOUT
- * when bit 0 was set (ft_last_error() says so), FT_OK otherwise (flags 0 when
- * no split precision was ever set). */
+ * when a bit was set (ft_last_error() says which), FT_OK otherwise. */
 ft_status ft_plan_tc_errors(ft_plan plan, uint32_t* flags);
 
-/* Bound, in SM cycles, of every wait of the plan's tensor-core kernels for
- * their GEMMs (FT_WAIT_CYCLES_DEFAULT, about 2 s at 2 GHz, after creation).
+/* Bound, in SM cycles, of every device-side wait of the plan's kernels (the
+ * tensor-core kernels for their GEMMs, the FP32 row kernel for its bulk
+ * copies; FT_WAIT_CYCLES_DEFAULT, about 2 s at 2 GHz, after creation).
  * The limit is checked before each try, so 0 makes every such wait give up at
  * once: a test setting that runs the timeout path (flag, drain, free, stop)
  * without any GPU fault.  cycles < 0 is FT_ERR_INVALID_ARG.  Changes later

@@ -16,6 +16,7 @@
 //    rounding of the exact fraction).
 #pragma once
 
+#include "async_copy.cuh"
 #include "fft_fast.cuh"
 
 // The last pass of the column R2C and the split of each complex transform (two
@@ -232,9 +233,15 @@ __host__ __device__ constexpr int srow_pitch(int W) { return W + 4; }
 // after): the NVMT gather with the exact positions x' H' / (2 l), then the
 // exp(+j) transform along x'.  Row 0 becomes zero.  Shared memory: the larger
 // of the FFT's exchange buffer and B staged rows of srow_pitch(W) complex.
-template <int N, int INTERP, int B>
-__device__ __forceinline__ void rows_block(float2* __restrict__ base, int W, int Hp, int L,
-                                           const float2* __restrict__ stw, int bx, float2* sm) {
+// BULK: each staged row arrives by one bulk copy (the copy engine, not the
+// threads' load/store path) completing on an mbarrier, waited for with the
+// bound `wait` in SM cycles; when a wait runs out, bit 1 of *err is set, the
+// block waits (default bound) for its copies in flight and returns false
+// without writing.  Otherwise every thread copies 16-byte pieces (cp.async).
+template <int N, int INTERP, int B, bool BULK = false>
+__device__ __forceinline__ bool rows_block(float2* __restrict__ base, int W, int Hp, int L,
+                                           const float2* __restrict__ stw, int bx, float2* sm,
+                                           unsigned* err = nullptr, long long wait = FT_WAIT_CYCLES) {
     constexpr int E = fs_E(N), T = N / E;
     constexpr int R0 = fs_radix(N, 0), G0 = E / R0;
     constexpr int RL = fs_radix(N, fs_nst(N) - 1), GL = E / RL;
@@ -250,24 +257,46 @@ __device__ __forceinline__ void rows_block(float2* __restrict__ base, int W, int
     const int l0 = bx * B;
     const int l = l0 + f;
 
-    // stage the block's B spectrum rows (W complex each) with 16-byte async copies
+    // stage the block's B spectrum rows (W complex each)
     const int chunks = W >> 1;                         // two complex per 16 bytes
     if (threadIdx.x < 2 * B) {
         const int r = threadIdx.x >> 1;
         *reinterpret_cast<float4*>(srow + r * WP + ((threadIdx.x & 1) ? W + 2 : 0)) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-#pragma unroll
-    for (int r = 0; r < B; ++r) {
-        float2* dst = srow + r * WP + 2;
-        const float2* src = base + (size_t)(l0 + r) * N;
-        if (l0 + r < L) {
-            for (int c = threadIdx.x; c < chunks; c += fs_T(N) * B) cp_async16(dst + 2 * c, src + 2 * c);
-        } else {
-            for (int c = threadIdx.x; c < chunks; c += fs_T(N) * B)
-                *reinterpret_cast<float4*>(dst + 2 * c) = make_float4(0.f, 0.f, 0.f, 0.f);
+    if constexpr (BULK) {
+        __shared__ uint64_t mbar;
+        const uint32_t mb = smem_u32(&mbar);
+        const int nrows = min(B, L - l0);              // >= 1: the grid covers rows 0 .. L-1
+        if (threadIdx.x == 0) {
+            mbar_init(mb, 1);
+            mbar_arrive_expect_tx(mb, (uint32_t)(nrows * W * sizeof(float2)));
+            for (int r = 0; r < nrows; ++r)
+                bulk_g2s(srow + r * WP + 2, base + (size_t)(l0 + r) * N, (uint32_t)(W * sizeof(float2)), mb);
         }
+        for (int r = nrows; r < B; ++r)                // rows past the end: zeros
+            for (int c = threadIdx.x; c < chunks; c += fs_T(N) * B)
+                *reinterpret_cast<float4*>(srow + r * WP + 2 + 2 * c) = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncthreads();                               // the mbarrier is initialised
+        const bool ok = mbar_wait(mb, 0, wait);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0 && err) atomicOr(err, 2u);
+            mbar_wait(mb, 0);                          // the copies in flight land first
+            return false;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < B; ++r) {
+            float2* dst = srow + r * WP + 2;
+            const float2* src = base + (size_t)(l0 + r) * N;
+            if (l0 + r < L) {
+                for (int c = threadIdx.x; c < chunks; c += fs_T(N) * B) cp_async16(dst + 2 * c, src + 2 * c);
+            } else {
+                for (int c = threadIdx.x; c < chunks; c += fs_T(N) * B)
+                    *reinterpret_cast<float4*>(dst + 2 * c) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        cp_async_wait_all();
     }
-    cp_async_wait_all();
     __syncthreads();
 
     float2 v[E];
@@ -318,7 +347,7 @@ __device__ __forceinline__ void rows_block(float2* __restrict__ base, int W, int
     }
     __syncthreads();                                   // the staged rows are dead from here
     F::template run<0>(v, sm, t, f, stw);
-    if (l >= L) return;
+    if (l >= L) return true;
     float2* row = base + (size_t)l * N;
 #pragma unroll
     for (int m = 0; m < GL; ++m)
@@ -329,4 +358,5 @@ __device__ __forceinline__ void rows_block(float2* __restrict__ base, int W, int
             if ((s + N / 2) & 1) val = make_float2(-val.x, -val.y);
             row[s] = val;
         }
+    return true;
 }

@@ -239,7 +239,8 @@ cudaError_t launch_col_c2r_fast(const float2* in, int ncols, int in_pitch, size_
 // A tile is 256 cells: 128 / B rows of one column block of 2B columns.
 __host__ __device__ constexpr int c2r_tile_rows(int N) { return 128 / fs_Bc2r(N); }
 bool c2r_tile_shape(int N, int* rows, int* cols, int* bands);
+// (err: bit 1 set when a bulk-copy wait ran out after `wait` SM cycles)
 cudaError_t launch_nvmt_rows_fast(float2* ws, int W, int Hp, int L, int interp, const FftLen& fx,
-                                  int batch, cudaStream_t st, bool pdl = false);
+                                  int batch, cudaStream_t st, bool pdl, unsigned* err, long long wait);
 cudaError_t launch_nvmt_rows_adjoint_fast(float2* ws, int W, int Hp, int L, int interp,
                                           const FftLen& fx, int batch, cudaStream_t st);

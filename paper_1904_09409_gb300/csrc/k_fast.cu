@@ -93,11 +93,13 @@ k_col_r2c_loss_fast(const float* __restrict__ map, const float* __restrict__ tar
 // at most 64 registers, so that 4 blocks of 256 threads share a multiprocessor
 template <int N, int INTERP>
 __global__ void __launch_bounds__(fs_T(N) * fs_Brow(N), 1024 / (fs_T(N) * fs_Brow(N)))
-k_nvmt_rows_fast(float2* __restrict__ ws, int W, int Hp, int L, const float2* __restrict__ stw) {
-    extern __shared__ float2 sm[];
+k_nvmt_rows_fast(float2* __restrict__ ws, int W, int Hp, int L, const float2* __restrict__ stw,
+                 unsigned* __restrict__ err, long long wait) {
+    extern __shared__ __align__(16) float2 sm[];
     pdl_trigger();
     pdl_wait();
-    rows_block<N, INTERP, fs_Brow(N)>(ws + (size_t)blockIdx.y * L * N, W, Hp, L, stw, blockIdx.x, sm);
+    rows_block<N, INTERP, fs_Brow(N), true>(ws + (size_t)blockIdx.y * L * N, W, Hp, L, stw, blockIdx.x, sm, err,
+                                            wait);
 }
 
 template <int N, int INTERP>
@@ -226,21 +228,22 @@ static cudaError_t go_c2r(const float2* in, int ncols, int in_pitch, size_t in_i
 
 template <int N, int INTERP>
 static cudaError_t go_rows_i(float2* ws, int W, int Hp, int L, const float2* stw, int batch, cudaStream_t st,
-                             bool pdl) {
+                             bool pdl, unsigned* err, long long wait) {
     constexpr int B = fs_Brow(N);
     const size_t slots = FastFft<N, +1, B>::SLOTS, rows = (size_t)srow_pitch(W) * B;
     const size_t sm = (slots > rows ? slots : rows) * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_nvmt_rows_fast<N, INTERP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     dim3 grid((L + B - 1) / B, batch);
-    return launch_maybe_pdl(k_nvmt_rows_fast<N, INTERP>, grid, dim3(fs_T(N) * B), sm, st, pdl, ws, W, Hp, L, stw);
+    return launch_maybe_pdl(k_nvmt_rows_fast<N, INTERP>, grid, dim3(fs_T(N) * B), sm, st, pdl, ws, W, Hp, L, stw,
+                            err, wait);
 }
 
 template <int N>
 static cudaError_t go_rows(float2* ws, int W, int Hp, int L, int interp, const float2* stw, int batch,
-                           cudaStream_t st, bool pdl) {
-    return interp == FT_INTERP_LINEAR ? go_rows_i<N, FT_INTERP_LINEAR>(ws, W, Hp, L, stw, batch, st, pdl)
-                                      : go_rows_i<N, FT_INTERP_CUBIC>(ws, W, Hp, L, stw, batch, st, pdl);
+                           cudaStream_t st, bool pdl, unsigned* err, long long wait) {
+    return interp == FT_INTERP_LINEAR ? go_rows_i<N, FT_INTERP_LINEAR>(ws, W, Hp, L, stw, batch, st, pdl, err, wait)
+                                      : go_rows_i<N, FT_INTERP_CUBIC>(ws, W, Hp, L, stw, batch, st, pdl, err, wait);
 }
 
 template <int N, int INTERP>
@@ -319,9 +322,10 @@ bool c2r_tile_shape(int N, int* rows, int* cols, int* bands) {
 }
 
 cudaError_t launch_nvmt_rows_fast(float2* ws, int W, int Hp, int L, int interp, const FftLen& fx,
-                                  int batch, cudaStream_t st, bool pdl) {
+                                  int batch, cudaStream_t st, bool pdl, unsigned* err, long long wait) {
+    if (((uintptr_t)ws & 15) || (W & 1) || wait < 0) return cudaErrorInvalidValue;   // bulk-copy alignment
     switch (fx.N) {
-#define X(n) case n: return go_rows<n>(ws, W, Hp, L, interp, fx.stw, batch, st, pdl);
+#define X(n) case n: return go_rows<n>(ws, W, Hp, L, interp, fx.stw, batch, st, pdl, err, wait);
         FT_FAST_LENGTHS(X)
 #undef X
     }

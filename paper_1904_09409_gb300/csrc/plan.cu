@@ -244,7 +244,9 @@ static cudaError_t nvmt_rows(ft_plan p, float2* ws, int batch, cudaStream_t st) 
     if (p->precision != FT_PRECISION_FP32 && p->S == 4096)
         return launch_nvmt_rows_tc4096(ws, p->W, p->Hp, p->L, p->interp, p->precision, p->d_tc_err, p->tc_wait,
                                        batch, st);
-    if (p->use_fast_x) return launch_nvmt_rows_fast(ws, p->W, p->Hp, p->L, p->interp, p->fx, batch, st, p->pdl);
+    if (p->use_fast_x)
+        return launch_nvmt_rows_fast(ws, p->W, p->Hp, p->L, p->interp, p->fx, batch, st, p->pdl, p->d_tc_err,
+                                     p->tc_wait);
     return launch_nvmt_rows(ws, p->W, p->S, p->Hp, p->L, p->interp, p->fx, p->row_logB_x, batch, st);
 }
 
@@ -366,6 +368,15 @@ ft_status ft_plan_create_space(ft_plan* out, int img_H, int img_W, int n_slope, 
         delete p;
         return cuda_fail(e, "cudaMemcpy(twiddles)");
     }
+    // the error word of the device-side waits (bulk copies, tensor cores)
+    e = cudaMalloc(&p->d_tc_err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(p->d_tc_err, 0, sizeof(unsigned));
+    if (e != cudaSuccess) {
+        if (p->d_tc_err) cudaFree(p->d_tc_err);
+        cudaFree(p->d_tw);
+        delete p;
+        return cuda_fail(e, "cudaMalloc(error word)");
+    }
     p->fy.tw = p->d_tw;
     p->fx.tw = p->d_tw + fy.N;
     p->fy.stw = fast_y ? p->d_tw + fy.N + fx.N : nullptr;
@@ -466,20 +477,12 @@ ft_status ft_plan_set_precision(ft_plan p, int precision) {
             return ft_record_error(FT_ERR_UNSUPPORTED_SIZE,
                                    "split precision: a length-4096 transform (n_slope 4096 with the linear or "
                                    "cubic interpolator, or n_intercept 4096) is needed");
-        if (!p->d_tc_err) {
-            int cur = 0;
-            FT_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
-            FT_CUDA(cudaSetDevice(p->device), "cudaSetDevice");
-            cudaError_t e = cudaMalloc(&p->d_tc_err, sizeof(unsigned));
-            if (e == cudaSuccess) e = cudaMemset(p->d_tc_err, 0, sizeof(unsigned));
-            if (e == cudaSuccess) e = tc_prepare();
-            cudaSetDevice(cur);
-            if (e != cudaSuccess) {
-                if (p->d_tc_err) cudaFree(p->d_tc_err);
-                p->d_tc_err = nullptr;
-                return ft_record_cuda(e, "tensor-core error flags");
-            }
-        }
+        int cur = 0;
+        FT_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
+        FT_CUDA(cudaSetDevice(p->device), "cudaSetDevice");
+        const cudaError_t e = tc_prepare();
+        cudaSetDevice(cur);
+        if (e != cudaSuccess) return ft_record_cuda(e, "tensor-core tables");
     }
     p->precision = precision;
     return FT_OK;
@@ -502,6 +505,9 @@ ft_status ft_plan_tc_errors(ft_plan p, uint32_t* flags) {
     if (*flags & 1u)
         return ft_record_error(FT_ERR_TIMEOUT, "ft_plan_tc_errors: a wait for the tensor cores timed out; the rows "
                                                "of the blocks that gave up are incomplete");
+    if (*flags & 2u)
+        return ft_record_error(FT_ERR_TIMEOUT, "ft_plan_tc_errors: a wait for a bulk copy of the NVMT rows timed "
+                                               "out; the rows of the blocks that gave up were not written");
     return FT_OK;
 }
 

@@ -15,10 +15,10 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include "async_copy.cuh"
 #include "ft_internal.cuh"
 
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // byte offset of element (r, k) in the K-major no-swizzle layout of a [R][K] tile
 __device__ __forceinline__ uint32_t kmajor_off(int r, int k, int K) {
@@ -66,31 +66,6 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 // make generic-proxy writes to shared memory visible to the tensor cores
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// bounded wait for the completion of phase `parity`: false once `limit` SM
-// cycles have passed (FT_WAIT_CYCLES, about 2 s, by default).  The limit is
-// checked before every try, so a limit of 0 gives up at once (the plan's test
-// setting that exercises the timeout path).
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit = FT_WAIT_CYCLES) {
-    const long long t0 = clock64();
-    for (;;) {
-        if (clock64() - t0 >= limit) return false;
-        if (mbar_try(mbar, parity)) return true;
-    }
-}
 
 // 16 consecutive 32-bit columns starting at `taddr` for this warp's 32 lanes
 __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {

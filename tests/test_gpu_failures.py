@@ -84,3 +84,27 @@ def test_injected_allocation_failure_leaves_the_plan_usable(torch):
         assert _gpu.rel_l2(got[i], oracle.funnel_ref(imgs[i], W, H)) <= 1e-5
         pk = [(int(p["t"]), int(p["s"]), float(p["value"])) for p in recs[i][:cnt[i]]]
         assert pk == oracle.peaks_ref(np.abs(got[i]).astype(np.float64), 5)
+
+
+@pytest.mark.parametrize("interp", ["linear", "cubic"])
+def test_bulk_copy_wait_timeout_fp32_rows(torch, interp):
+    """The FP32 row kernel stages its spectrum rows with bulk copies completing on
+    an mbarrier; with the plan's wait limit at 0 every such wait gives up: the
+    block drains its copies, writes nothing, and ft_plan_tc_errors returns
+    FT_ERR_TIMEOUT; with the default limit the next map is the oracle's."""
+    from paper_1904_09409_gb300 import funnel as f
+    H = W = 256
+    imgs = _images(2, H, W, seed=3)
+    with f.Plan(H, W, W, H, interp) as plan:
+        assert f.ft_plan_tc_errors(plan) == 0
+        f.ft_plan_set_wait_cycles(plan, 0)
+        _gpu.forward(plan, imgs)
+        with pytest.raises(f.FunnelError) as e:
+            f.ft_plan_tc_errors(plan)
+        assert e.value.status == f.FT_ERR_TIMEOUT
+        assert "bulk copy" in f.ft_last_error()
+        f.ft_plan_set_wait_cycles(plan, f.FT_WAIT_CYCLES_DEFAULT)
+        got = _gpu.forward(plan, imgs)
+        assert f.ft_plan_tc_errors(plan) == 0
+    for i in range(2):
+        assert _gpu.rel_l2(got[i], oracle.funnel_ref(imgs[i], W, H, interp)) <= 1e-5
