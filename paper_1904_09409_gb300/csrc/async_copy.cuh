@@ -4,6 +4,7 @@
 // moves the bytes; the issuing thread only posts one instruction).
 #pragma once
 
+#include <cuda.h>
 #include <stdint.h>
 
 #include "ft_internal.cuh"
@@ -45,5 +46,17 @@ __device__ __forceinline__ void bulk_g2s(void* smem_dst, const void* gmem_src, u
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
             smem_u32(smem_dst)),
         "l"(gmem_src), "r"(bytes), "r"(mbar)
+        : "memory");
+}
+
+// 3-D tiled tensor copy (TMA) of the box at (x, y, z) of the tensor described by
+// *tmap (a __grid_constant__ kernel parameter) into this block's shared memory,
+// completing on mbar; x times the element size must be a multiple of 16 bytes
+__device__ __forceinline__ void tma_load_3d(void* smem_dst, const CUtensorMap* tmap, int x, int y, int z,
+                                            uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(smem_dst)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(mbar)
         : "memory");
 }

@@ -230,10 +230,13 @@ cudaError_t launch_col_r2c_loss_fast(const float* map, const float* target, int 
 // tmax (may be NULL; only with row0 = 0 and rows_out = N): the maxima of |out| per
 // tile of c2r_tile_shape rows x columns, [batch][N / rows][ceil(ncols / cols)] as
 // float bits
+// (err, wait: with err given, the staging goes through tensor copies whose
+// bounded waits set bit 2 of *err when they run out; without, cp.async)
 cudaError_t launch_col_c2r_fast(const float2* in, int ncols, int in_pitch, size_t in_img,
                                 const FftLen& f, float mid_scale, float* out, int row0, int rows_out,
                                 int out_pitch, size_t out_img, float out_scale, int batch,
-                                cudaStream_t st, unsigned* tmax = nullptr, bool pdl = false);
+                                cudaStream_t st, unsigned* tmax = nullptr, bool pdl = false,
+                                unsigned* err = nullptr, long long wait = FT_WAIT_CYCLES);
 // tiles of the tile maxima of launch_col_c2r_fast for length N: rows x cols
 // cells, bands = N / rows tiles per column block; false without a schedule.
 // A tile is 256 cells: 128 / B rows of one column block of 2B columns.

@@ -1,6 +1,8 @@
 // Fixed-length versions of the column and row kernels over a uniform batch
 // (see k_cols.cu and k_rows.cu for what each step computes): one block of
 // fast_blocks.cuh per CUDA block, the image index in blockIdx.y.
+#include <string.h>
+
 #include "fast_blocks.cuh"
 
 template <int N>
@@ -14,18 +16,29 @@ k_col_r2c_fast(const float* __restrict__ in, int rows_in, int ncols, int in_pitc
                              out + (size_t)blockIdx.y * out_img, out_pitch, end_scale, mid_scale, blockIdx.x, sm);
 }
 
+// tma_nb > 0: the Hermitian half is staged by tma_nb tensor copies of tma_h rows
+// (tmap describes the launch's half spectra), else by cp.async
 template <int N>
 __global__ void __launch_bounds__(fs_T(N) * fs_Bc2r(N), 1024 / (fs_T(N) * fs_Bc2r(N)))
 k_col_c2r_fast(const float2* __restrict__ in, int ncols, int in_pitch, size_t in_img,
                const float2* __restrict__ stw, float mid_scale, float* __restrict__ out, int row0,
-               int rows_out, int out_pitch, size_t out_img, float out_scale, unsigned* __restrict__ tmax) {
-    extern __shared__ float2 sm[];
+               int rows_out, int out_pitch, size_t out_img, float out_scale, unsigned* __restrict__ tmax,
+               const __grid_constant__ CUtensorMap tmap, int tma_h, int tma_nb, unsigned* __restrict__ err,
+               long long wait) {
+    extern __shared__ __align__(128) float2 sm[];
     pdl_trigger();
     pdl_wait();
     constexpr int bands = fs_E(N) * fs_T(N) / c2r_tile_rows(N);
-    c2r_block<N, fs_Bc2r(N)>(in + (size_t)blockIdx.y * in_img, ncols, in_pitch, stw, mid_scale,
-                             out + (size_t)blockIdx.y * out_img, row0, rows_out, out_pitch, out_scale,
-                             tmax ? tmax + (size_t)blockIdx.y * bands * gridDim.x : nullptr, gridDim.x, blockIdx.x, sm);
+    const float2* src = in + (size_t)blockIdx.y * in_img;
+    float* dst = out + (size_t)blockIdx.y * out_img;
+    unsigned* tm = tmax ? tmax + (size_t)blockIdx.y * bands * gridDim.x : nullptr;
+    if (tma_nb > 0)
+        c2r_block<N, fs_Bc2r(N), true>(src, ncols, in_pitch, stw, mid_scale, dst, row0, rows_out, out_pitch,
+                                       out_scale, tm, gridDim.x, blockIdx.x, sm, &tmap, tma_h, tma_nb, blockIdx.y,
+                                       err, wait);
+    else
+        c2r_block<N, fs_Bc2r(N)>(src, ncols, in_pitch, stw, mid_scale, dst, row0, rows_out, out_pitch, out_scale,
+                                 tm, gridDim.x, blockIdx.x, sm);
 }
 
 // The adjoint of step 4 fed straight from the loss of the gradient workload:
@@ -213,17 +226,73 @@ static cudaError_t go_r2c_loss(const float* map, const float* target, int ncols,
     return cudaGetLastError();
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry points (no link to
+// the driver library); null when unavailable
+typedef CUresult (*encode_tiled_fn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static encode_tiled_fn encode_tiled() {
+    static encode_tiled_fn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (encode_tiled_fn)f;
+    }
+    return fn;
+}
+
+// Tensor copies of step 4's staging: the N/2 + 1 Hermitian rows in nb boxes of
+// h <= 256 rows, h B a multiple of 8 (each box starts on a 128-byte boundary of
+// shared memory), all within the block's exchange buffer; false when that does
+// not fit, the input is not 16-byte aligned or the map cannot be encoded (the
+// kernel then stages with cp.async).
+template <int N>
+static bool c2r_tma_map(const float2* in, int in_pitch, size_t in_img, int batch, CUtensorMap* map, int* h, int* nb) {
+    constexpr int B = fs_Bc2r(N), rows = N / 2 + 1;
+    const encode_tiled_fn enc = encode_tiled();
+    if (!enc || ((uintptr_t)in & 15) || (in_pitch & 1) || (in_img & 1)) return false;
+    const int step = B >= 8 ? 1 : 8 / B;
+    int n = (rows + 255) / 256, hh = 0;
+    for (;; ++n) {
+        hh = (rows + n - 1) / n;
+        hh = (hh + step - 1) / step * step;
+        if (hh <= 256) break;
+    }
+    if ((size_t)n * hh * 2 * B > (size_t)FastFft<N, +1, B>::SLOTS) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)in_pitch, (cuuint64_t)rows, (cuuint64_t)batch};
+    const cuuint64_t strides[2] = {(cuuint64_t)in_pitch * sizeof(float2), (cuuint64_t)in_img * sizeof(float2)};
+    const cuuint32_t box[3] = {(cuuint32_t)(2 * B), (cuuint32_t)hh, 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    if (enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<float2*>(in), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    *h = hh;
+    *nb = n;
+    return true;
+}
+
 template <int N>
 static cudaError_t go_c2r(const float2* in, int ncols, int in_pitch, size_t in_img, const float2* stw,
                           float mid, float* out, int row0, int rows_out, int out_pitch, size_t out_img,
-                          float os, unsigned* tmax, int batch, cudaStream_t st, bool pdl) {
+                          float os, unsigned* tmax, int batch, cudaStream_t st, bool pdl, unsigned* err,
+                          long long wait) {
     constexpr int B = fs_Bc2r(N);
     const size_t sm = (size_t)FastFft<N, +1, B>::SLOTS * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_col_c2r_fast<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
+    CUtensorMap map;
+    memset(&map, 0, sizeof(map));
+    int h = 0, nb = 0;
+    if (!err || wait < 0 || !c2r_tma_map<N>(in, in_pitch, in_img, batch, &map, &h, &nb)) nb = 0;
     dim3 grid((ncols + 2 * B - 1) / (2 * B), batch);
     return launch_maybe_pdl(k_col_c2r_fast<N>, grid, dim3(fs_T(N) * B), sm, st, pdl, in, ncols, in_pitch, in_img, stw,
-                            mid, out, row0, rows_out, out_pitch, out_img, os, tmax);
+                            mid, out, row0, rows_out, out_pitch, out_img, os, tmax, map, h, nb, err, wait);
 }
 
 template <int N, int INTERP>
@@ -301,11 +370,11 @@ cudaError_t launch_col_r2c_loss_fast(const float* map, const float* target, int 
 cudaError_t launch_col_c2r_fast(const float2* in, int ncols, int in_pitch, size_t in_img,
                                 const FftLen& f, float mid_scale, float* out, int row0, int rows_out,
                                 int out_pitch, size_t out_img, float out_scale, int batch,
-                                cudaStream_t st, unsigned* tmax, bool pdl) {
+                                cudaStream_t st, unsigned* tmax, bool pdl, unsigned* err, long long wait) {
     if (tmax && (row0 != 0 || rows_out != f.N)) return cudaErrorInvalidValue;
     switch (f.N) {
 #define X(n) case n: return go_c2r<n>(in, ncols, in_pitch, in_img, f.stw, mid_scale, out, row0, rows_out, \
-                                      out_pitch, out_img, out_scale, tmax, batch, st, pdl);
+                                      out_pitch, out_img, out_scale, tmax, batch, st, pdl, err, wait);
         FT_FAST_LENGTHS(X)
 #undef X
     }

@@ -220,7 +220,7 @@ static cudaError_t col_c2r(ft_plan p, const float2* in, int ncols, float mid, fl
     const size_t in_img = (size_t)p->L * p->S;
     if (p->use_fast_y)
         return launch_col_c2r_fast(in, ncols, p->S, in_img, p->fy, mid, out, row0, rows_out, out_pitch,
-                                   out_img, os, batch, st, tmax, p->pdl);
+                                   out_img, os, batch, st, tmax, p->pdl, p->d_tc_err, p->tc_wait);
     if (tmax) return cudaErrorInvalidValue;
     return launch_col_c2r(in, ncols, p->S, in_img, p->fy, p->col_logB_y, mid, out, row0, rows_out,
                           out_pitch, out_img, os, batch, st);
@@ -508,6 +508,9 @@ ft_status ft_plan_tc_errors(ft_plan p, uint32_t* flags) {
     if (*flags & 2u)
         return ft_record_error(FT_ERR_TIMEOUT, "ft_plan_tc_errors: a wait for a bulk copy of the NVMT rows timed "
                                                "out; the rows of the blocks that gave up were not written");
+    if (*flags & 4u)
+        return ft_record_error(FT_ERR_TIMEOUT, "ft_plan_tc_errors: a wait for a tensor copy of step 4's columns "
+                                               "timed out; the columns of the blocks that gave up were not written");
     return FT_OK;
 }
 
