@@ -74,10 +74,18 @@ __device__ __forceinline__ void r2c_finish(float2 (&v)[fs_E(N)], float2* sm, int
 // out_pitch complex).  The first pass reads global memory directly (8-byte
 // loads of the thread's column pair): staging the image tile through shared
 // memory first measured slower on GB300 (67 vs 60 us for 32 images of 1024^2).
-template <int N, int B>
-__device__ __forceinline__ void r2c_block(const float* __restrict__ in, int rows_in, int ncols, int in_pitch,
+// TMA: the block's 2B image columns of all N expanded rows arrive by tma_nb
+// tensor copies of tma_h rows (tmap: the launch's images as [images][rows_in]
+// [ncols] floats, image `img`; rows outside the image and columns past it read
+// zeros), waited for on an mbarrier with the bound `wait`; when it runs out, bit
+// 3 of *err is set, the block waits (default bound) for its copies and returns
+// false without writing.  Otherwise the first pass reads global memory directly.
+template <int N, int B, bool TMA = false>
+__device__ __forceinline__ bool r2c_block(const float* __restrict__ in, int rows_in, int ncols, int in_pitch,
                                           int row0, const float2* __restrict__ stw, float2* __restrict__ out,
-                                          int out_pitch, float end_scale, float mid_scale, int bx, float2* sm) {
+                                          int out_pitch, float end_scale, float mid_scale, int bx, float2* sm,
+                                          const CUtensorMap* tmap = nullptr, int tma_h = 0, int tma_nb = 0,
+                                          int img = 0, unsigned* err = nullptr, long long wait = FT_WAIT_CYCLES) {
     constexpr int E = fs_E(N);
     constexpr int R0 = fs_radix(N, 0), G0 = E / R0;
     using F = FastFft<N, -1, B>;
@@ -88,7 +96,30 @@ __device__ __forceinline__ void r2c_block(const float* __restrict__ in, int rows
     const float* src = in + c;
 
     float2 v[E];
-    if (colok && row0 == 0 && rows_in == N) {          // every row is an image row
+    if constexpr (TMA) {
+        float* stg = reinterpret_cast<float*>(sm);     // [tma_nb tma_h][2B] floats
+        __shared__ uint64_t mbar;
+        const uint32_t mb = smem_u32(&mbar);
+        if (threadIdx.x == 0) {
+            mbar_init(mb, 1);
+            mbar_arrive_expect_tx(mb, (uint32_t)(tma_nb * tma_h * 2 * B * sizeof(float)));
+            for (int k = 0; k < tma_nb; ++k)
+                tma_load_3d(stg + k * tma_h * 2 * B, tmap, bx * 2 * B, k * tma_h - row0, img, mb);
+        }
+        __syncthreads();                               // the mbarrier is initialised
+        const bool ok = mbar_wait(mb, 0, wait);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0 && err) atomicOr(err, 8u);
+            mbar_wait(mb, 0);                          // the copies in flight land first
+            return false;
+        }
+#pragma unroll
+        for (int m = 0; m < G0; ++m)
+#pragma unroll
+            for (int q = 0; q < R0; ++q)
+                v[m * R0 + q] = *reinterpret_cast<const float2*>(stg + F::template in_pos<0>(t, m, q) * 2 * B + 2 * f);
+        __syncthreads();                               // the staged tile is dead before the first exchange
+    } else if (colok && row0 == 0 && rows_in == N) {   // every row is an image row
 #pragma unroll
         for (int m = 0; m < G0; ++m)
 #pragma unroll
@@ -111,6 +142,7 @@ __device__ __forceinline__ void r2c_block(const float* __restrict__ in, int rows
             }
     }
     r2c_finish<N, B>(v, sm, t, f, stw, colok, out + c, out_pitch, end_scale, mid_scale);
+    return true;
 }
 
 // Step 4 (and the transpose of step 1) for column block bx of one image: the
@@ -204,32 +236,33 @@ __device__ __forceinline__ bool c2r_block(const float2* __restrict__ in, int nco
         // Tile maxima of |map| for the peak pass: thread t holds rows t + T j,
         // j = m + GL q, of its column pair.  A tile is RS = 128 / B consecutive
         // rows of one band (rows T j + RS u .. T j + RS u + RS - 1, u < T / RS) of
-        // the block's 2B columns, 256 cells held by the RS B consecutive threads
-        // t = RS u .. RS u + RS - 1; its tile row is RS-row index T j / RS + u.
-        // Each thread puts max(|re|, |im|) of its element of band j (the stored,
-        // scaled values; NaN counts as 0, like a cell that is never a peak) at
-        // bm[j][thread] in the exchange buffer, which the FFT no longer reads;
-        // then every warp reduces tiles w, w + warps, ...: 4 conflict-free words
-        // per lane and one redux.sync.
+        // the block's 2B columns: 256 cells held, one each, by the 128
+        // consecutive threads RS B u .. RS B u + 127, i.e. by whole warps
+        // 4u .. 4u + 3.  Every warp reduces its 32 values of band j with one
+        // redux.sync (max(|re|, |im|) of the stored, scaled values; NaN counts
+        // as 0, like a cell that is never a peak), lane 0 keeps the partial in
+        // the exchange buffer, which the FFT no longer reads, and one thread per
+        // tile combines its four warps' partials.
         constexpr int NT = fs_T(N) * B;                // threads of the block
+        constexpr int NW = NT / 32;
         constexpr int RS = 128 / B, TPB = fs_T(N) / RS;   // tile rows, tiles per band
         static_assert(RS * B == 128 && TPB * RS == fs_T(N), "a tile is 128 threads' values");
-        static_assert(E * NT <= FastFft<N, +1, B>::SLOTS * 2, "band maxima fit the exchange buffer");
-        unsigned* bm = reinterpret_cast<unsigned*>(sm);
+        static_assert(E * NW <= FastFft<N, +1, B>::SLOTS * 2, "partial maxima fit the exchange buffer");
+        unsigned* part = reinterpret_cast<unsigned*>(sm);  // [E][NW]
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
         for (int m = 0; m < GL; ++m)
 #pragma unroll
             for (int q = 0; q < RL; ++q) {
                 const float a = fabsf(v[m * RL + q].x * out_scale), b = fabsf(v[m * RL + q].y * out_scale);
-                bm[(m + GL * q) * NT + threadIdx.x] = colok ? __float_as_uint(fmaxf(fmaxf(a, b), 0.f)) : 0u;
+                const unsigned x = __reduce_max_sync(0xffffffffu, colok ? __float_as_uint(fmaxf(fmaxf(a, b), 0.f)) : 0u);
+                if (lane == 0) part[(m + GL * q) * NW + warp] = x;
             }
         __syncthreads();
-        const int lane = threadIdx.x & 31;
-        for (int w = threadIdx.x >> 5; w < E * TPB; w += NT / 32) {
-            const unsigned* src = bm + (w / TPB) * NT + (w % TPB) * 128 + lane;
-            unsigned x = max(max(src[0], src[32]), max(src[64], src[96]));
-            x = __reduce_max_sync(0xffffffffu, x);
-            if (lane == 0 && FT_IN(bx, nbx, FT_DBG_C2R_STORE)) tmax[(size_t)w * nbx + bx] = x;
+        for (int w = threadIdx.x; w < E * TPB; w += NT) {
+            const unsigned* p = part + (w / TPB) * NW + 4 * (w % TPB);
+            const unsigned x = max(max(p[0], p[1]), max(p[2], p[3]));
+            if (FT_IN(bx, nbx, FT_DBG_C2R_STORE)) tmax[(size_t)w * nbx + bx] = x;
         }
     }
     if (!colok) return true;

@@ -5,15 +5,24 @@
 
 #include "fast_blocks.cuh"
 
+// tma_nb > 0: the image columns are staged by tma_nb tensor copies of tma_h
+// rows (tmap describes the launch's images), else read from global memory
 template <int N>
 __global__ void __launch_bounds__(fs_T(N) * fs_Bcol(N), 1024 / (fs_T(N) * fs_Bcol(N)))
 k_col_r2c_fast(const float* __restrict__ in, int rows_in, int ncols, int in_pitch, size_t in_img,
                int row0, const float2* __restrict__ stw, float2* __restrict__ out, int out_pitch,
-               size_t out_img, float end_scale, float mid_scale) {
-    extern __shared__ float2 sm[];
+               size_t out_img, float end_scale, float mid_scale, const __grid_constant__ CUtensorMap tmap,
+               int tma_h, int tma_nb, unsigned* __restrict__ err, long long wait) {
+    extern __shared__ __align__(128) float2 sm[];
     pdl_trigger();
-    r2c_block<N, fs_Bcol(N)>(in + (size_t)blockIdx.y * in_img, rows_in, ncols, in_pitch, row0, stw,
-                             out + (size_t)blockIdx.y * out_img, out_pitch, end_scale, mid_scale, blockIdx.x, sm);
+    const float* src = in + (size_t)blockIdx.y * in_img;
+    float2* dst = out + (size_t)blockIdx.y * out_img;
+    if (tma_nb > 0)
+        r2c_block<N, fs_Bcol(N), true>(src, rows_in, ncols, in_pitch, row0, stw, dst, out_pitch, end_scale,
+                                       mid_scale, blockIdx.x, sm, &tmap, tma_h, tma_nb, blockIdx.y, err, wait);
+    else
+        r2c_block<N, fs_Bcol(N)>(src, rows_in, ncols, in_pitch, row0, stw, dst, out_pitch, end_scale, mid_scale,
+                                 blockIdx.x, sm);
 }
 
 // tma_nb > 0: the Hermitian half is staged by tma_nb tensor copies of tma_h rows
@@ -198,34 +207,6 @@ FT_DEBUG_READER(ft_debug_read_fast)
 // ------------------------------------------------------------------ dispatch
 #define FT_FAST_LENGTHS(X) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(8192) X(192) X(384) X(768) X(1536)
 
-template <int N>
-static cudaError_t go_r2c(const float* in, int rows_in, int ncols, int in_pitch, size_t in_img, int row0,
-                          const float2* stw, float2* out, int out_pitch, size_t out_img, float es, float ms,
-                          int batch, cudaStream_t st) {
-    constexpr int B = fs_Bcol(N);
-    const size_t sm = (size_t)FastFft<N, -1, B>::SLOTS * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(k_col_r2c_fast<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    dim3 grid((ncols + 2 * B - 1) / (2 * B), batch);
-    k_col_r2c_fast<N><<<grid, fs_T(N) * B, sm, st>>>(in, rows_in, ncols, in_pitch, in_img, row0, stw, out,
-                                                     out_pitch, out_img, es, ms);
-    return cudaGetLastError();
-}
-
-template <int N>
-static cudaError_t go_r2c_loss(const float* map, const float* target, int ncols, const float2* stw, float2* out,
-                               int out_pitch, size_t out_img, float es, float ms, float scale, float gscale,
-                               float* partial, int batch, cudaStream_t st) {
-    constexpr int B = fs_Bcol(N);
-    const size_t sm = (size_t)FastFft<N, -1, B>::SLOTS * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(k_col_r2c_loss_fast<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    dim3 grid((ncols + 2 * B - 1) / (2 * B), batch);
-    k_col_r2c_loss_fast<N><<<grid, fs_T(N) * B, sm, st>>>(map, target, ncols, (size_t)N * ncols, stw, out, out_pitch,
-                                                          out_img, es, ms, scale, gscale, partial);
-    return cudaGetLastError();
-}
-
 // cuTensorMapEncodeTiled through the runtime's driver entry points (no link to
 // the driver library); null when unavailable
 typedef CUresult (*encode_tiled_fn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -244,6 +225,71 @@ static encode_tiled_fn encode_tiled() {
             fn = (encode_tiled_fn)f;
     }
     return fn;
+}
+
+// Tensor copies of step 1's image columns: the N expanded rows of 2B columns in
+// nb boxes of h <= 256 rows (each box 128-byte aligned in shared memory), within
+// the exchange buffer; false when that does not fit, B < 2 (a box row of 16
+// bytes at least), the images are not laid out in 16-byte multiples or the map
+// cannot be encoded (the first pass then reads global memory directly).
+template <int N>
+static bool r2c_tma_map(const float* in, int rows_in, int ncols, int in_pitch, size_t in_img, int batch,
+                        CUtensorMap* map, int* h, int* nb) {
+    constexpr int B = fs_Bcol(N);
+    const encode_tiled_fn enc = encode_tiled();
+    if (!enc || B < 2 || ((uintptr_t)in & 15) || (in_pitch & 3) || (in_img & 3) || ncols < 1 || rows_in < 1)
+        return false;
+    const int step = B >= 16 ? 1 : 16 / B;             // h 2B 4 bytes a multiple of 128
+    int n = (N + 255) / 256, hh = 0;
+    for (;; ++n) {
+        hh = (N + n - 1) / n;
+        hh = (hh + step - 1) / step * step;
+        if (hh <= 256) break;
+    }
+    if ((size_t)n * hh * 2 * B * sizeof(float) > (size_t)FastFft<N, -1, B>::SLOTS * sizeof(float2)) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)ncols, (cuuint64_t)rows_in, (cuuint64_t)batch};
+    const cuuint64_t strides[2] = {(cuuint64_t)in_pitch * sizeof(float), (cuuint64_t)in_img * sizeof(float)};
+    const cuuint32_t box[3] = {(cuuint32_t)(2 * B), (cuuint32_t)hh, 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    if (enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(in), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    *h = hh;
+    *nb = n;
+    return true;
+}
+
+template <int N>
+static cudaError_t go_r2c(const float* in, int rows_in, int ncols, int in_pitch, size_t in_img, int row0,
+                          const float2* stw, float2* out, int out_pitch, size_t out_img, float es, float ms,
+                          int batch, cudaStream_t st, unsigned* err, long long wait) {
+    constexpr int B = fs_Bcol(N);
+    const size_t sm = (size_t)FastFft<N, -1, B>::SLOTS * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_col_r2c_fast<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    CUtensorMap map;
+    memset(&map, 0, sizeof(map));
+    int h = 0, nb = 0;
+    if (!err || wait < 0 || !r2c_tma_map<N>(in, rows_in, ncols, in_pitch, in_img, batch, &map, &h, &nb)) nb = 0;
+    dim3 grid((ncols + 2 * B - 1) / (2 * B), batch);
+    k_col_r2c_fast<N><<<grid, fs_T(N) * B, sm, st>>>(in, rows_in, ncols, in_pitch, in_img, row0, stw, out,
+                                                     out_pitch, out_img, es, ms, map, h, nb, err, wait);
+    return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t go_r2c_loss(const float* map, const float* target, int ncols, const float2* stw, float2* out,
+                               int out_pitch, size_t out_img, float es, float ms, float scale, float gscale,
+                               float* partial, int batch, cudaStream_t st) {
+    constexpr int B = fs_Bcol(N);
+    const size_t sm = (size_t)FastFft<N, -1, B>::SLOTS * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_col_r2c_loss_fast<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid((ncols + 2 * B - 1) / (2 * B), batch);
+    k_col_r2c_loss_fast<N><<<grid, fs_T(N) * B, sm, st>>>(map, target, ncols, (size_t)N * ncols, stw, out, out_pitch,
+                                                          out_img, es, ms, scale, gscale, partial);
+    return cudaGetLastError();
 }
 
 // Tensor copies of step 4's staging: the N/2 + 1 Hermitian rows in nb boxes of
@@ -335,10 +381,11 @@ static cudaError_t go_rows_adj(float2* ws, int W, int Hp, int L, int interp, con
 
 cudaError_t launch_col_r2c_fast(const float* in, int rows_in, int ncols, int in_pitch, size_t in_img,
                                 int row0, const FftLen& f, float2* out, int out_pitch, size_t out_img,
-                                float end_scale, float mid_scale, int batch, cudaStream_t st) {
+                                float end_scale, float mid_scale, int batch, cudaStream_t st, unsigned* err,
+                                long long wait) {
     switch (f.N) {
 #define X(n) case n: return go_r2c<n>(in, rows_in, ncols, in_pitch, in_img, row0, f.stw, out, out_pitch, \
-                                      out_img, end_scale, mid_scale, batch, st);
+                                      out_img, end_scale, mid_scale, batch, st, err, wait);
         FT_FAST_LENGTHS(X)
 #undef X
     }

@@ -209,7 +209,7 @@ static cudaError_t col_r2c(ft_plan p, const float* in, int rows_in, int ncols, i
     const size_t out_img = (size_t)p->L * p->S;
     if (p->use_fast_y)
         return launch_col_r2c_fast(in, rows_in, ncols, in_pitch, in_img, row0, p->fy, out, p->S, out_img,
-                                   es, ms, batch, st);
+                                   es, ms, batch, st, p->d_tc_err, p->tc_wait);
     return launch_col_r2c(in, rows_in, ncols, in_pitch, in_img, row0, p->fy, p->col_logB_y, out, p->S,
                           out_img, es, ms, batch, st);
 }
@@ -511,6 +511,10 @@ ft_status ft_plan_tc_errors(ft_plan p, uint32_t* flags) {
     if (*flags & 4u)
         return ft_record_error(FT_ERR_TIMEOUT, "ft_plan_tc_errors: a wait for a tensor copy of step 4's columns "
                                                "timed out; the columns of the blocks that gave up were not written");
+    if (*flags & 8u)
+        return ft_record_error(FT_ERR_TIMEOUT, "ft_plan_tc_errors: a wait for a tensor copy of step 1's image "
+                                               "columns timed out; the columns of the blocks that gave up were not "
+                                               "written");
     return FT_OK;
 }
 

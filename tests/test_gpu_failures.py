@@ -88,11 +88,12 @@ def test_injected_allocation_failure_leaves_the_plan_usable(torch):
 
 @pytest.mark.parametrize("interp", ["linear", "cubic"])
 def test_bulk_copy_wait_timeout_fp32_rows(torch, interp):
-    """The FP32 row kernel stages its spectrum rows with bulk copies and step 4 its
-    Hermitian halves with tensor copies, both completing on an mbarrier; with the
-    plan's wait limit at 0 every such wait gives up: the block drains its copies,
-    writes nothing, and ft_plan_tc_errors returns FT_ERR_TIMEOUT with bits 1 and
-    2; with the default limit the next map is the oracle's."""
+    """Step 1 stages its image columns and step 4 its Hermitian halves with tensor
+    copies, the row kernel its spectrum rows with bulk copies, all completing on
+    an mbarrier; with the plan's wait limit at 0 every such wait gives up: the
+    block drains its copies, writes nothing, and ft_plan_tc_errors returns
+    FT_ERR_TIMEOUT with bits 1, 2 and 3; with the default limit the next map is
+    the oracle's."""
     from paper_1904_09409_gb300 import funnel as f
     H = W = 256
     imgs = _images(2, H, W, seed=3)
@@ -104,7 +105,7 @@ def test_bulk_copy_wait_timeout_fp32_rows(torch, interp):
             f.ft_plan_tc_errors(plan)
         assert e.value.status == f.FT_ERR_TIMEOUT
         assert "bulk copy" in f.ft_last_error()
-        assert "flags 0x6" in str(e.value)             # the rows' bulk copies and step 4's tensor copies
+        assert "flags 0xe" in str(e.value)             # steps 1 and 4's tensor copies, the rows' bulk copies
         f.ft_plan_set_wait_cycles(plan, f.FT_WAIT_CYCLES_DEFAULT)
         got = _gpu.forward(plan, imgs)
         assert f.ft_plan_tc_errors(plan) == 0
