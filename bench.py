@@ -3,10 +3,15 @@
 
 Workload: 64 synthetic 1024 x 1024 FP32 images per GPU (1-20 ridge/step lines,
 occluders, noise), map 1024 x 1024 (n_slope = W, n_intercept = H), top-32
-peaks per image.  One step = ft_detect over the resident batch: Sec. 3.1
+peaks per image.  One step = detection over the resident batch: Sec. 3.1
 steps 1-4 (step 4 also writes the maximum of |P| per tile) and the peak
-detection of Sec. 4.4, which reads only the tiles that can hold a top-32 peak.  Metric: megapixels (input pixels) per
-second, whole job.  Inputs (268 MB) and maps (268 MB) exceed the 129 MB L2.
+detection of Sec. 4.4, which reads only the tiles that can hold a top-32 peak.
+The timed steps go through ft_detect_batches, PIPE_RUN steps per run (step 1
+of one step runs beside the peak pass of the step before); the first step of
+every run is a separate one-batch call whose launches are bracketed by CUDA
+events (per-kernel durations).  The same step through one ft_detect call each
+is timed too ("per_call").  Metric: megapixels (input pixels) per second, whole
+job.  Inputs (268 MB) and maps (268 MB) exceed the 129 MB L2.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun (N > 1) every rank runs its own 64 images (weak scaling, no
@@ -34,7 +39,8 @@ sys.path.insert(0, ROOT)
 BATCH = 64
 SIDE = 1024
 TOP_K = 32
-PROF_EVERY = 10     # per-launch CUDA events on every 10th step of a timed region
+PROF_EVERY = 10     # per-launch CUDA events on every 10th step of a timed region (extra legs)
+PIPE_RUN = 50       # main step: steps per ft_detect_batches run; the first of each run is instrumented
 METRIC = "megapixels/s funnel fwd(+bwd) at 1024² FP32 vs plain form; % of HBM roofline"
 UNIT = "Mpx/s"
 WORKLOAD = "64 x 1024x1024 FP32 synthetic line images, map 1024x1024, top-32 peaks per image"
@@ -554,9 +560,27 @@ def run_ours(args):
     def step():
         f.ft_detect(plan, x, m, TOP_K, out=pk, count=cnt, stream=stream)
 
+    # PIPE_RUN pipelined steps per ft_detect_batches call, over the same resident images
+    xs = [x] * PIPE_RUN
+    pk_n = torch.empty(PIPE_RUN * BATCH * TOP_K * f.PEAK_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    cnt_n = torch.empty(PIPE_RUN * BATCH, dtype=torch.int32, device=dev)
+
+    def steps(n):
+        f.ft_detect_batches(plan, xs[:n], m, TOP_K, out=pk_n, count=cnt_n, stream=stream)
+
     for _ in range(max(args.warmup, 3)):
         step()
+    steps(PIPE_RUN)
     torch.cuda.synchronize(dev)
+    # the same step, one ft_detect call each (uninstrumented)
+    n_pc = min(args.steps, 300)
+    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pe0.record(stream)
+    for _ in range(n_pc):
+        step()
+    pe1.record(stream)
+    torch.cuda.synchronize(dev)
+    per_call_ms = pe0.elapsed_time(pe1) / n_pc
 
     uuid = str(getattr(torch.cuda.get_device_properties(dev), "uuid", "") or "")
     sampler = ClockSampler(uuid)
@@ -568,11 +592,15 @@ def run_ours(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    # every PROF_EVERY-th step's launches are bracketed by CUDA events (per-kernel
-    # durations inside the timed region); the others run uninstrumented
-    for i in range(args.steps):
-        f.ft_profile_enable(plan, i % PROF_EVERY == 0)
-        step()
+    # every PIPE_RUN-th step's launches are bracketed by CUDA events (per-kernel
+    # durations inside the timed region); the others run uninstrumented and pipelined
+    for c0 in range(0, args.steps, PIPE_RUN):
+        n = min(PIPE_RUN, args.steps - c0)
+        f.ft_profile_enable(plan, True)
+        steps(1)
+        f.ft_profile_enable(plan, False)
+        if n > 1:
+            steps(n - 1)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     replicas.barrier()
@@ -592,7 +620,7 @@ def run_ours(args):
     # roofline of the dominant kernel
     kernels = {}
     total_kernel_ms = sum(v[0] for v in prof.values()) or 1.0
-    prof_steps = (args.steps + PROF_EVERY - 1) // PROF_EVERY
+    prof_steps = (args.steps + PIPE_RUN - 1) // PIPE_RUN
     for name, (kms, n) in prof.items():
         per = kms / n
         imgs_per_launch = BATCH * prof_steps / n          # the plan may split a batch over streams
@@ -633,7 +661,11 @@ def run_ours(args):
                        "top_k": TOP_K, "l2": "inputs larger than L2 (268 MB images + 268 MB maps per GPU)",
                        "parallelism": f"replicas x{ws}, no collective on the data path"},
             "roofline": roof,
-            "kernel_timing": f"CUDA events around every launch of every {PROF_EVERY}th timed step",
+            "kernel_timing": f"CUDA events around every launch of every {PIPE_RUN}th timed step",
+            "pipelining": f"ft_detect_batches, {PIPE_RUN - 1} pipelined steps per call after one instrumented "
+                          "step (step 1 of a step beside the peak pass of the one before)",
+            "per_call": {"call": "ft_detect", "steps": n_pc, "ms_per_step": per_call_ms,
+                         "value": px_step / (per_call_ms / 1e3) / 1e6, "unit": UNIT},
             "step_roofline": step_roof,
             "kernels": kernels,
             "cpu_baseline": cpu,

@@ -156,6 +156,27 @@ ft_status ft_peaks(ft_plan plan, const float* d_map, int batch, int top_k, float
 ft_status ft_detect(ft_plan plan, const float* d_img, float* d_map, int batch, int top_k, float threshold,
                     ft_peak* d_out, int32_t* d_count, void* stream);
 
+/* ft_detect over nb consecutive batches of `batch` images each, enqueued on
+ * `stream` as one pipeline: batch j reads its images from d_imgs[j] (a HOST
+ * array of nb device pointers, each to [batch][H][W] FP32, 8-byte aligned) and
+ * writes its top_k records per image to d_out + j * batch * top_k and its counts
+ * to d_count + j * batch (device, caller-owned, nb * batch * top_k records and
+ * nb * batch counts).  d_map ([batch][H'][S]) is scratch shared by the batches
+ * and holds the last batch's maps afterwards.  The records and counts equal
+ * those of nb ft_detect calls (Sec. 3.1 steps 1-4 and the peak detection of
+ * Sec. 4.4 per batch).  Where ft_detect takes the peak pass from tile maxima
+ * and the plan launches its fixed-length kernels with programmatic dependent
+ * launch (the default; FT_PDL=0 at plan creation turns it off), step 1 of
+ * batch j + 1 runs beside the peak pass of batch j: it reads only its images
+ * and writes only the plan's workspace, and it completes only after that pass
+ * has, so the rest of batch j + 1 is ordered after batch j.  The images must not
+ * overlap d_out, d_count or d_map.  Otherwise the batches run as nb ft_detect
+ * calls.  Errors as for ft_detect (FT_ERR_INVALID_ARG for a NULL or misaligned
+ * pointer in d_imgs or nb < 0); nb or batch 0 is a no-op.  4 launches per batch
+ * on the pipelined path. */
+ft_status ft_detect_batches(ft_plan plan, const float* const* d_imgs, int nb, int batch, float* d_map, int top_k,
+                            float threshold, ft_peak* d_out, int32_t* d_count, void* stream);
+
 /* Loss for fitting by gradient through ft_backward (the paper fits nothing by
  * gradient; this is the loss of the differentiable workload): with
  * r = |d_map| * scale - d_target elementwise,
@@ -345,15 +366,19 @@ int ft_plan_get_precision(ft_plan plan);
  * its block and stops, so the rows it had not finished are left incomplete.
  * Bit 1: a wait of the FP32 row kernel (steps 2-3) for the bulk copies that
  * stage its spectrum rows timed out; the block waits for its copies in flight
- * with the default bound and returns without writing its rows.  The CUDA
- * context stays usable either way.  Waits for all work on the plan's device,
+ * with the default bound and returns without writing its rows.  Bit 2: a wait
+ * of the inverse column kernel (step 4) for the tensor copies that stage its
+ * Hermitian half columns timed out; bit 3: the same for the forward column
+ * kernel (step 1) and its image columns.  Those blocks likewise drain their
+ * copies in flight and return without writing.  The CUDA context stays usable
+ * in every case.  Waits for all work on the plan's device,
  * copies the flags to *flags (host) and clears them; returns FT_ERR_TIMEOUT
  * when a bit was set (ft_last_error() says which), FT_OK otherwise. */
 ft_status ft_plan_tc_errors(ft_plan plan, uint32_t* flags);
 
 /* Bound, in SM cycles, of every device-side wait of the plan's kernels (the
- * tensor-core kernels for their GEMMs, the FP32 row kernel for its bulk
- * copies; FT_WAIT_CYCLES_DEFAULT, about 2 s at 2 GHz, after creation).
+ * tensor-core kernels for their GEMMs, the FP32 row and column kernels for
+ * their bulk and tensor copies; FT_WAIT_CYCLES_DEFAULT, about 2 s at 2 GHz, after creation).
  * The limit is checked before each try, so 0 makes every such wait give up at
  * once: a test setting that runs the timeout path (flag, drain, free, stop)
  * without any GPU fault.  cycles < 0 is FT_ERR_INVALID_ARG.  Changes later

@@ -217,12 +217,17 @@ struct FastFft {
 // launchers of the fixed-length kernels (k_fast.cu); they return
 // cudaErrorNotSupported when N has no schedule
 
-// (err, wait: with err given, the image columns are staged through tensor
-// copies whose bounded waits set bit 3 of *err when they run out)
+// (pdl: launched with programmatic stream serialisation, the blocks waiting for
+// the predecessor before they read or write; follows_peak (with pdl): the
+// predecessor is the peak pass of the previous batch of ft_detect_batches, not
+// waited for (see k_col_r2c_fast); err, wait: with err given, the image columns
+// are staged through tensor copies whose bounded waits set bit 3 of *err when
+// they run out)
 cudaError_t launch_col_r2c_fast(const float* in, int rows_in, int ncols, int in_pitch, size_t in_img,
                                 int row0, const FftLen& f, float2* out, int out_pitch, size_t out_img,
-                                float end_scale, float mid_scale, int batch, cudaStream_t st,
-                                unsigned* err = nullptr, long long wait = FT_WAIT_CYCLES);
+                                float end_scale, float mid_scale, int batch, cudaStream_t st, bool pdl = false,
+                                bool follows_peak = false, unsigned* err = nullptr,
+                                long long wait = FT_WAIT_CYCLES);
 // the adjoint of step 4 with the input gradient computed from the map and the
 // target of the gradient workload (k_col_r2c_loss_fast); partial gets
 // col_r2c_loss_blocks() floats per image

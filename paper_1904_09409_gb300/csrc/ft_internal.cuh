@@ -87,12 +87,14 @@ __device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int t) 
 }
 
 // ------------------------------------------- programmatic dependent launch
-// A kernel of the forward chain (steps 2-3, step 4, the peak pass) may be
+// A kernel of the forward chain (steps 1, 2-3 and 4, the peak pass) may be
 // launched while its predecessor on the stream is still running (its blocks are
 // placed as the predecessor's last blocks retire); pdl_wait() blocks until the
 // predecessor has completed and its writes are visible, and is a no-op for a
-// kernel launched without the attribute.  pdl_trigger() lets the successor be
-// launched early (the predecessor's blocks call it when they start).
+// kernel launched without the attribute.  Every such kernel calls it before its
+// first read or write of device memory.  pdl_trigger() lets the successor be
+// launched early (steps 1-4 call it when their blocks start, the peak pass
+// after its wait).
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 

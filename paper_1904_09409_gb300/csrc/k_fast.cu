@@ -6,15 +6,22 @@
 #include "fast_blocks.cuh"
 
 // tma_nb > 0: the image columns are staged by tma_nb tensor copies of tma_h
-// rows (tmap describes the launch's images), else read from global memory
+// rows (tmap describes the launch's images), else read from global memory.
+// follows_peak: the predecessor on the stream is the peak pass of the previous
+// batch of ft_detect_batches, which has waited for its own step 4 and touches
+// only the maps, the tile maxima and the peak records: this kernel reads its
+// images and writes the spectrum workspace without waiting for it, and only its
+// last block waits for that pass before exiting, so that the completion of this
+// grid (which the next kernels wait for) implies the completion of the pass.
 template <int N>
 __global__ void __launch_bounds__(fs_T(N) * fs_Bcol(N), 1024 / (fs_T(N) * fs_Bcol(N)))
 k_col_r2c_fast(const float* __restrict__ in, int rows_in, int ncols, int in_pitch, size_t in_img,
                int row0, const float2* __restrict__ stw, float2* __restrict__ out, int out_pitch,
                size_t out_img, float end_scale, float mid_scale, const __grid_constant__ CUtensorMap tmap,
-               int tma_h, int tma_nb, unsigned* __restrict__ err, long long wait) {
+               int tma_h, int tma_nb, unsigned* __restrict__ err, long long wait, int follows_peak) {
     extern __shared__ __align__(128) float2 sm[];
     pdl_trigger();
+    if (!follows_peak) pdl_wait();
     const float* src = in + (size_t)blockIdx.y * in_img;
     float2* dst = out + (size_t)blockIdx.y * out_img;
     if (tma_nb > 0)
@@ -23,6 +30,7 @@ k_col_r2c_fast(const float* __restrict__ in, int rows_in, int ncols, int in_pitc
     else
         r2c_block<N, fs_Bcol(N)>(src, rows_in, ncols, in_pitch, row0, stw, dst, out_pitch, end_scale, mid_scale,
                                  blockIdx.x, sm);
+    if (follows_peak && blockIdx.x == gridDim.x - 1 && blockIdx.y == gridDim.y - 1) pdl_wait();
 }
 
 // tma_nb > 0: the Hermitian half is staged by tma_nb tensor copies of tma_h rows
@@ -263,7 +271,7 @@ static bool r2c_tma_map(const float* in, int rows_in, int ncols, int in_pitch, s
 template <int N>
 static cudaError_t go_r2c(const float* in, int rows_in, int ncols, int in_pitch, size_t in_img, int row0,
                           const float2* stw, float2* out, int out_pitch, size_t out_img, float es, float ms,
-                          int batch, cudaStream_t st, unsigned* err, long long wait) {
+                          int batch, cudaStream_t st, bool pdl, bool follows_peak, unsigned* err, long long wait) {
     constexpr int B = fs_Bcol(N);
     const size_t sm = (size_t)FastFft<N, -1, B>::SLOTS * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_col_r2c_fast<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -273,9 +281,9 @@ static cudaError_t go_r2c(const float* in, int rows_in, int ncols, int in_pitch,
     int h = 0, nb = 0;
     if (!err || wait < 0 || !r2c_tma_map<N>(in, rows_in, ncols, in_pitch, in_img, batch, &map, &h, &nb)) nb = 0;
     dim3 grid((ncols + 2 * B - 1) / (2 * B), batch);
-    k_col_r2c_fast<N><<<grid, fs_T(N) * B, sm, st>>>(in, rows_in, ncols, in_pitch, in_img, row0, stw, out,
-                                                     out_pitch, out_img, es, ms, map, h, nb, err, wait);
-    return cudaGetLastError();
+    return launch_maybe_pdl(k_col_r2c_fast<N>, grid, dim3(fs_T(N) * B), sm, st, pdl, in, rows_in, ncols, in_pitch,
+                            in_img, row0, stw, out, out_pitch, out_img, es, ms, map, h, nb, err, wait,
+                            (pdl && follows_peak) ? 1 : 0);
 }
 
 template <int N>
@@ -381,11 +389,11 @@ static cudaError_t go_rows_adj(float2* ws, int W, int Hp, int L, int interp, con
 
 cudaError_t launch_col_r2c_fast(const float* in, int rows_in, int ncols, int in_pitch, size_t in_img,
                                 int row0, const FftLen& f, float2* out, int out_pitch, size_t out_img,
-                                float end_scale, float mid_scale, int batch, cudaStream_t st, unsigned* err,
-                                long long wait) {
+                                float end_scale, float mid_scale, int batch, cudaStream_t st, bool pdl,
+                                bool follows_peak, unsigned* err, long long wait) {
     switch (f.N) {
 #define X(n) case n: return go_r2c<n>(in, rows_in, ncols, in_pitch, in_img, row0, f.stw, out, out_pitch, \
-                                      out_img, end_scale, mid_scale, batch, st, err, wait);
+                                      out_img, end_scale, mid_scale, batch, st, pdl, follows_peak, err, wait);
         FT_FAST_LENGTHS(X)
 #undef X
     }

@@ -10,19 +10,25 @@
 // k_peaks.cu).  A peak inside tile j has |P| <= M[j], the tile's maximum.  So
 // once K = top_k peaks with keys >= kth are known, a tile with M[j] < value(kth)
 // cannot contribute and is never read.  One block per image:
-//   round 1  the tiles with the largest maxima, one per warp of the block
-//            (radix selection over the tile keys (M[j], j)), among the tiles
-//            with M[j] >= threshold;
-//   round 2  every other tile with M[j] >= max(threshold, value(kth)), where kth
-//            is the top_k-th key found so far (all tiles with M[j] >= threshold
-//            while fewer than top_k peaks are known);
-// then the top_k keys sorted descending become the ft_peak records.  Warps take
-// one tile each per batch, staged in shared memory with its one-cell halo;
-// after a batch the candidates are cut back to the best top_k, which raises
-// value(kth) for the next batch.  Every cell of a processed tile gets the exact
-// test of k_peak_tiles (neighbours across tile borders and around the wrap),
-// so the list equals the dense one: keys are distinct, and every key of the
-// dense list lies in a tile that is processed.
+//   round 1  the brightest tiles, about one per warp of the block: every valid
+//            tile (M[j] >= threshold) with M[j] >= T, where each thread takes
+//            the largest valid maximum among the tiles it copies and T is the
+//            nw-th largest of those (one shuffle sort per warp, then a merge
+//            tree over the warps).  At least nw tiles reach T, and so does
+//            every tile among the nw brightest;
+//   round 2  every other valid tile with M[j] >= the bound.
+// Warps take one tile each per batch, staged in shared memory with its one-cell
+// halo (interior tiles as aligned float4 rows, all loads of a lane in flight at
+// once; edge tiles cell by cell with the wrap).  After each batch the
+// candidates are cut to the best K, and the bound becomes value(kth): for
+// top_k <= 32 every warp sorts chunks of 32 keys with shuffles and keeps the
+// best 32, and a merge tree over the warps leaves the best K sorted (so the
+// final list needs no further sort); for larger top_k, radix selection once
+// there are K candidates.  Every cell of a processed tile gets the exact test
+// of k_peak_tiles (neighbours across tile borders and around the wrap), so the
+// list equals the dense one: keys are distinct, and every key of the dense list
+// lies in a tile that is processed and is at or above the bound when it is
+// tested.
 //
 // Capacity: two cells of one 2 x 2 block are neighbours, so a tile of r x c cells
 // holds at most r c / 4 strict local maxima; a batch (one tile per warp) adds at
@@ -35,6 +41,7 @@ k_peak_sparse(const float* __restrict__ map, const unsigned* __restrict__ tmax, 
     extern __shared__ __align__(16) unsigned char spsm[];
     __shared__ SparseShared sh;
     pdl_wait();
+    pdl_trigger();                                     // step 4 is complete: the next launch may be placed
     const int img = blockIdx.x;
     peak_sparse_block(map + (size_t)img * Hp * S, tmax + (size_t)img * nty * ntx, Hp, S, TH, logTW, nty, ntx, K, thr,
                       out + (size_t)img * K, count + img, spsm, sh);
@@ -89,7 +96,7 @@ static int sparse_warps(int rows, int cols, int top_k) {
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
     if ((rows * cols) % 32 != 0 || (cols & (cols - 1)) != 0) return 0;
-    if (rows * (cols < 32 ? cols : 32) > 64 * 32) return 0;      // a lane's rows fit one 64-bit mask
+    if (rows * cols > 64 * 32) return 0;                          // a lane's cells fit one 64-bit mask
     for (int nw = 32; nw >= 8; nw /= 2)
         if (sparse_smem(rows, cols, top_k, nw, 0) + sizeof(SparseShared) + SP_TM_SMEM * sizeof(unsigned) <=
             (size_t)optin)

@@ -205,11 +205,11 @@ static size_t aux_off(ft_plan p, int batch) { return tposed_off(p, batch) + tpos
 // Fixed-length kernels where the length has a schedule, generic ones otherwise.
 static cudaError_t col_r2c(ft_plan p, const float* in, int rows_in, int ncols, int in_pitch,
                            size_t in_img, int row0, float2* out, float es, float ms, int batch,
-                           cudaStream_t st) {
+                           cudaStream_t st, bool follows_peak = false) {
     const size_t out_img = (size_t)p->L * p->S;
     if (p->use_fast_y)
         return launch_col_r2c_fast(in, rows_in, ncols, in_pitch, in_img, row0, p->fy, out, p->S, out_img,
-                                   es, ms, batch, st, p->d_tc_err, p->tc_wait);
+                                   es, ms, batch, st, p->pdl, follows_peak, p->d_tc_err, p->tc_wait);
     return launch_col_r2c(in, rows_in, ncols, in_pitch, in_img, row0, p->fy, p->col_logB_y, out, p->S,
                           out_img, es, ms, batch, st);
 }
@@ -669,13 +669,15 @@ static cudaError_t tc_c2r(ft_plan p, const float2* ws, float* d_map, float* cm, 
 }
 
 // Steps 1-4 of nb images; tmax (fixed-length FP32 step 4 only, else NULL) gets
-// the tile maxima of |map| for the peak pass of ft_detect.
+// the tile maxima of |map| for the peak pass of ft_detect; follows_peak: step 1
+// comes right after the peak pass of the previous batch of ft_detect_batches.
 static ft_status forward_part(ft_plan p, const float* src, float* d_map, float2* ws, float* cm, int nb,
-                              cudaStream_t st, unsigned* tmax = nullptr) {
+                              cudaStream_t st, unsigned* tmax = nullptr, bool follows_peak = false) {
     const bool tc_cols = tc_columns(p);
     FT_LAUNCH(p, FT_KERNEL_COL_R2C, st,
               tc_cols ? tc_r2c(p, src, ws, cm, nb, st)
-                      : col_r2c(p, src, p->H, p->W, p->W, (size_t)p->H * p->W, p->top, ws, 1.f, 1.f, nb, st),
+                      : col_r2c(p, src, p->H, p->W, p->W, (size_t)p->H * p->W, p->top, ws, 1.f, 1.f, nb, st,
+                                follows_peak),
               "step 1 (column R2C)");
     FT_LAUNCH(p, FT_KERNEL_NVMT_ROWS, st, nvmt_rows(p, ws, nb, st), "steps 2-3 (NVMT + row FFT)");
     FT_LAUNCH(p, FT_KERNEL_COL_C2R, st,
@@ -861,6 +863,44 @@ ft_status ft_detect(ft_plan p, const float* d_img, float* d_map, int batch, int 
               launch_peak_sparse(d_map, tmax, p->Hp, p->S, rows, cols, batch, top_k, threshold, d_out, d_count, st,
                                  p->pdl),
               "peak detection (tile maxima)");
+    return FT_OK;
+}
+
+ft_status ft_detect_batches(ft_plan p, const float* const* d_imgs, int nb, int batch, float* d_map, int top_k,
+                            float threshold, ft_peak* d_out, int32_t* d_count, void* stream) {
+    if (!p || nb < 0 || batch < 0 || batch > 65535) return FT_ERR_INVALID_ARG;
+    if (top_k < 1 || top_k > FT_MAX_TOPK || threshold != threshold) return FT_ERR_INVALID_ARG;
+    if (nb == 0 || batch == 0) return FT_OK;
+    if (!d_imgs || !d_map || !d_out || !d_count || ((uintptr_t)d_map & 7)) return FT_ERR_INVALID_ARG;
+    for (int j = 0; j < nb; ++j)
+        if (!d_imgs[j] || ((uintptr_t)d_imgs[j] & 7)) return FT_ERR_INVALID_ARG;
+    const size_t recs = (size_t)batch * top_k;
+    int rows, cols, bands;
+    // the pipeline needs step 1 on the fixed-length kernel right after the peak
+    // pass from tile maxima; otherwise one ft_detect per batch
+    const bool pipe = p->pdl && p->use_fast_y && !tc_columns(p) && p->space != FT_SPACE_INVERSE &&
+                      sparse_peaks(p, batch, top_k, &rows, &cols, &bands);
+    if (!pipe) {
+        for (int j = 0; j < nb; ++j) {
+            const ft_status s = ft_detect(p, d_imgs[j], d_map, batch, top_k, threshold, d_out + j * recs,
+                                          d_count + (size_t)j * batch, stream);
+            if (s != FT_OK) return s;
+        }
+        return FT_OK;
+    }
+    const size_t off = aux_off(p, batch);
+    ft_status s = ensure(p, &p->d_ws, &p->ws_bytes, off + tmax_bytes(p, batch, top_k), "cudaMalloc(workspace)");
+    if (s != FT_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    float2* ws = (float2*)p->d_ws;
+    unsigned* tmax = (unsigned*)((char*)p->d_ws + off);
+    for (int j = 0; j < nb; ++j) {
+        if ((s = forward_part(p, d_imgs[j], d_map, ws, nullptr, batch, st, tmax, j > 0)) != FT_OK) return s;
+        FT_LAUNCH(p, FT_KERNEL_PEAK_SPARSE, st,
+                  launch_peak_sparse(d_map, tmax, p->Hp, p->S, rows, cols, batch, top_k, threshold, d_out + j * recs,
+                                     d_count + (size_t)j * batch, st, p->pdl),
+                  "peak detection (tile maxima)");
+    }
     return FT_OK;
 }
 

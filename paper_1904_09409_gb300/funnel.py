@@ -39,7 +39,7 @@ EXPORTED = (
     "ft_batch_create", "ft_batch_destroy", "ft_batch_layout", "ft_batch_group_count",
     "ft_batch_group_info", "ft_batch_group_tuned_ms", "ft_batch_run", "ft_tc_dft64",
     "ft_plan_set_precision", "ft_plan_get_precision", "ft_plan_tc_errors", "ft_verify",
-    "ft_abs_mse_backward", "ft_detect", "ft_detect_launches",
+    "ft_abs_mse_backward", "ft_detect", "ft_detect_launches", "ft_detect_batches",
     "ft_plan_set_wait_cycles", "ft_plan_get_wait_cycles", "ft_plan_inject_alloc_failures",
     "ft_batch_config", "ft_batch_set_config", "ft_batch_tune_ms", "ft_batch_launches", "ft_fma_probe",
     "ft_debug_flags", "ft_debug_build",
@@ -136,6 +136,8 @@ def lib() -> ctypes.CDLL:
     L.ft_abs_mse_backward.restype = ci
     L.ft_detect.argtypes = [vp, vp, vp, ci, ci, cf, vp, vp, vp]
     L.ft_detect.restype = ci
+    L.ft_detect_batches.argtypes = [vp, ctypes.POINTER(vp), ci, ci, vp, ci, cf, vp, vp, vp]
+    L.ft_detect_batches.restype = ci
     L.ft_plan_set_wait_cycles.argtypes = [vp, ctypes.c_int64]
     L.ft_plan_set_wait_cycles.restype = ci
     L.ft_plan_get_wait_cycles.argtypes = [vp]
@@ -302,6 +304,34 @@ def ft_detect(plan: Plan, img, out_map, top_k: int, threshold: float = float("-i
     cp = _dev_ptr(count, "int32", b, "count")
     _check(lib().ft_detect(plan.handle, ip, mp, b, int(top_k), float(threshold), op, cp, _stream_ptr(stream)),
            "ft_detect")
+    return out, count
+
+
+def ft_detect_batches(plan: Plan, imgs, out_map, top_k: int, threshold: float = float("-inf"), out=None,
+                      count=None, stream=None):
+    """ft_detect over the batches imgs[j] (CUDA float32 tensors of one shape
+    (batch, H, W)) as one pipeline on the stream; out_map (batch maps) is shared
+    scratch.  Returns (peaks, count): len(imgs) * batch * top_k records and
+    len(imgs) * batch counts, batch j's first, equal to len(imgs) ft_detect
+    calls."""
+    import torch
+    nb = len(imgs)
+    b = imgs[0].shape[0] if nb else 0
+    ptrs = (ctypes.c_void_p * max(nb, 1))()
+    for j, t in enumerate(imgs):
+        if t.shape[0] != b:
+            raise ValueError("all batches must hold the same number of images")
+        ptrs[j] = _dev_ptr(t, "float32", b * plan.H * plan.W, f"imgs[{j}]")
+    mp = _dev_ptr(out_map, "float32", b * plan.Hp * plan.S, "map")
+    dev = out_map.device
+    if out is None:
+        out = torch.empty(nb * b * top_k * PEAK_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    if count is None:
+        count = torch.empty(nb * b, dtype=torch.int32, device=dev)
+    op = _dev_ptr(out, "uint8", nb * b * top_k * PEAK_DTYPE.itemsize, "out")
+    cp = _dev_ptr(count, "int32", nb * b, "count")
+    _check(lib().ft_detect_batches(plan.handle, ptrs, nb, b, mp, int(top_k), float(threshold), op, cp,
+                                   _stream_ptr(stream)), "ft_detect_batches")
     return out, count
 
 

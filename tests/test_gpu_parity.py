@@ -307,6 +307,40 @@ def test_peaks_tile_bound_edge_cases(torch, peak_mode, kind, K):
                 assert got[i] == oracle.peaks_ref(np.abs(maps[i]).astype(np.float64), K, thr), (i, thr)
 
 
+def _value_spread_map(kind, rng, Hp, S):
+    """Maps that drive the value histograms of the peak pass from tile maxima to
+    each of their branches: one spike 2^20 above noise (fewer tiles than warps
+    within 8 octaves of the brightest: exact selection of the first tiles, and
+    the K-th candidate in the open last bin), a nearly flat map (every tile
+    maximum and candidate in one 1/32-octave bin: all tiles in the first round,
+    more than SP_LIST of them, and more than 64 candidates at the final bound),
+    log-uniform values over 60 octaves, and bands of bright and dim rows."""
+    if kind == "spike":
+        m = rng.uniform(0.0, 1e-3, size=(Hp, S)).astype(np.float32)
+        m[Hp // 3, S // 5] = 1.0e3
+        return m
+    if kind == "flat":
+        return (1.0 + 1e-4 * rng.uniform(size=(Hp, S))).astype(np.float32)
+    if kind == "octaves":
+        return np.exp2(rng.uniform(-30.0, 30.0, size=(Hp, S))).astype(np.float32)
+    m = rng.uniform(0.0, 1.0, size=(Hp, S)).astype(np.float32)
+    m[(np.arange(Hp) // 40) % 2 == 1] *= 1e-3
+    return m
+
+
+@pytest.mark.parametrize("kind", ["spike", "flat", "octaves", "bands"])
+@pytest.mark.parametrize("K", [1, 32, 33, 200])
+def test_peaks_value_histogram_branches(torch, peak_mode, kind, K):
+    rng = np.random.default_rng(K + len(kind))
+    Hp, S = 768, 512                                   # 48 x 32 = 1536 tiles of 16 x 16 cells
+    maps = np.stack([_value_spread_map(kind, rng, Hp, S), -_value_spread_map(kind, rng, Hp, S)])
+    with make_plan(Hp, S, S, Hp) as plan:
+        for thr in (float("-inf"), 0.5):
+            got, _ = _gpu.peaks(plan, maps, K, thr)
+            for i in range(2):
+                assert got[i] == oracle.peaks_ref(np.abs(maps[i]).astype(np.float64), K, thr), (i, thr)
+
+
 def test_lane_split_gives_identical_results(torch, monkeypatch):
     """FT_LANES=2 splits a batch over two plan-owned streams: maps and peaks are
     bit-identical to the single-stream run."""
