@@ -145,26 +145,14 @@ __device__ __forceinline__ bool r2c_block(const float* __restrict__ in, int rows
     return true;
 }
 
-// Step 4 (and the transpose of step 1) for column block bx of one image: the
-// Hermitian halves in[l][c] (pitch in_pitch complex, l = 0 .. N/2) of columns
-// bx 2B + 2f, + 1 -> rows row0 .. row0 + rows_out - 1 of the length-N real
-// results, times out_scale, at out[t - row0][c] (pitch out_pitch floats).
-// tmax (may be NULL; only with row0 = 0 and rows_out = N): the maximum of |out|
-// of every tile of 128 / B rows x 2B columns, at tmax[tile row * nbx + bx]
-// (nbx = column blocks of the image) as float bits.
-// TMA: the Hermitian half arrives by nb tensor copies of h rows x 2B complex
-// (tmap: the launch's half spectra as [images][rows][in_pitch] 8-byte elements,
-// image `img`; rows past N/2 and columns past the tensor read zeros), waited for
-// on an mbarrier with the bound `wait` in SM cycles; when a wait runs out, bit 2
-// of *err is set, the block waits (default bound) for its copies in flight and
-// returns false without writing.  Otherwise every thread copies 16-byte pieces.
-template <int N, int B, bool TMA = false>
-__device__ __forceinline__ bool c2r_block(const float2* __restrict__ in, int ncols, int in_pitch,
-                                          const float2* __restrict__ stw, float mid_scale, float* __restrict__ out,
-                                          int row0, int rows_out, int out_pitch, float out_scale,
-                                          unsigned* __restrict__ tmax, int nbx, int bx, float2* sm,
-                                          const CUtensorMap* tmap = nullptr, int tma_h = 0, int tma_nb = 0,
-                                          int img = 0, unsigned* err = nullptr, long long wait = FT_WAIT_CYCLES) {
+// The part of step 4 after staging, for column block bx of one image: sm holds
+// the Hermitian half [N/2 + 1][2B] complex (and serves as the FFT's exchange
+// buffer afterwards); arguments as for c2r_block.
+template <int N, int B>
+__device__ __forceinline__ void c2r_from_stage(float2* sm, int ncols, const float2* __restrict__ stw,
+                                               float mid_scale, float* __restrict__ out, int row0, int rows_out,
+                                               int out_pitch, float out_scale, unsigned* __restrict__ tmax, int nbx,
+                                               int bx) {
     constexpr int E = fs_E(N);
     constexpr int R0 = fs_radix(N, 0), G0 = E / R0;
     constexpr int RL = fs_radix(N, fs_nst(N) - 1), GL = E / RL;
@@ -173,38 +161,7 @@ __device__ __forceinline__ bool c2r_block(const float2* __restrict__ in, int nco
     const int t = threadIdx.x / B;
     const int c = bx * 2 * B + 2 * f;
     const bool colok = c < ncols;
-
-    // stage the Hermitian half (rows 0 .. N/2, 2B complex each) with 16-byte async
-    // copies; every row is read once and serves both n and N - n.  Thread (t, f)
-    // copies the column pair f of rows t, t + T, ...
-    float2* stg = sm;                                  // [N/2 + 1][2B]
-    if constexpr (TMA) {
-        __shared__ uint64_t mbar;
-        const uint32_t mb = smem_u32(&mbar);
-        if (threadIdx.x == 0) {
-            mbar_init(mb, 1);
-            mbar_arrive_expect_tx(mb, (uint32_t)(tma_nb * tma_h * 2 * B * sizeof(float2)));
-            for (int k = 0; k < tma_nb; ++k) tma_load_3d(stg + k * tma_h * 2 * B, tmap, bx * 2 * B, k * tma_h, img, mb);
-        }
-        __syncthreads();                               // the mbarrier is initialised
-        const bool ok = mbar_wait(mb, 0, wait);
-        if (__syncthreads_or(!ok)) {
-            if (threadIdx.x == 0 && err) atomicOr(err, 4u);
-            mbar_wait(mb, 0);                          // the copies in flight land first
-            return false;
-        }
-    } else {
-        const float2* src = in + c + (size_t)t * in_pitch;
-        float2* dst = stg + t * 2 * B + 2 * f;
-        for (int r = t; r <= N / 2; r += fs_T(N), src += (size_t)fs_T(N) * in_pitch, dst += fs_T(N) * 2 * B) {
-            if (colok)
-                cp_async16(dst, src);
-            else
-                *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        cp_async_wait_all();
-        __syncthreads();
-    }
+    const float2* stg = sm;
     // sample n = t + T (m + G0 q) comes from row n when m + G0 q < E/2 and from
     // row N - n otherwise (the two agree at n = N/2); the end bins 0 and N/2,
     // which only thread t = 0 holds, enter through their real parts
@@ -265,7 +222,7 @@ __device__ __forceinline__ bool c2r_block(const float2* __restrict__ in, int nco
             if (FT_IN(bx, nbx, FT_DBG_C2R_STORE)) tmax[(size_t)w * nbx + bx] = x;
         }
     }
-    if (!colok) return true;
+    if (!colok) return;
     // row n of the result goes to output row n - row0 when that is in range
     float* dst = out + c;
 #pragma unroll
@@ -277,6 +234,65 @@ __device__ __forceinline__ bool c2r_block(const float2* __restrict__ in, int nco
                 *reinterpret_cast<float2*>(dst + (size_t)rr * out_pitch) =
                     make_float2(v[m * RL + q].x * out_scale, v[m * RL + q].y * out_scale);
         }
+}
+
+// Step 4 (and the transpose of step 1) for column block bx of one image: the
+// Hermitian halves in[l][c] (pitch in_pitch complex, l = 0 .. N/2) of columns
+// bx 2B + 2f, + 1 -> rows row0 .. row0 + rows_out - 1 of the length-N real
+// results, times out_scale, at out[t - row0][c] (pitch out_pitch floats).
+// tmax (may be NULL; only with row0 = 0 and rows_out = N): the maximum of |out|
+// of every tile of 128 / B rows x 2B columns, at tmax[tile row * nbx + bx]
+// (nbx = column blocks of the image) as float bits.
+// TMA: the Hermitian half arrives by nb tensor copies of h rows x 2B complex
+// (tmap: the launch's half spectra as [images][rows][in_pitch] 8-byte elements,
+// image `img`; rows past N/2 and columns past the tensor read zeros), waited for
+// on an mbarrier with the bound `wait` in SM cycles; when a wait runs out, bit 2
+// of *err is set, the block waits (default bound) for its copies in flight and
+// returns false without writing.  Otherwise every thread copies 16-byte pieces.
+template <int N, int B, bool TMA = false>
+__device__ __forceinline__ bool c2r_block(const float2* __restrict__ in, int ncols, int in_pitch,
+                                          const float2* __restrict__ stw, float mid_scale, float* __restrict__ out,
+                                          int row0, int rows_out, int out_pitch, float out_scale,
+                                          unsigned* __restrict__ tmax, int nbx, int bx, float2* sm,
+                                          const CUtensorMap* tmap = nullptr, int tma_h = 0, int tma_nb = 0,
+                                          int img = 0, unsigned* err = nullptr, long long wait = FT_WAIT_CYCLES) {
+    const int f = threadIdx.x % B;
+    const int t = threadIdx.x / B;
+    const int c = bx * 2 * B + 2 * f;
+    const bool colok = c < ncols;
+
+    // stage the Hermitian half (rows 0 .. N/2, 2B complex each) with 16-byte async
+    // copies; every row is read once and serves both n and N - n.  Thread (t, f)
+    // copies the column pair f of rows t, t + T, ...
+    float2* stg = sm;                                  // [N/2 + 1][2B]
+    if constexpr (TMA) {
+        __shared__ uint64_t mbar;
+        const uint32_t mb = smem_u32(&mbar);
+        if (threadIdx.x == 0) {
+            mbar_init(mb, 1);
+            mbar_arrive_expect_tx(mb, (uint32_t)(tma_nb * tma_h * 2 * B * sizeof(float2)));
+            for (int k = 0; k < tma_nb; ++k) tma_load_3d(stg + k * tma_h * 2 * B, tmap, bx * 2 * B, k * tma_h, img, mb);
+        }
+        __syncthreads();                               // the mbarrier is initialised
+        const bool ok = mbar_wait(mb, 0, wait);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0 && err) atomicOr(err, 4u);
+            mbar_wait(mb, 0);                          // the copies in flight land first
+            return false;
+        }
+    } else {
+        const float2* src = in + c + (size_t)t * in_pitch;
+        float2* dst = stg + t * 2 * B + 2 * f;
+        for (int r = t; r <= N / 2; r += fs_T(N), src += (size_t)fs_T(N) * in_pitch, dst += fs_T(N) * 2 * B) {
+            if (colok)
+                cp_async16(dst, src);
+            else
+                *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+    }
+    c2r_from_stage<N, B>(sm, ncols, stw, mid_scale, out, row0, rows_out, out_pitch, out_scale, tmax, nbx, bx);
     return true;
 }
 

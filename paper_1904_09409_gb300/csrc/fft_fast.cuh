@@ -60,12 +60,17 @@ __host__ __device__ constexpr int fs_twsize(int N) { return fs_twoff(N, fs_nst(N
 // transforms per block for the column R2C kernels (512 threads; for N >= 4096,
 // 1024 threads so that a block still reads 4 column pairs = 32-byte row
 // segments), the column C2R kernel (256 threads, at least 4 column pairs, so
-// 512 threads for N = 1536, 2048; measured faster than 512 for N = 1024 while
-// the R2C kernel is faster with 512) and the row kernels (128 threads: at
-// N = 1024, 2 rows per block run 116 us per 64 x 1024^2, 4 rows 128 us, 1 row 142 us)
+// 512 threads for N = 1536, 2048; for N = 1024 512 threads, 8 column pairs:
+// with the tile maxima of ft_detect 121 us per 64 x 1024^2 against 124 us with
+// 256, and the peak pass is faster on the 16 x 16 tiles that gives) and the row
+// kernels (128 threads: at N = 1024, 2 rows per block run 116 us per
+// 64 x 1024^2, 4 rows 128 us, 1 row 142 us)
 __host__ __device__ constexpr int fs_clampB(int v, int hi) { return v < 1 ? 1 : (v > hi ? hi : v); }
 __host__ __device__ constexpr int fs_Bcol(int N) { return fs_T(N) >= 256 ? 1024 / fs_T(N) : fs_clampB(512 / fs_T(N), 32); }
-__host__ __device__ constexpr int fs_Bc2r(int N) { return fs_T(N) >= 256 ? 1024 / fs_T(N) : fs_clampB(256 / fs_T(N) < 4 ? 4 : 256 / fs_T(N), 32); }
+__host__ __device__ constexpr int fs_Bc2r(int N) {
+    return fs_T(N) >= 256 ? 1024 / fs_T(N)
+                          : fs_clampB(N == 1024 ? 512 / fs_T(N) : (256 / fs_T(N) < 4 ? 4 : 256 / fs_T(N)), 32);
+}
 __host__ __device__ constexpr int fs_Brow(int N) { return fs_clampB(128 / fs_T(N), 16); }
 // padded shared-memory slot of sample n (one spare slot every 16 samples
 // spreads the strided stores of the first pass over the banks)

@@ -204,7 +204,7 @@ def test_peaks_dense_tile_with_k_1024(torch, peak_mode, Hp, S):
 # top_k, threshold; the c2r tile of each H' in the comment.
 DETECT_CASES = [
     (256, 256, 256, 256, 3, float("-inf")),      # 8 x 32 tiles, the single-image workload
-    (1024, 1024, 1024, 1024, 32, float("-inf")),  # 32 x 8 tiles, the batch workload
+    (1024, 1024, 1024, 1024, 32, float("-inf")),  # 16 x 16 tiles, the batch workload
     (200, 200, 216, 256, 40, float("-inf")),      # S = 216 ragged against 32-column tiles
     (100, 96, 96, 192, 17, float("-inf")),        # H' = 192 (3-smooth): 8 x 32 tiles
     (128, 200, 216, 4096, 100, float("-inf")),    # 32 x 8 tiles, expansion H' > H
