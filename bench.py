@@ -146,15 +146,15 @@ def kernel_bytes(name: str, H: int, W: int, S: int, Hp: int, K: int) -> float:
     L = Hp // 2 + 1
     ntiles = ((Hp + 31) // 32) * ((S + 63) // 64)
     kt = min(K, 512)
-    # tiles of step 4's maxima at H' = 1024: 32 rows x 8 columns; the first 32
-    # (one per warp) are read with their one-cell halo (34 x 10 cells)
-    c2r_tiles = (Hp // 32) * ((S + 7) // 8)
+    # tiles of step 4's maxima at H' = 1024: 16 rows x 16 columns; the first 32
+    # (one per warp) are read with their one-cell halo (18 x 18 cells)
+    c2r_tiles = (Hp // 16) * ((S + 15) // 16)
     R = min(c2r_tiles, 32)
     return {
         "k_col_r2c": 4.0 * H * W + 8.0 * L * W,          # image in, half spectrum out
         "k_nvmt_rows": 8.0 * L * W + 8.0 * L * S,        # spectrum rows in, G rows out
         "k_col_c2r": 8.0 * L * S + 4.0 * Hp * S + 4.0 * c2r_tiles,   # G in, map and tile maxima out
-        "k_peak_sparse": 4.0 * c2r_tiles + 4.0 * R * 34 * 10 + 20.0 * K + 4.0,
+        "k_peak_sparse": 4.0 * c2r_tiles + 4.0 * R * 18 * 18 + 20.0 * K + 4.0,
         "k_tile_max": 4.0 * Hp * S + 4.0 * ((Hp + 15) // 16) * ((S + 15) // 16),
         "k_peak_tiles": 4.0 * Hp * S + 8.0 * ntiles * kt,  # map in, tile keys out
         "k_peak_select": 8.0 * ntiles * kt + 20.0 * K + 4.0,

@@ -319,7 +319,7 @@ __device__ __forceinline__ bool rows_block(float2* __restrict__ base, int W, int
     constexpr int R0 = fs_radix(N, 0), G0 = E / R0;
     constexpr int RL = fs_radix(N, fs_nst(N) - 1), GL = E / RL;
     constexpr int STEPX = N / R0;                      // x' distance between a thread's elements
-    using F = FastFft<N, +1, B>;
+    using F = FastFft<N, +1, B, true>;
     // [B][W + 4] input rows (sample x at 2 + x, 16-byte aligned, two zeros on
     // each side) in the FFT's own exchange buffer: they are read only by the
     // gather, which ends before the first exchange

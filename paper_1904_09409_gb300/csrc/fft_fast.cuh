@@ -14,8 +14,15 @@
 // global memory directly.  All index arithmetic is by compile-time constants.
 //
 // Twiddles come from a per-length table (FP64 values rounded to FP32, built on
-// the host): for pass s >= 1, row k holds exp(-2 pi i q k / (P R)) at column q
-// (q = 0 .. R-1, rows padded to an even length so pairs load as float4).
+// the host): for pass s >= 1, row k of a full table holds w_k^q at column q
+// (q = 0 .. R-1), w_k = exp(-2 pi i k / (P R)); row k of a seed table holds
+// only w_k^e for the exponents e = 1, 2, 4, 8 below R (1, 2 for R = 3), and a
+// thread builds the other powers as products of at most four seeds (a few
+// FP32 roundings).  Rows are padded to an even length so that pairs load as
+// float4.  A radix-16 group reads 8 float4 of a full row against 2 of a seed
+// row and 11 complex products: the row kernels (steps 2-3, scattered rows k
+// per lane) run faster on seed tables (103 against 112 us per 64 x 1024^2),
+// the column kernels on full ones (step 4: 121 against 128 us).
 #pragma once
 
 #include "ft_internal.cuh"
@@ -49,14 +56,16 @@ __host__ __device__ constexpr int fs_P(int N, int s) {
     for (int j = 0; j < s; ++j) p *= fs_radix(N, j);
     return p;
 }
-// twiddle row stride of a pass with radix R: R rounded up to even (16-byte rows)
-__host__ __device__ constexpr int fs_rs(int R) { return (R + 1) & ~1; }
-__host__ __device__ constexpr int fs_twoff(int N, int s) {
+// seed powers of a pass with radix R (exponents 1 << j, j < fs_nseed(R)) and the
+// twiddle row stride of a full or a seed table, rounded up to even (16-byte rows)
+__host__ __device__ constexpr int fs_nseed(int R) { return R == 16 ? 4 : R == 8 ? 3 : R == 2 ? 1 : 2; }
+__host__ __device__ constexpr int fs_rs(int R, bool seed) { return ((seed ? fs_nseed(R) : R) + 1) & ~1; }
+__host__ __device__ constexpr int fs_twoff(int N, int s, bool seed) {
     int o = 0;
-    for (int j = 1; j < s; ++j) o += fs_P(N, j) * fs_rs(fs_radix(N, j));
+    for (int j = 1; j < s; ++j) o += fs_P(N, j) * fs_rs(fs_radix(N, j), seed);
     return o;
 }
-__host__ __device__ constexpr int fs_twsize(int N) { return fs_twoff(N, fs_nst(N)); }
+__host__ __device__ constexpr int fs_twsize(int N, bool seed) { return fs_twoff(N, fs_nst(N), seed); }
 // transforms per block for the column R2C kernels (512 threads; for N >= 4096,
 // 1024 threads so that a block still reads 4 column pairs = 32-byte row
 // segments), the column C2R kernel (256 threads, at least 4 column pairs, so
@@ -87,6 +96,32 @@ __device__ __forceinline__ void cp_async_wait_all() {
 
 template <int SIGN>
 __device__ __forceinline__ float2 tw_sign(float2 w) { return SIGN > 0 ? make_float2(w.x, -w.y) : w; }
+
+// w[q] = w_k^q (conjugated for SIGN > 0), q = 1 .. R-1, from the seed row at wp
+template <int R, int SIGN>
+__device__ __forceinline__ void tw_powers(const float4* __restrict__ wp, float2 (&w)[R]) {
+    const float4 a = __ldg(wp);
+    w[1] = tw_sign<SIGN>(make_float2(a.x, a.y));
+    if constexpr (R == 3) {
+        w[2] = tw_sign<SIGN>(make_float2(a.z, a.w));
+    } else if constexpr (R >= 4) {
+        w[2] = tw_sign<SIGN>(make_float2(a.z, a.w));
+        w[3] = cmul(w[1], w[2]);
+        if constexpr (R >= 8) {
+            const float4 b = __ldg(wp + 1);
+            w[4] = tw_sign<SIGN>(make_float2(b.x, b.y));
+            w[5] = cmul(w[1], w[4]);
+            w[6] = cmul(w[2], w[4]);
+            w[7] = cmul(w[3], w[4]);
+            if constexpr (R == 16) {
+                w[8] = tw_sign<SIGN>(make_float2(b.z, b.w));
+#pragma unroll
+                for (int q = 9; q < 16; ++q) w[q] = cmul(w[q - 8], w[8]);
+            }
+        }
+    }
+    static_assert(R == 2 || R == 3 || R == 4 || R == 8 || R == 16, "radix without seed powers");
+}
 
 // radix-16 as 4 x 4 with the internal twiddles exp(SIGN 2 pi i m / 16)
 template <int SIGN>
@@ -125,7 +160,8 @@ struct Dft<16, SIGN> {
     }
 };
 
-template <int N, int SIGN, int B>
+// SEED: the twiddle table is a seed table (the row kernels' tables), else full
+template <int N, int SIGN, int B, bool SEED = false>
 struct FastFft {
     static constexpr int E = fs_E(N);
     static constexpr int T = N / E;
@@ -147,10 +183,17 @@ struct FastFft {
         constexpr int R = fs_radix(N, s), P = fs_P(N, s), G = E / R;
 #pragma unroll
         for (int m = 0; m < G; ++m) {
-            if constexpr (P > 1) {
-                constexpr int RS = fs_rs(R);
+            if constexpr (P > 1 && SEED) {
+                constexpr int RS = fs_rs(R, true);
                 const int k = (t + m * T) % P;
-                const float4* w = reinterpret_cast<const float4*>(stw + fs_twoff(N, s) + k * RS);
+                float2 w[R];
+                tw_powers<R, SIGN>(reinterpret_cast<const float4*>(stw + fs_twoff(N, s, true) + k * RS), w);
+#pragma unroll
+                for (int q = 1; q < R; ++q) v[m * R + q] = cmul(v[m * R + q], w[q]);
+            } else if constexpr (P > 1) {
+                constexpr int RS = fs_rs(R, false);
+                const int k = (t + m * T) % P;
+                const float4* w = reinterpret_cast<const float4*>(stw + fs_twoff(N, s, false) + k * RS);
 #pragma unroll
                 for (int h = 0; h < RS / 2; ++h) {
                     const float4 ww = __ldg(w + h);

@@ -125,7 +125,7 @@ template <int N, int INTERP>
 __global__ void __launch_bounds__(fs_T(N) * fs_Brow(N), 1024 / (fs_T(N) * fs_Brow(N)))
 k_nvmt_rows_fast(float2* __restrict__ ws, int W, int Hp, int L, const float2* __restrict__ stw,
                  unsigned* __restrict__ err, long long wait) {
-    extern __shared__ __align__(16) float2 sm[];
+    extern __shared__ __align__(128) float2 sm[];
     pdl_trigger();
     pdl_wait();
     rows_block<N, INTERP, fs_Brow(N), true>(ws + (size_t)blockIdx.y * L * N, W, Hp, L, stw, blockIdx.x, sm, err,
@@ -138,7 +138,7 @@ k_nvmt_rows_adjoint_fast(float2* __restrict__ ws, int W, int Hp, int L, const fl
     constexpr int B = fs_Brow(N), E = fs_E(N), T = N / E;
     constexpr int R0 = fs_radix(N, 0), G0 = E / R0;
     constexpr int RL = fs_radix(N, fs_nst(N) - 1), GL = E / RL;
-    using F = FastFft<N, -1, B>;
+    using F = FastFft<N, -1, B, true>;                 // the row length's seed table
     extern __shared__ float2 sm[];
     const int f = threadIdx.x % B;
     const int t = threadIdx.x / B;

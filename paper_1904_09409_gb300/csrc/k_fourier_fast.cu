@@ -43,10 +43,10 @@ k_nvmt_rows_fourier_fast(float2* __restrict__ ws, int Hp, int L, int batch, cons
     using Sh = FrShape<W, M, S>;
     constexpr int B = Sh::B, TW = Sh::TW, TS = Sh::TS;
     constexpr int EW = fs_E(W), EM = fs_E(M), ES = fs_E(S);
-    using FW = FastFft<W, -1, B>;
-    using FMf = FastFft<M, -1, B>;
-    using FMi = FastFft<M, +1, B>;
-    using FS = FastFft<S, +1, B>;
+    using FW = FastFft<W, -1, B, true>;
+    using FMf = FastFft<M, -1, B, true>;
+    using FMi = FastFft<M, +1, B, true>;
+    using FS = FastFft<S, +1, B, true>;
     constexpr int R0W = fs_radix(W, 0), G0W = EW / R0W, RLW = fs_radix(W, fs_nst(W) - 1), GLW = EW / RLW;
     constexpr int R0M = fs_radix(M, 0), G0M = EM / R0M, RLM = fs_radix(M, fs_nst(M) - 1), GLM = EM / RLM;
     constexpr int R0S = fs_radix(S, 0), G0S = ES / R0S, RLS = fs_radix(S, fs_nst(S) - 1), GLS = ES / RLS;
@@ -187,10 +187,10 @@ k_nvmt_rows_fourier_adj_fast(float2* __restrict__ ws, int Hp, int L, int batch, 
     using Sh = FrShape<W, M, S>;
     constexpr int B = Sh::B, TW = Sh::TW, TS = Sh::TS;
     constexpr int EW = fs_E(W), EM = fs_E(M), ES = fs_E(S);
-    using FS = FastFft<S, -1, B>;
-    using FMf = FastFft<M, -1, B>;
-    using FMi = FastFft<M, +1, B>;
-    using FW = FastFft<W, +1, B>;
+    using FS = FastFft<S, -1, B, true>;
+    using FMf = FastFft<M, -1, B, true>;
+    using FMi = FastFft<M, +1, B, true>;
+    using FW = FastFft<W, +1, B, true>;
     constexpr int R0W = fs_radix(W, 0), G0W = EW / R0W, RLW = fs_radix(W, fs_nst(W) - 1), GLW = EW / RLW;
     constexpr int R0M = fs_radix(M, 0), G0M = EM / R0M, RLM = fs_radix(M, fs_nst(M) - 1), GLM = EM / RLM;
     constexpr int R0S = fs_radix(S, 0), G0S = ES / R0S, RLS = fs_radix(S, fs_nst(S) - 1), GLS = ES / RLS;

@@ -144,15 +144,18 @@ static ft_status build_chirps(ft_plan p) {
 }
 
 // Per-pass twiddles of the fixed-length kernels: for pass s >= 1 with radix R and
-// P = product of the earlier radices, row k (stride fs_rs(R)) holds
-// exp(-2 pi i q k / (P R)) at column q, taken from the exact-index table tw of
-// length N; padding entries are zero.
-static void stage_twiddles(int N, const float2* tw, float2* out) {
+// P = product of the earlier radices, row k (stride fs_rs(R, seed)) holds
+// exp(-2 pi i q k / (P R)) at column q (full table), or at column j the power
+// q = 1 << j for j < fs_nseed(R) (seed table: the row lengths fx, fw, fm), taken
+// from the exact-index table tw of length N; padding entries are zero.
+static void stage_twiddles(int N, const float2* tw, float2* out, bool seed) {
     for (int s = 1; s < fs_nst(N); ++s) {
-        const int R = fs_radix(N, s), P = fs_P(N, s), step = N / (P * R), RS = fs_rs(R);
-        float2* o = out + fs_twoff(N, s);
+        const int R = fs_radix(N, s), P = fs_P(N, s), step = N / (P * R), RS = fs_rs(R, seed);
+        const int ncol = seed ? fs_nseed(R) : R;
+        float2* o = out + fs_twoff(N, s, seed);
         for (int k = 0; k < P; ++k)
-            for (int q = 0; q < RS; ++q) o[k * RS + q] = q < R ? tw[q * k * step] : make_float2(0.f, 0.f);
+            for (int j = 0; j < RS; ++j)
+                o[k * RS + j] = j < ncol ? tw[(seed ? 1 << j : j) * k * step] : make_float2(0.f, 0.f);
     }
 }
 
@@ -341,21 +344,22 @@ ft_status ft_plan_create_space(ft_plan* out, int img_H, int img_W, int n_slope, 
     const char* force = getenv("FT_FORCE_GENERIC");
     const bool generic = force && force[0] == '1';
     const bool fast_y = fs_has(fy.N), fast_x = fs_has(fx.N);
-    const size_t sy = fast_y ? fs_twsize(fy.N) : 0, sx = fast_x ? fs_twsize(fx.N) : 0;
+    // the column length's table is full, the row lengths' tables are seed tables
+    const size_t sy = fast_y ? fs_twsize(fy.N, false) : 0, sx = fast_x ? fs_twsize(fx.N, true) : 0;
     // per-pass tables of the band-limited interpolator's lengths W and M
     const bool fast_w = fw.N && fs_has(fw.N), fast_m = fm.N && fs_has(fm.N);
-    const size_t sw = fast_w ? fs_twsize(fw.N) : 0, smm = fast_m ? fs_twsize(fm.N) : 0;
+    const size_t sw = fast_w ? fs_twsize(fw.N, true) : 0, smm = fast_m ? fs_twsize(fm.N, true) : 0;
     std::vector<float2> tw((size_t)fy.N + fx.N + sy + sx + fw.N + fm.N + sw + smm);
     twiddles(fy.N, tw.data());
     twiddles(fx.N, tw.data() + fy.N);
-    if (fast_y) stage_twiddles(fy.N, tw.data(), tw.data() + fy.N + fx.N);
-    if (fast_x) stage_twiddles(fx.N, tw.data() + fy.N, tw.data() + fy.N + fx.N + sy);
+    if (fast_y) stage_twiddles(fy.N, tw.data(), tw.data() + fy.N + fx.N, false);
+    if (fast_x) stage_twiddles(fx.N, tw.data() + fy.N, tw.data() + fy.N + fx.N + sy, true);
     const size_t wo = (size_t)fy.N + fx.N + sy + sx;
     if (fw.N) twiddles(fw.N, tw.data() + wo);
     if (fm.N) twiddles(fm.N, tw.data() + wo + fw.N);
     const size_t so = wo + fw.N + fm.N;
-    if (fast_w) stage_twiddles(fw.N, tw.data() + wo, tw.data() + so);
-    if (fast_m) stage_twiddles(fm.N, tw.data() + wo + fw.N, tw.data() + so + sw);
+    if (fast_w) stage_twiddles(fw.N, tw.data() + wo, tw.data() + so, true);
+    if (fast_m) stage_twiddles(fm.N, tw.data() + wo + fw.N, tw.data() + so + sw, true);
     e = cudaMalloc(&p->d_tw, tw.size() * sizeof(float2));
     if (e != cudaSuccess) {
         delete p;
