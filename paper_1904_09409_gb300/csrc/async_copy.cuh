@@ -49,6 +49,15 @@ __device__ __forceinline__ void bulk_g2s(void* smem_dst, const void* gmem_src, u
         : "memory");
 }
 
+// prefetch into L2 of the box at (x, y, z) of the tensor *tmap (a hint: no
+// shared memory, nothing to wait for; coordinates outside the tensor fetch nothing)
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* tmap, int x, int y, int z) {
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
+                     reinterpret_cast<uint64_t>(tmap)),
+                 "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+
 // 3-D tiled tensor copy (TMA) of the box at (x, y, z) of the tensor described by
 // *tmap (a __grid_constant__ kernel parameter) into this block's shared memory,
 // completing on mbar; x times the element size must be a multiple of 16 bytes

@@ -79,13 +79,16 @@ __device__ __forceinline__ void r2c_finish(float2 (&v)[fs_E(N)], float2* sm, int
 // [ncols] floats, image `img`; rows outside the image and columns past it read
 // zeros), waited for on an mbarrier with the bound `wait`; when it runs out, bit
 // 3 of *err is set, the block waits (default bound) for its copies and returns
-// false without writing.  Otherwise the first pass reads global memory directly.
+// false without writing; pf_img >= 0: the same boxes of column block pf_bx of
+// image pf_img (a block one resident wave later) are prefetched into L2.
+// Otherwise the first pass reads global memory directly.
 template <int N, int B, bool TMA = false>
 __device__ __forceinline__ bool r2c_block(const float* __restrict__ in, int rows_in, int ncols, int in_pitch,
                                           int row0, const float2* __restrict__ stw, float2* __restrict__ out,
                                           int out_pitch, float end_scale, float mid_scale, int bx, float2* sm,
                                           const CUtensorMap* tmap = nullptr, int tma_h = 0, int tma_nb = 0,
-                                          int img = 0, unsigned* err = nullptr, long long wait = FT_WAIT_CYCLES) {
+                                          int img = 0, unsigned* err = nullptr, long long wait = FT_WAIT_CYCLES,
+                                          int pf_bx = 0, int pf_img = -1) {
     constexpr int E = fs_E(N);
     constexpr int R0 = fs_radix(N, 0), G0 = E / R0;
     using F = FastFft<N, -1, B>;
@@ -105,6 +108,8 @@ __device__ __forceinline__ bool r2c_block(const float* __restrict__ in, int rows
             mbar_arrive_expect_tx(mb, (uint32_t)(tma_nb * tma_h * 2 * B * sizeof(float)));
             for (int k = 0; k < tma_nb; ++k)
                 tma_load_3d(stg + k * tma_h * 2 * B, tmap, bx * 2 * B, k * tma_h - row0, img, mb);
+            if (pf_img >= 0)
+                for (int k = 0; k < tma_nb; ++k) tma_prefetch_3d(tmap, pf_bx * 2 * B, k * tma_h - row0, pf_img);
         }
         __syncthreads();                               // the mbarrier is initialised
         const bool ok = mbar_wait(mb, 0, wait);
@@ -248,14 +253,17 @@ __device__ __forceinline__ void c2r_from_stage(float2* sm, int ncols, const floa
 // image `img`; rows past N/2 and columns past the tensor read zeros), waited for
 // on an mbarrier with the bound `wait` in SM cycles; when a wait runs out, bit 2
 // of *err is set, the block waits (default bound) for its copies in flight and
-// returns false without writing.  Otherwise every thread copies 16-byte pieces.
+// returns false without writing; pf_img >= 0: the same boxes of column block
+// pf_bx of image pf_img (a block one resident wave later) are prefetched into
+// L2.  Otherwise every thread copies 16-byte pieces.
 template <int N, int B, bool TMA = false>
 __device__ __forceinline__ bool c2r_block(const float2* __restrict__ in, int ncols, int in_pitch,
                                           const float2* __restrict__ stw, float mid_scale, float* __restrict__ out,
                                           int row0, int rows_out, int out_pitch, float out_scale,
                                           unsigned* __restrict__ tmax, int nbx, int bx, float2* sm,
                                           const CUtensorMap* tmap = nullptr, int tma_h = 0, int tma_nb = 0,
-                                          int img = 0, unsigned* err = nullptr, long long wait = FT_WAIT_CYCLES) {
+                                          int img = 0, unsigned* err = nullptr, long long wait = FT_WAIT_CYCLES,
+                                          int pf_bx = 0, int pf_img = -1) {
     const int f = threadIdx.x % B;
     const int t = threadIdx.x / B;
     const int c = bx * 2 * B + 2 * f;
@@ -272,6 +280,8 @@ __device__ __forceinline__ bool c2r_block(const float2* __restrict__ in, int nco
             mbar_init(mb, 1);
             mbar_arrive_expect_tx(mb, (uint32_t)(tma_nb * tma_h * 2 * B * sizeof(float2)));
             for (int k = 0; k < tma_nb; ++k) tma_load_3d(stg + k * tma_h * 2 * B, tmap, bx * 2 * B, k * tma_h, img, mb);
+            if (pf_img >= 0)
+                for (int k = 0; k < tma_nb; ++k) tma_prefetch_3d(tmap, pf_bx * 2 * B, k * tma_h, pf_img);
         }
         __syncthreads();                               // the mbarrier is initialised
         const bool ok = mbar_wait(mb, 0, wait);

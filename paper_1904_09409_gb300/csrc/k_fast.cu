@@ -18,15 +18,19 @@ __global__ void __launch_bounds__(fs_T(N) * fs_Bcol(N), 1024 / (fs_T(N) * fs_Bco
 k_col_r2c_fast(const float* __restrict__ in, int rows_in, int ncols, int in_pitch, size_t in_img,
                int row0, const float2* __restrict__ stw, float2* __restrict__ out, int out_pitch,
                size_t out_img, float end_scale, float mid_scale, const __grid_constant__ CUtensorMap tmap,
-               int tma_h, int tma_nb, unsigned* __restrict__ err, long long wait, int follows_peak) {
+               int tma_h, int tma_nb, unsigned* __restrict__ err, long long wait, int pf, int follows_peak) {
     extern __shared__ __align__(128) float2 sm[];
     pdl_trigger();
     if (!follows_peak) pdl_wait();
     const float* src = in + (size_t)blockIdx.y * in_img;
     float2* dst = out + (size_t)blockIdx.y * out_img;
-    if (tma_nb > 0)
+    if (tma_nb > 0) {
+        const int nxt = blockIdx.y * gridDim.x + blockIdx.x + pf;
+        const int pimg = pf > 0 && nxt < gridDim.x * gridDim.y ? nxt / gridDim.x : -1;
         r2c_block<N, fs_Bcol(N), true>(src, rows_in, ncols, in_pitch, row0, stw, dst, out_pitch, end_scale,
-                                       mid_scale, blockIdx.x, sm, &tmap, tma_h, tma_nb, blockIdx.y, err, wait);
+                                       mid_scale, blockIdx.x, sm, &tmap, tma_h, tma_nb, blockIdx.y, err, wait,
+                                       nxt - pimg * gridDim.x, pimg);
+    }
     else
         r2c_block<N, fs_Bcol(N)>(src, rows_in, ncols, in_pitch, row0, stw, dst, out_pitch, end_scale, mid_scale,
                                  blockIdx.x, sm);
@@ -41,7 +45,7 @@ k_col_c2r_fast(const float2* __restrict__ in, int ncols, int in_pitch, size_t in
                const float2* __restrict__ stw, float mid_scale, float* __restrict__ out, int row0,
                int rows_out, int out_pitch, size_t out_img, float out_scale, unsigned* __restrict__ tmax,
                const __grid_constant__ CUtensorMap tmap, int tma_h, int tma_nb, unsigned* __restrict__ err,
-               long long wait) {
+               long long wait, int pf) {
     extern __shared__ __align__(128) float2 sm[];
     pdl_trigger();
     pdl_wait();
@@ -49,10 +53,13 @@ k_col_c2r_fast(const float2* __restrict__ in, int ncols, int in_pitch, size_t in
     const float2* src = in + (size_t)blockIdx.y * in_img;
     float* dst = out + (size_t)blockIdx.y * out_img;
     unsigned* tm = tmax ? tmax + (size_t)blockIdx.y * bands * gridDim.x : nullptr;
-    if (tma_nb > 0)
+    if (tma_nb > 0) {
+        const int nxt = blockIdx.y * gridDim.x + blockIdx.x + pf;
+        const int pimg = pf > 0 && nxt < gridDim.x * gridDim.y ? nxt / gridDim.x : -1;
         c2r_block<N, fs_Bc2r(N), true>(src, ncols, in_pitch, stw, mid_scale, dst, row0, rows_out, out_pitch,
                                        out_scale, tm, gridDim.x, blockIdx.x, sm, &tmap, tma_h, tma_nb, blockIdx.y,
-                                       err, wait);
+                                       err, wait, nxt - pimg * gridDim.x, pimg);
+    }
     else
         c2r_block<N, fs_Bc2r(N)>(src, ncols, in_pitch, stw, mid_scale, dst, row0, rows_out, out_pitch, out_scale,
                                  tm, gridDim.x, blockIdx.x, sm);
@@ -268,6 +275,19 @@ static bool r2c_tma_map(const float* in, int rows_in, int ncols, int in_pitch, s
     return true;
 }
 
+// blocks of kernel k (threads, sm bytes of dynamic shared memory) resident on
+// the whole GPU at once: the distance, in blocks, of the column kernels' L2
+// prefetch (0 when it cannot be determined)
+template <typename K>
+static int resident_blocks(K k, int threads, size_t sm) {
+    int dev = 0, per = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, threads, sm) != cudaSuccess)
+        return 0;
+    return per * nsm;
+}
+
 template <int N>
 static cudaError_t go_r2c(const float* in, int rows_in, int ncols, int in_pitch, size_t in_img, int row0,
                           const float2* stw, float2* out, int out_pitch, size_t out_img, float es, float ms,
@@ -281,8 +301,9 @@ static cudaError_t go_r2c(const float* in, int rows_in, int ncols, int in_pitch,
     int h = 0, nb = 0;
     if (!err || wait < 0 || !r2c_tma_map<N>(in, rows_in, ncols, in_pitch, in_img, batch, &map, &h, &nb)) nb = 0;
     dim3 grid((ncols + 2 * B - 1) / (2 * B), batch);
+    const int pf = resident_blocks(k_col_r2c_fast<N>, fs_T(N) * B, sm);
     return launch_maybe_pdl(k_col_r2c_fast<N>, grid, dim3(fs_T(N) * B), sm, st, pdl, in, rows_in, ncols, in_pitch,
-                            in_img, row0, stw, out, out_pitch, out_img, es, ms, map, h, nb, err, wait,
+                            in_img, row0, stw, out, out_pitch, out_img, es, ms, map, h, nb, err, wait, pf,
                             (pdl && follows_peak) ? 1 : 0);
 }
 
@@ -345,8 +366,9 @@ static cudaError_t go_c2r(const float2* in, int ncols, int in_pitch, size_t in_i
     int h = 0, nb = 0;
     if (!err || wait < 0 || !c2r_tma_map<N>(in, in_pitch, in_img, batch, &map, &h, &nb)) nb = 0;
     dim3 grid((ncols + 2 * B - 1) / (2 * B), batch);
+    const int pf = resident_blocks(k_col_c2r_fast<N>, fs_T(N) * B, sm);
     return launch_maybe_pdl(k_col_c2r_fast<N>, grid, dim3(fs_T(N) * B), sm, st, pdl, in, ncols, in_pitch, in_img, stw,
-                            mid, out, row0, rows_out, out_pitch, out_img, os, tmax, map, h, nb, err, wait);
+                            mid, out, row0, rows_out, out_pitch, out_img, os, tmax, map, h, nb, err, wait, pf);
 }
 
 template <int N, int INTERP>
