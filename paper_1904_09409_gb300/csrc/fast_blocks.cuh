@@ -80,7 +80,7 @@ __device__ __forceinline__ void r2c_finish(float2 (&v)[fs_E(N)], float2* sm, int
 // zeros), waited for on an mbarrier with the bound `wait`; when it runs out, bit
 // 3 of *err is set, the block waits (default bound) for its copies and returns
 // false without writing; pf_img >= 0: the same boxes of column block pf_bx of
-// image pf_img (a block one resident wave later) are prefetched into L2.
+// image pf_img (a block half a resident wave later) are prefetched into L2.
 // Otherwise the first pass reads global memory directly.
 template <int N, int B, bool TMA = false>
 __device__ __forceinline__ bool r2c_block(const float* __restrict__ in, int rows_in, int ncols, int in_pitch,
@@ -254,7 +254,7 @@ __device__ __forceinline__ void c2r_from_stage(float2* sm, int ncols, const floa
 // on an mbarrier with the bound `wait` in SM cycles; when a wait runs out, bit 2
 // of *err is set, the block waits (default bound) for its copies in flight and
 // returns false without writing; pf_img >= 0: the same boxes of column block
-// pf_bx of image pf_img (a block one resident wave later) are prefetched into
+// pf_bx of image pf_img (a block half a resident wave later) are prefetched into
 // L2.  Otherwise every thread copies 16-byte pieces.
 template <int N, int B, bool TMA = false>
 __device__ __forceinline__ bool c2r_block(const float2* __restrict__ in, int ncols, int in_pitch,
