@@ -154,7 +154,9 @@ k_nvmt_rows_adjoint_fast(float2* __restrict__ ws, int W, int Hp, int L, const fl
     const int f = threadIdx.x % B;
     const int t = threadIdx.x / B;
     const int l = blockIdx.x * B + f;
-    float2* row = ws + (size_t)blockIdx.y * L * N + (size_t)l * N;
+    // images in reverse order, as in k_nvmt_rows_fast (L2 reuse with the column
+    // kernels before and after, which run in forward order)
+    float2* row = ws + (size_t)(gridDim.y - 1 - blockIdx.y) * L * N + (size_t)l * N;
 
     float2 v[E];
 #pragma unroll
