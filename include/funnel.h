@@ -369,7 +369,8 @@ int ft_plan_get_precision(ft_plan plan);
  * with the default bound and returns without writing its rows.  Bit 2: a wait
  * of the inverse column kernel (step 4) for the tensor copies that stage its
  * Hermitian half columns timed out; bit 3: the same for the forward column
- * kernel (step 1) and its image columns.  Those blocks likewise drain their
+ * kernel (step 1) and its image columns, or for the first kernel of
+ * ft_abs_mse_backward and its map columns.  Those blocks likewise drain their
  * copies in flight and return without writing.  The CUDA context stays usable
  * in every case.  Waits for all work on the plan's device,
  * copies the flags to *flags (host) and clears them; returns FT_ERR_TIMEOUT

@@ -280,9 +280,12 @@ cudaError_t launch_col_r2c_fast(const float* in, int rows_in, int ncols, int in_
 // target of the gradient workload (k_col_r2c_loss_fast); partial gets
 // col_r2c_loss_blocks() floats per image
 int col_r2c_loss_blocks(const FftLen& f, int ncols);
+// (err, wait: with err given, the map columns are staged through tensor copies
+// whose bounded waits set bit 3 of *err when they run out)
 cudaError_t launch_col_r2c_loss_fast(const float* map, const float* target, int ncols, const FftLen& f,
                                      float2* out, int out_pitch, size_t out_img, float end_scale, float mid_scale,
-                                     float scale, float gscale, float* partial, int batch, cudaStream_t st);
+                                     float scale, float gscale, float* partial, int batch, cudaStream_t st,
+                                     unsigned* err = nullptr, long long wait = FT_WAIT_CYCLES);
 // tmax (may be NULL; only with row0 = 0 and rows_out = N): the maxima of |out| per
 // tile of c2r_tile_shape rows x columns, [batch][N / rows][ceil(ncols / cols)] as
 // float bits

@@ -72,25 +72,84 @@ k_col_c2r_fast(const float2* __restrict__ in, int ncols, int in_pitch, size_t in
 // gradient of k_loss.cu), while every thread adds r^2 of its samples (FP32,
 // compensated) and the block writes one partial of the image's loss.  Each map
 // cell is loaded by exactly one thread, so the partials of an image's blocks
-// add up to its sum of r^2.  Everything after the load is r2c_finish.
+// add up to its sum of r^2 (within a block by a fixed shuffle tree).  With
+// tma_nb > 0 the map columns arrive by tensor copies into the exchange buffer
+// (pmap, waited for with the bound `wait`; bit 3 of *err when it runs out, and
+// the block returns without writing), their values go to registers, and the
+// target columns (tmapt) follow into the same buffer; the map and target boxes
+// of the block pf blocks later are prefetched into L2.  Everything after the
+// load is r2c_finish.
 template <int N>
 __global__ void __launch_bounds__(fs_T(N) * fs_Bcol(N), 1024 / (fs_T(N) * fs_Bcol(N)))
 k_col_r2c_loss_fast(const float* __restrict__ map, const float* __restrict__ target, int ncols, size_t img_cells,
                     const float2* __restrict__ stw, float2* __restrict__ out, int out_pitch, size_t out_img,
-                    float end_scale, float mid_scale, float scale, float gscale, float* __restrict__ partial) {
-    constexpr int B = fs_Bcol(N), E = fs_E(N);
+                    float end_scale, float mid_scale, float scale, float gscale, float* __restrict__ partial,
+                    const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUtensorMap tmapt, int tma_h,
+                    int tma_nb, unsigned* __restrict__ err, long long wait, int pf) {
+    constexpr int B = fs_Bcol(N), E = fs_E(N), NT = fs_T(N) * fs_Bcol(N), NW = NT / 32;
     constexpr int R0 = fs_radix(N, 0), G0 = E / R0;
     using F = FastFft<N, -1, B>;
-    extern __shared__ float2 sm[];
-    __shared__ float red[fs_T(N) * fs_Bcol(N)];
+    extern __shared__ __align__(128) float2 sm[];
+    __shared__ float red[NW];
     const int f = threadIdx.x % B;
     const int t = threadIdx.x / B;
     const int c = blockIdx.x * 2 * B + 2 * f;
     const bool colok = c < ncols;
     const float* P = map + (size_t)blockIdx.y * img_cells + c;
     const float* Tg = target + (size_t)blockIdx.y * img_cells + c;
-
+    const float* stg = reinterpret_cast<const float*>(sm);   // [tma_nb tma_h][2B] map, then target values
+    __shared__ uint64_t mbar;
+    const uint32_t mb = smem_u32(&mbar);
     float2 v[E];
+    if (tma_nb > 0) {
+        // the block's map columns by tensor copies into the exchange buffer, their
+        // values to registers, then the target columns into the same buffer
+        // (the mbarrier's second phase; both are read before the FFT's first
+        // exchange); the map and target boxes of the block pf blocks later are
+        // prefetched into L2
+        if (threadIdx.x == 0) {
+            mbar_init(mb, 1);
+            mbar_arrive_expect_tx(mb, (uint32_t)(tma_nb * tma_h * 2 * B * sizeof(float)));
+            for (int k = 0; k < tma_nb; ++k)
+                tma_load_3d(reinterpret_cast<float*>(sm) + k * tma_h * 2 * B, &pmap, blockIdx.x * 2 * B, k * tma_h,
+                            blockIdx.y, mb);
+            const int nxt = blockIdx.y * gridDim.x + blockIdx.x + pf;
+            if (pf > 0 && nxt < gridDim.x * gridDim.y) {
+                const int pimg = nxt / gridDim.x, pbx = nxt - pimg * gridDim.x;
+                for (int k = 0; k < tma_nb; ++k) {
+                    tma_prefetch_3d(&pmap, pbx * 2 * B, k * tma_h, pimg);
+                    tma_prefetch_3d(&tmapt, pbx * 2 * B, k * tma_h, pimg);
+                }
+            }
+        }
+        __syncthreads();                               // the mbarrier is initialised
+        bool ok = mbar_wait(mb, 0, wait);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0 && err) atomicOr(err, 8u);
+            mbar_wait(mb, 0);                          // the copies in flight land first
+            return;
+        }
+#pragma unroll
+        for (int m = 0; m < G0; ++m)
+#pragma unroll
+            for (int q = 0; q < R0; ++q)
+                v[m * R0 + q] = *reinterpret_cast<const float2*>(stg + F::template in_pos<0>(t, m, q) * 2 * B + 2 * f);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // these reads before the refill
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            mbar_arrive_expect_tx(mb, (uint32_t)(tma_nb * tma_h * 2 * B * sizeof(float)));
+            for (int k = 0; k < tma_nb; ++k)
+                tma_load_3d(reinterpret_cast<float*>(sm) + k * tma_h * 2 * B, &tmapt, blockIdx.x * 2 * B, k * tma_h,
+                            blockIdx.y, mb);
+        }
+        ok = mbar_wait(mb, 1, wait);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0 && err) atomicOr(err, 8u);
+            mbar_wait(mb, 1);
+            return;
+        }
+    }
+
     float acc = 0.f, comp = 0.f;
     auto add = [&](float y) {                          // compensated sum of r^2
         const float z = y - comp;
@@ -105,8 +164,9 @@ k_col_r2c_loss_fast(const float* __restrict__ map, const float* __restrict__ tar
             const int row = F::template in_pos<0>(t, m, q);
             float2 g = make_float2(0.f, 0.f);
             if (colok) {
-                const float2 p = __ldg(reinterpret_cast<const float2*>(P + (size_t)row * ncols));
-                const float2 tt = __ldg(reinterpret_cast<const float2*>(Tg + (size_t)row * ncols));
+                const float2 p = tma_nb > 0 ? v[m * R0 + q] : __ldg(reinterpret_cast<const float2*>(P + (size_t)row * ncols));
+                const float2 tt = tma_nb > 0 ? *reinterpret_cast<const float2*>(stg + row * 2 * B + 2 * f)
+                                             : __ldg(reinterpret_cast<const float2*>(Tg + (size_t)row * ncols));
                 const float r0 = fabsf(p.x) * scale - tt.x, r1 = fabsf(p.y) * scale - tt.y;
                 add(r0 * r0);
                 add(r1 * r1);
@@ -116,13 +176,18 @@ k_col_r2c_loss_fast(const float* __restrict__ map, const float* __restrict__ tar
             }
             v[m * R0 + q] = g;
         }
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int o = (fs_T(N) * fs_Bcol(N)) / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
+    // the block's partial: a fixed shuffle tree per warp, then over the warps
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();                                   // also: the staged map is no longer read
+    if (warp == 0) {
+        float x = lane < NW ? red[lane] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) partial[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = x;
     }
-    if (threadIdx.x == 0) partial[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
     r2c_finish<N, fs_Bcol(N)>(v, sm, t, f, stw, colok, out + (size_t)blockIdx.y * out_img + c, out_pitch, end_scale,
                               mid_scale);
 }
@@ -318,14 +383,23 @@ static cudaError_t go_r2c(const float* in, int rows_in, int ncols, int in_pitch,
 template <int N>
 static cudaError_t go_r2c_loss(const float* map, const float* target, int ncols, const float2* stw, float2* out,
                                int out_pitch, size_t out_img, float es, float ms, float scale, float gscale,
-                               float* partial, int batch, cudaStream_t st) {
+                               float* partial, int batch, cudaStream_t st, unsigned* err, long long wait) {
     constexpr int B = fs_Bcol(N);
     const size_t sm = (size_t)FastFft<N, -1, B>::SLOTS * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_col_r2c_loss_fast<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
+    CUtensorMap pm, tm;
+    memset(&pm, 0, sizeof(pm));
+    memset(&tm, 0, sizeof(tm));
+    const size_t cells = (size_t)N * ncols;
+    int h = 0, nb = 0, h2 = 0, nb2 = 0;
+    if (!err || wait < 0 || !r2c_tma_map<N>(map, N, ncols, ncols, cells, batch, &pm, &h, &nb) ||
+        !r2c_tma_map<N>(target, N, ncols, ncols, cells, batch, &tm, &h2, &nb2))
+        nb = 0;
     dim3 grid((ncols + 2 * B - 1) / (2 * B), batch);
-    k_col_r2c_loss_fast<N><<<grid, fs_T(N) * B, sm, st>>>(map, target, ncols, (size_t)N * ncols, stw, out, out_pitch,
-                                                          out_img, es, ms, scale, gscale, partial);
+    const int pf = prefetch_distance(k_col_r2c_loss_fast<N>, fs_T(N) * B, sm);
+    k_col_r2c_loss_fast<N><<<grid, fs_T(N) * B, sm, st>>>(map, target, ncols, cells, stw, out, out_pitch, out_img, es,
+                                                          ms, scale, gscale, partial, pm, tm, h, nb, err, wait, pf);
     return cudaGetLastError();
 }
 
@@ -441,11 +515,12 @@ int col_r2c_loss_blocks(const FftLen& f, int ncols) {
 
 cudaError_t launch_col_r2c_loss_fast(const float* map, const float* target, int ncols, const FftLen& f,
                                      float2* out, int out_pitch, size_t out_img, float end_scale, float mid_scale,
-                                     float scale, float gscale, float* partial, int batch, cudaStream_t st) {
+                                     float scale, float gscale, float* partial, int batch, cudaStream_t st,
+                                     unsigned* err, long long wait) {
     if (ncols & 1) return cudaErrorInvalidValue;
     switch (f.N) {
 #define X(n) case n: return go_r2c_loss<n>(map, target, ncols, f.stw, out, out_pitch, out_img, end_scale, mid_scale, \
-                                           scale, gscale, partial, batch, st);
+                                           scale, gscale, partial, batch, st, err, wait);
         FT_FAST_LENGTHS(X)
 #undef X
     }

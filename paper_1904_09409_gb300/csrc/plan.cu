@@ -781,7 +781,7 @@ ft_status ft_abs_mse_backward(ft_plan p, const float* d_map, const float* d_targ
     const float gscale = (float)(1.0 / ((double)batch * (double)cells));
     FT_LAUNCH(p, FT_KERNEL_COL_R2C, st,
               launch_col_r2c_loss_fast(d_map, d_target, p->S, p->fy, ws, p->S, (size_t)p->L * p->S, inv, 2.f * inv,
-                                       scale, gscale, partial, batch, st),
+                                       scale, gscale, partial, batch, st, p->d_tc_err, p->tc_wait),
               "loss and adjoint of step 4");
     FT_LAUNCH(p, FT_KERNEL_LOSS, st, launch_loss_finish(partial, nblk, cells, d_loss, batch, st), "loss");
     return backward_tail(p, ws, d_grad_img, batch, st);

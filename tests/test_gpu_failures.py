@@ -111,3 +111,34 @@ def test_bulk_copy_wait_timeout_fp32_rows(torch, interp):
         assert f.ft_plan_tc_errors(plan) == 0
     for i in range(2):
         assert _gpu.rel_l2(got[i], oracle.funnel_ref(imgs[i], W, H, interp)) <= 1e-5
+
+
+def test_loss_backward_tensor_copy_timeout(torch):
+    """The first kernel of ft_abs_mse_backward stages its map columns with tensor
+    copies (bit 3) and the adjoint of step 1 its Hermitian halves (bit 2); with
+    the wait limit at 0 both give up, the blocks drain their copies and write
+    nothing, and ft_plan_tc_errors returns FT_ERR_TIMEOUT with flags 0xc; with
+    the default limit the loss and the image gradient equal ft_abs_mse_grad
+    followed by ft_backward."""
+    from paper_1904_09409_gb300 import funnel as f
+    H = W = 256
+    imgs = _images(2, H, W, seed=5)
+    rng = np.random.default_rng(5)
+    with f.Plan(H, W, W, H) as plan:
+        P = torch.from_numpy(_gpu.forward(plan, imgs)).cuda()
+        tgt = torch.from_numpy(rng.uniform(0.0, 1.0, size=(2, H, W)).astype(np.float32)).cuda()
+        f.ft_plan_set_wait_cycles(plan, 0)
+        f.ft_abs_mse_backward(plan, P, tgt, 2.0 / W)
+        with pytest.raises(f.FunnelError) as e:
+            f.ft_plan_tc_errors(plan)
+        assert e.value.status == f.FT_ERR_TIMEOUT
+        assert "flags 0xc" in str(e.value)
+        f.ft_plan_set_wait_cycles(plan, f.FT_WAIT_CYCLES_DEFAULT)
+        loss, gx = f.ft_abs_mse_backward(plan, P, tgt, 2.0 / W)
+        loss_g, gmap = f.ft_abs_mse_grad(plan, P, tgt, 2.0 / W)
+        gx_ref = torch.empty_like(gx)
+        f.ft_backward(plan, gmap, gx_ref)
+        torch.cuda.synchronize()
+        assert f.ft_plan_tc_errors(plan) == 0
+    assert torch.allclose(loss, loss_g, rtol=1e-5, atol=0.0)
+    assert float((gx - gx_ref).norm() / gx_ref.norm()) <= 1e-5
