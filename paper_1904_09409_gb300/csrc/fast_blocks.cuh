@@ -420,7 +420,6 @@ __device__ __forceinline__ bool rows_block(float2* __restrict__ base, int W, int
                         acc.y = fmaf(w, a.y, acc.y);
                     }
                 }
-                if ((i + q * STEPX) & 1) acc = make_float2(-acc.x, -acc.y);
                 v[m * R0 + q] = acc;
                 rem += sB;
                 qf += sA;
@@ -429,6 +428,10 @@ __device__ __forceinline__ bool rows_block(float2* __restrict__ base, int W, int
         }
     }
     __syncthreads();                                   // the staged rows are dead from here
+    // The centring factor (-1)^i of the gathered samples is a shift of the
+    // transform by N/2: with Z the transform of the taps, the row gets
+    // G[s] = (-1)^(s + N/2) Z[(s + N/2) mod N], i.e. Z[s'] (times (-1)^s') goes
+    // to position (s' + N/2) mod N
     F::template run<0>(v, sm, t, f, stw);
     if (l >= L) return true;
     float2* row = base + (size_t)l * N;
@@ -438,8 +441,8 @@ __device__ __forceinline__ bool rows_block(float2* __restrict__ base, int W, int
         for (int q = 0; q < RL; ++q) {
             const int s = F::out_pos(t, m, q);
             float2 val = v[m * RL + q];
-            if ((s + N / 2) & 1) val = make_float2(-val.x, -val.y);
-            row[s] = val;
+            if (s & 1) val = make_float2(-val.x, -val.y);
+            row[s < N / 2 ? s + N / 2 : s - N / 2] = val;
         }
     return true;
 }
