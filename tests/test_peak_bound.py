@@ -3,13 +3,18 @@
 The detected list of Sec. 4.4 is the top K strict local maxima of the order
 (|P| descending, linear index ascending).  A peak never exceeds the maximum M of
 its tile, so once K peaks are known, a tile whose M is below the K-th of them
-cannot contribute.  This file replays that procedure in plain NumPy (the brightest
-tiles first, batches of tiles cut back to the best K, a rising bound, then every
-other tile whose maximum reaches the bound) and checks that it reproduces the
-oracle's list procedure exactly, on maps built to stress it: ties, plateaus
-across tile borders, tile maxima on borders next to brighter cells, thresholds,
-ragged last tiles and K above the number of peaks.  The CUDA kernel is checked
-against the oracle by the GPU tests; this pins the procedure itself.
+cannot contribute.  This file replays the procedure of the peak pass in plain
+NumPy: round 1 takes every valid tile whose maximum reaches T, the nw-th largest
+valid maximum (ties included); tiles run nw per batch; in a batch every tile
+marks its strict local maxima at or above the bound and reports its best marked
+value, the K-th largest of those (K <= nw) cuts the appends, the candidates are
+cut back to the best K, which raises the bound; round 2 takes every other valid
+tile whose maximum reaches the bound.  It must reproduce the oracle's list
+procedure exactly, on maps built to stress it: ties, plateaus across tile
+borders, tile maxima on borders next to brighter cells, thresholds, ragged last
+tiles and K above the number of peaks; mistakes planted in the replay (no second
+round, strict comparisons, an off-by-one cut) must change some list.  The CUDA
+kernel is checked against the oracle by the GPU tests; this pins the procedure.
 """
 import numpy as np
 import pytest
@@ -32,10 +37,12 @@ def strict_local_maxima(A):
     return ok
 
 
-def tile_bound_peaks(A, K, thr, th, tw, warps, round2=True, strict=False):
+def tile_bound_peaks(A, K, thr, th, tw, warps, round2=True, strict=False, cut_strict=False, cut_rank=0):
     """Peaks read from the tiles that the bound admits; returns (list, tiles read).
-    round2=False / strict=True plant mistakes (no second round; tiles admitted
-    only when their maximum exceeds the bound, which loses tied peaks)."""
+    The keyword arguments plant mistakes: round2=False drops the second round,
+    strict=True admits a tile only when its maximum exceeds the bound, cut_strict
+    appends only cells strictly above the cut, cut_rank=-1 takes the cut from
+    the (K-1)-th best tile value instead of the K-th."""
     Hp, S = A.shape
     lm = strict_local_maxima(A)
     nty, ntx = -(-Hp // th), -(-S // tw)
@@ -43,33 +50,36 @@ def tile_bound_peaks(A, K, thr, th, tw, warps, round2=True, strict=False):
                   for ty in range(nty)]).ravel()
     state = {"cand": [], "bound": thr, "read": 0}
 
-    def scan(tile):
+    def marks(tile, bound):
         ty, tx = divmod(tile, ntx)
         state["read"] += 1
-        for t in range(ty * th, min((ty + 1) * th, Hp)):
-            for s in range(tx * tw, min((tx + 1) * tw, S)):
-                if A[t, s] >= state["bound"] and lm[t, s]:
-                    state["cand"].append((-float(A[t, s]), t * S + s))
-
-    def cut():                                   # keep the best K, raise the bound
-        if len(state["cand"]) >= K:
-            state["cand"] = sorted(state["cand"])[:K]
-            state["bound"] = max(thr, -state["cand"][-1][0])
+        return [(float(A[t, s]), t * S + s)
+                for t in range(ty * th, min((ty + 1) * th, Hp))
+                for s in range(tx * tw, min((tx + 1) * tw, S))
+                if A[t, s] >= bound and lm[t, s]]
 
     def run(tiles):
         for b0 in range(0, len(tiles), warps):
             bound = state["bound"]
-            for tile in tiles[b0:b0 + warps]:
-                if M[tile] > bound or (M[tile] == bound and not strict):
-                    scan(tile)
-            cut()
+            marked = [marks(tile, bound) for tile in tiles[b0:b0 + warps]
+                      if M[tile] > bound or (M[tile] == bound and not strict)]
+            cut = bound
+            bests = sorted((max(v for v, _ in mk) for mk in marked if mk), reverse=True)
+            r = K - 1 + cut_rank
+            if K <= warps and 0 <= r < len(bests) and len(bests) >= K:
+                cut = max(cut, bests[r])
+            for mk in marked:
+                state["cand"] += [(-v, lin) for v, lin in mk if (v > cut if cut_strict else v >= cut)]
+            if len(state["cand"]) >= K:          # keep the best K, raise the bound
+                state["cand"] = sorted(state["cand"])[:K]
+                state["bound"] = max(state["bound"], -state["cand"][-1][0])
 
-    eligible = [i for i in range(M.size) if M[i] >= thr]
-    first = sorted(eligible, key=lambda i: (-M[i], i))[:warps]
-    run(first)
-    rest = [i for i in eligible if i not in set(first) and M[i] >= state["bound"]]
+    valid = [i for i in range(M.size) if M[i] >= thr]
+    top = sorted((M[i] for i in valid), reverse=True)
+    T = top[warps - 1] if len(top) >= warps else -np.inf
+    run([i for i in valid if M[i] >= T])
     if round2:
-        run(rest)
+        run([i for i in valid if M[i] < T and M[i] >= state["bound"]])
     out = sorted(state["cand"])[:K]
     return [(lin // S, lin % S, -v) for v, lin in out], state["read"]
 
@@ -119,10 +129,12 @@ def test_tile_bound_reads_few_tiles_when_peaks_stand_out():
     assert read <= 8                                   # of 64 tiles
 
 
-@pytest.mark.parametrize("mistake", [{"round2": False}, {"strict": True}])
+@pytest.mark.parametrize("mistake", [{"round2": False}, {"strict": True}, {"cut_strict": True}, {"cut_rank": -1}])
 def test_planted_mistakes_are_caught(mistake):
-    """Dropping the second round, or admitting a tile only when its maximum is
-    strictly above the bound, changes the list on some of the maps above."""
+    """Dropping the second round, admitting a tile only when its maximum is
+    strictly above the bound, appending only cells strictly above the cut, or
+    taking the cut from the (K-1)-th best tile value changes the list on some of
+    the maps above."""
     caught = False
     for kind in ("noise", "ties", "plateaus", "border_max", "peaks"):
         for Hp, S, th, tw in ((32, 48, 8, 8), (24, 30, 4, 8)):
