@@ -104,3 +104,23 @@ def test_detect_batches_arguments(torch):
         assert call([], 0) == f.FT_OK
         assert call([good], 1, batch=0) == f.FT_OK
         torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("case", ["inverse", "dense"])
+def test_detect_batches_fallbacks(torch, monkeypatch, case):
+    """The inverse space and the per-tile key pass (FT_PEAKS=dense) take nb
+    ft_detect calls instead of the pipeline: the same records, counts and maps."""
+    from paper_1904_09409_gb300 import funnel as f
+    if case == "dense":
+        monkeypatch.setenv("FT_PEAKS", "dense")
+        plan = f.Plan(256, 256, 256, 256)
+    else:
+        plan = f.Plan(256, 192, space="inverse")
+    with plan:
+        xs = [torch.from_numpy(b[:, :plan.H, :plan.W].copy()).cuda()
+              for b in _batches(3, 4, 256, seed=11 if case == "dense" else 13)]
+        ref_out, ref_cnt, ref_map = _per_call(plan, xs, 8, float("-inf"))
+        m = torch.empty((4, plan.Hp, plan.S), device="cuda")
+        out, cnt = f.ft_detect_batches(plan, xs, m, 8)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref_out) and torch.equal(cnt, ref_cnt) and torch.equal(m, ref_map)
